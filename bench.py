@@ -1,0 +1,390 @@
+"""Benchmark of the vectorial PSF hot path on GB300.
+
+Default workload: the Fourier strategy at scale - 256^2 pupil, 512 x 512
+pixels at 10 nm, 128 planes over +-2 um, Gibson-Lanni + Noll c_4..c_21 - one
+full z-stack per step.  `--workload bessel` times the batched Bessel strategy
+(4096 emitters, 128^2 px) instead.
+
+Prints one JSON line (rank 0).  `value` is voxels/s over all ranks with the
+inputs resident on the device; `e2e` repeats the measurement through the same
+C-ABI call with the result read back to pinned host memory every step.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+
+Multi-GPU (torchrun): every rank computes its own independent stack (weak
+scaling, no collective on the data path); the step time is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                  "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+def oracle_sample(workload, budget_s):
+    """Times the oracle on a bounded sample of the workload.
+    Returns (voxels/s, description)."""
+    from oracle import bessel as ob
+    from oracle import fourier as of
+    from oracle.optics import Optics
+    from paper_2502_03170_gb300 import workloads as W
+    t0 = time.perf_counter()
+    vox = 0
+    if workload == "fourier":
+        c = W.fourier()
+        opt = Optics.from_dict(c["optics"])
+        zs = np.asarray(c["grid"]["z"])
+        n = 0
+        while True:
+            g1 = dict(c["grid"], z=[zs[(n * 37) % len(zs)]])
+            of.psf_fourier(opt, c["n_pupil"], g1, zernike=c["zernike"])
+            n += 1
+            vox += c["grid"]["nx"] * c["grid"]["ny"]
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        desc = "%d planes of 512x512 (cycling over the 128 of the stack; separable FP64 form, numpy/BLAS)" % n
+    else:
+        c = W.bessel()
+        opt = Optics.from_dict(c["optics"])
+        n = 0
+        while True:
+            e = (n * 997) % c["n_emitters"]
+            I = ob.psf_bessel_batch(opt, c["depth"], c["zernike"], c["z_offsets"],
+                                    c["z"], c["n_theta"], c["n_r"], c["nx"],
+                                    c["ny"], c["dx"], c["dy"], project=True,
+                                    emitters=[e])
+            vox += I.size
+            n += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        desc = "%d emitters (cycling over the 4096; FP64 GL sum + interpolation, numpy)" % n
+    dt = time.perf_counter() - t0
+    return vox / dt, desc
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import ctypes
+
+    import torch
+
+    from paper_2502_03170_gb300 import _lib, api
+    from paper_2502_03170_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    peaks, peaks_src = load_peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ws = api.Workspace(dev)
+
+    if args.workload == "fourier":
+        c = W.fourier(seed_salt=rank)
+        g = api.Grid(c["grid"])
+        opt = api.make_optics(c["optics"])
+        N = c["n_pupil"]
+        nz, nx, ny = g.c.nz, g.c.nx, g.c.ny
+        out = torch.empty((nz, nx, ny), dtype=torch.float32, device=dev)
+
+        def step(o=out):
+            api.fourier(opt, N, g, zernike=c["zernike"], precision=args.precision,
+                        out=o, workspace=ws)
+        voxels = nz * nx * ny
+        h2d = nz * 8 + 21 * 8            # z list (double-float) + Zernike row
+        dom_class = 2                   # stage-2 contraction + |E|^2
+        dom_work = 8.0 * 3 * nz * nx * ny * N      # algorithmic FLOP per step
+        cfg = {"workload": "fourier_vectorial_zstack", "n_pupil": N,
+               "nx": nx, "ny": ny, "nz": nz, "dx_um": 0.010,
+               "z_range_um": [-2.0, 2.0], "gibson_lanni": True,
+               "zernike_noll": "4..21 ~ N(0, 0.1 rad)",
+               "precision": args.precision}
+    else:
+        c = W.bessel(seed_salt=rank)
+        opt = api.make_optics(c["optics"], _lib.PSF_PROJECT_AXISYMMETRIC)
+        nsl = int(c["z_offsets"][-1])
+        dv = lambda a, dt: torch.as_tensor(np.asarray(a)).to(dev, dt).contiguous()
+        depth_d, zern_d = dv(c["depth"], torch.float64), dv(c["zernike"], torch.float64)
+        offs_d, z_d = dv(c["z_offsets"], torch.int32), dv(c["z"], torch.float64)
+        out = torch.empty((nsl, c["nx"], c["ny"]), dtype=torch.float32, device=dev)
+        need = lib.psf_bessel_workspace_size(ctypes.byref(opt), c["n_emitters"], nsl,
+                                             c["n_theta"], c["n_r"], c["nx"], c["ny"], 0)
+        buf = ws.get(need)
+
+        def step(o=out):
+            _lib.check(lib, lib.psf_bessel_vectorial(
+                ctypes.byref(opt), c["n_emitters"], api._ptr(depth_d),
+                api._ptr(zern_d), 21, api._ptr(offs_d), api._ptr(z_d), nsl,
+                c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"], 0,
+                api._ptr(o), None, api._ptr(buf), buf.numel(), api._stream()))
+        voxels = nsl * c["nx"] * c["ny"]
+        h2d = 0
+        dom_class = 4                   # radial -> Cartesian epilogue (HBM write)
+        dom_work = 4.0 * voxels         # algorithmic bytes written per step
+        cfg = {"workload": "bessel_vectorial_batched", "n_emitters": c["n_emitters"],
+               "n_slices": nsl, "n_theta": c["n_theta"], "n_r": c["n_r"],
+               "nx": c["nx"], "ny": c["ny"], "dx_um": 0.020, "precision": "fp32"}
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing (value) ----
+    lib.psf_kernel_timing(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()                       # evict L2 between steps
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    counts = {}
+    for k in range(7):
+        n_ = ctypes.c_int(0)
+        t_ = ctypes.c_double(0.0)
+        lib.psf_kernel_timing_read(k, ctypes.byref(n_), ctypes.byref(t_))
+        counts[k] = (n_.value, t_.value)
+    lib.psf_kernel_timing(0)
+    launches = sum(v[0] for v in counts.values())
+
+    # ---- end-to-end through the C ABI with the result read back ----
+    host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_host = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev2[i][0].record(stream)
+        step()
+        host.copy_(out, non_blocking=True)
+        ev2[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_host += time.perf_counter() - t0
+    ms_e2e = max(sum(a.elapsed_time(b) for a, b in ev2), 1e3 * t_host)
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    ms_step = ms / args.steps
+    value = world * voxels / (ms_step * 1e-3)
+    e2e_value = world * voxels / (ms_e2e / args.steps * 1e-3)
+
+    n_dom, t_dom = counts[dom_class]
+    if args.workload == "fourier" and args.precision != "fp32":
+        bound, unit = "tensor", "TFLOP/s"
+        peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        achieved = dom_work * args.steps / (t_dom * 1e-3) / 1e12 if t_dom else None
+    elif args.workload == "fourier":
+        bound, unit = "alu", "TFLOP/s"
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        achieved = dom_work * args.steps / (t_dom * 1e-3) / 1e12 if t_dom else None
+    else:
+        bound, unit = "hbm", "GB/s"
+        peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+        achieved = dom_work * args.steps / (t_dom * 1e-3) / 1e9 if t_dom else None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": {2: "stage2_contraction_intensity",
+                       4: "bessel_radial_to_cartesian"}[dom_class],
+            "launches": n_dom // max(args.steps, 1),
+            "avg_launch_ms": t_dom / max(n_dom, 1),
+            "peak_source": "%s (MEASURED_PEAKS.json)" % peaks_src
+            if peaks_src == "measured" else "fallback"}
+    if bound == "alu":
+        roof["peak_source"] = ("FP32 CUDA cores: 152 SMs x 128 lanes x 2 FLOP x "
+                               "%.0f MHz (max SM clock)" % float(peaks.get("sm_max_mhz", 2070.0)))
+
+    result = {
+        "metric": "PSF voxels/s (fwd) at <=1e-5 rel err vs FP64",
+        "value": value, "unit": "voxels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded, paper-shaped parameters)",
+        "config": dict(cfg, l2="flushed between timed steps (256 MB write)",
+                       parallelism="independent stack per GPU" if world > 1 else "1 GPU"),
+        "e2e": {"value": e2e_value, "unit": "voxels/s",
+                "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(out.numel() * 4)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if args.precision == "split_fp16":
+        result["dtype"] = "f16x2 (split hi+lo, f32 accumulate)"
+    elif args.precision == "split_bf16":
+        result["dtype"] = "bf16x2 (split hi+lo, f32 accumulate)"
+    return result, rank
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fourier", choices=["fourier", "bessel"])
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "split_fp16", "split_bf16"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per_step = []
+        desc = ""
+        budget = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+        for i in range(args.warmup + args.steps):
+            v, desc = oracle_sample(args.workload, budget)
+            if i >= args.warmup:
+                per_step.append(v)
+        v = statistics.mean(per_step)
+        out = {"impl": "reference", "metric": "PSF voxels/s (fwd) at <=1e-5 rel err vs FP64",
+               "value": v, "unit": "voxels/s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic (seeded, paper-shaped parameters)",
+               "config": {"workload": "fourier_vectorial_zstack" if args.workload == "fourier"
+                          else "bessel_vectorial_batched"},
+               "cpu_baseline": {"value": v, "unit": "voxels/s", "cores": cores_used(),
+                                "kind": "oracle", "sample": desc},
+               "e2e": {"value": v, "unit": "voxels/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    result, rank = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1:
+            v, desc = oracle_sample(args.workload, args.cpu_budget)
+            result["cpu_baseline"] = {"value": v, "unit": "voxels/s",
+                                      "cores": cores_used(), "kind": "oracle",
+                                      "sample": desc}
+        print(json.dumps(result))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * psf.h - C ABI of the GB300 vectorial PSF library (libpsf.so).
+ *
+ * Computes vectorial high-NA point-spread-function z-stacks from the
+ * Richards-Wolf integral (Eq. 1) with the correction factors of Eq. 12
+ * (apodization Eq. 16, Gaussian envelope Eq. 17, Gibson-Lanni Eq. 13-14,
+ * Zernike + free phase mask Eq. 15) by the two strategies of Sec. 3:
+ *   - Cartesian / Fourier (Eq. 8): pupil fields mapped to a zoomed focal grid
+ *     by per-z separable matrix-DFT contractions;
+ *   - spherical / Bessel (Eq. 10-11): theta quadrature of J_0/J_1/J_2 as a
+ *     [r x theta] x [theta x z] contraction, then radial interpolation.
+ *
+ * Conventions shared by every entry point
+ *   - Lengths in micrometres.  k = 2 pi n_i / lambda (Sec. 3.1), f k = 1, so
+ *     E carries -i/(2 pi) (Eq. 8) or -i/2 (Eq. 10); both strategies return
+ *     fields on the same absolute scale.
+ *   - Pupil grid (Fourier): N x N cell-centred nodes u_p = (2p+1-N)/N, disk
+ *     (2p+1-N)^2 + (2q+1-N)^2 <= N^2, sin(theta) = (NA/n_i) sqrt(u^2+v^2)
+ *     (footnote of Sec. 3.4), weight ds^2 with ds = 2 NA / (n_i N).
+ *     Index p runs along x, q along y.
+ *   - Output grid: x_a = (a - (nx-1)/2) dx, y_b = (b - (ny-1)/2) dy.
+ *   - Layout (Sec. 4.1): row-major (z, channel, x, y).  Intensity is
+ *     float [nz][nx][ny]; fields are interleaved complex64 [nz][3][nx][ny].
+ *   - Zernike coefficients: Noll index j = 1..n_zern stored at [j-1], radians,
+ *     RMS-normalised on the unit pupil (Noll 1976); phi from +x towards +y.
+ *   - Fresnel coefficients q_s = q_p = 1 (Eq. 7 not applied).
+ *
+ * Ownership and execution
+ *   - Every device buffer is owned by the caller.  The library allocates no
+ *     device memory: each call takes a caller-provided device workspace whose
+ *     size the matching *_workspace_size() query returns.
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous with respect to the host.  Host arrays
+ *     passed in (z lists, Zernike rows) are read before the call returns.
+ *   - Calls that share a workspace must not overlap on the GPU.
+ *
+ * Errors
+ *   - Arguments are validated on the host before anything is enqueued; on
+ *     error nothing is launched and outputs are untouched.  The return value
+ *     is PSF_OK or a negative PSF_ERR_* code; psf_last_error() gives a
+ *     message (thread-local, valid until the next call on the thread).
+ *   - Conditions only the device can see (a bounded wait that gave up, a
+ *     non-axisymmetric Zernike row inside device data) are recorded in a
+ *     status word at the start of the workspace; psf_workspace_status()
+ *     synchronises the stream and returns it.  A kernel that records an
+ *     error returns early without trapping.
+ */
+#ifndef PSF_H
+#define PSF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define PSF_OK                    0
+#define PSF_ERR_ARG              -1  /* bad size / pointer / NA >= n_i ...     */
+#define PSF_ERR_NOT_AXISYMMETRIC -2  /* m != 0 Zernike term on the Bessel path */
+#define PSF_ERR_WORKSPACE        -3  /* workspace missing or too small         */
+#define PSF_ERR_PRECISION        -4  /* precision mode not supported here      */
+#define PSF_ERR_CUDA             -5  /* a CUDA runtime call failed             */
+#define PSF_ERR_DEVICE_TIMEOUT   -6  /* a bounded device wait gave up          */
+
+/* ---- precision of the contractions ---------------------------------------
+ * Phases are always formed in extended precision (FP64 host/device for the
+ * per-call pupil and twiddle tables, double-float for per-(node, z) defocus)
+ * and reduced modulo one cycle before sin/cos.                              */
+#define PSF_PREC_FP32        0  /* plain FP32 FMA complex contractions        */
+#define PSF_PREC_SPLIT_FP16  1  /* tcgen05 kind::f16, operands split hi+lo
+                                   fp16 (power-of-two scaled), 3 products,
+                                   FP32 accumulation in TMEM                  */
+#define PSF_PREC_SPLIT_BF16  2  /* same with bf16 hi+lo operands              */
+
+/* ---- flags ---------------------------------------------------------------- */
+#define PSF_PROJECT_AXISYMMETRIC 1  /* Bessel path: drop m != 0 Zernike terms
+                                       instead of reporting an error (Sec. 3.4:
+                                       the spherical form needs an
+                                       axisymmetric pupil)                     */
+
+/* Physical parameters (Eq. 1, Eq. 13-14, Eq. 16-17). */
+typedef struct {
+  double NA;          /* numerical aperture, 0 < NA < n_i                      */
+  double lambda;      /* vacuum wavelength, um                                 */
+  double n_i;         /* immersion index (propagation medium, Sec. 3.1)        */
+  double n_s;         /* sample index                                          */
+  double n_g;         /* coverslip index                                       */
+  double n_i_design;  /* design (starred) immersion index                      */
+  double n_g_design;  /* design coverslip index                                */
+  double t_g;         /* coverslip thickness, um                               */
+  double t_g_design;  /* design coverslip thickness, um                        */
+  double t_i_design;  /* design immersion thickness t_i*, um                   */
+  double depth;       /* emitter depth t_s, um (Fourier path; the Bessel path
+                         takes one depth per emitter)                          */
+  double pol[4];      /* Jones vector (p_x.re, p_x.im, p_y.re, p_y.im)         */
+  int    apodize;     /* 1: A = sqrt(cos theta) (Eq. 16); 0: A = 1            */
+  double s_env;       /* > 0: Gaussian envelope exp(-sin^2/s_env^2) (Eq. 17)   */
+  int    flags;       /* PSF_PROJECT_AXISYMMETRIC                              */
+} psf_optics;
+
+/* Output grid of the Fourier strategy. */
+typedef struct {
+  int nx, ny;         /* pixels along x and y                                 */
+  double dx, dy;      /* pixel pitch, um                                       */
+  int nz;             /* number of defocus planes                              */
+  const double* z;    /* host [nz] defocus distances, um                       */
+} psf_grid;
+
+/* ========================================================================== */
+/* Fourier (Cartesian) strategy, Eq. 8 with Eq. 12.                           */
+/* ========================================================================== */
+
+/* Bytes of device workspace psf_fourier_vectorial() needs for these sizes
+ * (0 on invalid arguments). */
+size_t psf_fourier_workspace_size(const psf_optics* opt, int n_pupil,
+                                  const psf_grid* grid, int precision);
+
+/* E_c(x_a, y_b, z) = -i/(2 pi) ds^2 sum_{p,q in disk} A e^{iW} e_inf,c / cos
+ *                    e^{i k z cos} e^{i k s_max (u_p x_a + v_q y_b)},
+ * I = |E_x|^2 + |E_y|^2 + |E_z|^2 (Eq. 8, Eq. 6, Eq. 12-17).
+ *   zernike    host [n_zern] (may be NULL if n_zern == 0), 0 <= n_zern <= 66
+ *   phase_map  device float [n_pupil][n_pupil] W_0 in radians, or NULL
+ *   intensity  device float [nz][nx][ny]  (required)
+ *   fields     device complex64 [nz][3][nx][ny], or NULL
+ * Sizes: 2 <= n_pupil <= 4096, nx, ny, nz >= 1. */
+int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
+                          const psf_grid* grid, const double* zernike,
+                          int n_zern, const float* phase_map, int precision,
+                          float* intensity, void* fields, void* workspace,
+                          size_t ws_bytes, void* stream);
+
+/* Workspace for psf_fourier_vectorial_backward(). */
+size_t psf_fourier_backward_workspace_size(const psf_optics* opt, int n_pupil,
+                                           const psf_grid* grid, int precision);
+
+/* Gradient of L_b = sum_{z,x,y} g(I_b) for `batch` independent pupils, by the
+ * adjoint of Eq. 8 with per-z recomputation (no pupil field is stored):
+ *   dL/dW_0[p,q] = sum_{z,c} 2 Re(conj(G^_{c,z}[p,q]) i P_{c,z}[p,q]),
+ *   G^ = conj(C ds^2) A_x^H R conj(A_y),  R = (dL/dI) E_c,
+ *   dL/dc_j = sum_{p,q} Z_j[p,q] dL/dW_0[p,q]   (chain rule through Eq. 15).
+ * With target != NULL the loss is sum (I - T)^2 (dL/dI = 2 (I - T));
+ * otherwise dL/dI = grad_intensity.
+ *   zernike         host [batch][n_zern]
+ *   phase_map       device [batch][n_pupil][n_pupil] or NULL (zero)
+ *   target          device [batch][nz][nx][ny] or NULL
+ *   grad_intensity  device [batch][nz][nx][ny] (used iff target == NULL)
+ *   loss            device float [batch] or NULL (only with target)
+ *   grad_phase_map  device float [batch][n_pupil][n_pupil] or NULL
+ *   grad_zernike    device float [batch][n_zern] or NULL                    */
+int psf_fourier_vectorial_backward(const psf_optics* opt, int n_pupil,
+                                   const psf_grid* grid, int batch,
+                                   const double* zernike, int n_zern,
+                                   const float* phase_map, int precision,
+                                   const float* target,
+                                   const float* grad_intensity, float* loss,
+                                   float* grad_phase_map, float* grad_zernike,
+                                   void* workspace, size_t ws_bytes,
+                                   void* stream);
+
+/* ========================================================================== */
+/* Bessel (spherical) strategy, Eq. 10-11, batched emitters.                  */
+/* ========================================================================== */
+
+/* Workspace for psf_bessel_vectorial(). */
+size_t psf_bessel_workspace_size(const psf_optics* base, int n_emitters,
+                                 int n_slices, int n_theta, int n_r, int nx,
+                                 int ny, int precision);
+
+/* Every emitter e has depth t_s = depth[e], Zernike row zernike[e][0..n_zern)
+ * (only m = 0 terms enter, Sec. 3.4) and defocus planes
+ * z[z_offsets[e] .. z_offsets[e+1]).  Per slice:
+ *   I_n(r_i, z) = sum_j w_j g_n(theta_j) J_n(k r_i sin theta_j)
+ *                 A(theta_j) e^{i(W_e(theta_j) + k z cos theta_j)},
+ * g_0 = sin(1+cos), g_1 = sin^2, g_2 = sin(cos-1) (Eq. 11), Gauss-Legendre
+ * nodes theta_j on [0, asin(NA/n_i)]; r_i = i r_max/(n_r-1) with r_max the
+ * corner radius of the output grid; complex linear interpolation of I_n at
+ * each pixel radius; E from Eq. 10 with the Jones vector of `base`.
+ *   depth, zernike, z_offsets, z : DEVICE arrays (double, double, int, double)
+ *   n_slices   = z_offsets[n_emitters] (host copy, for sizing)
+ *   intensity  device float [n_slices][nx][ny] (packed)
+ *   profiles   device complex64 [n_slices][3][n_r] (I_0, I_1, I_2) or NULL
+ * A non-zero m != 0 coefficient without PSF_PROJECT_AXISYMMETRIC marks the
+ * workspace status PSF_ERR_NOT_AXISYMMETRIC and that emitter's slices are not
+ * written.  Sizes: n_theta in [2, 880], n_r in [2, 4096].                 */
+int psf_bessel_vectorial(const psf_optics* base, int n_emitters,
+                         const double* depth, const double* zernike, int n_zern,
+                         const int* z_offsets, const double* z, int n_slices,
+                         int n_theta, int n_r, int nx, int ny, double dx,
+                         double dy, int precision, float* intensity,
+                         void* profiles, void* workspace, size_t ws_bytes,
+                         void* stream);
+
+/* ========================================================================== */
+/* Status and diagnostics.                                                    */
+/* ========================================================================== */
+
+/* Synchronises `stream` and returns the device status word of `workspace`
+ * (PSF_OK, PSF_ERR_NOT_AXISYMMETRIC or PSF_ERR_DEVICE_TIMEOUT), or
+ * PSF_ERR_CUDA if the stream itself reports an error. */
+int psf_workspace_status(const void* workspace, void* stream);
+
+/* Kernel timing for benchmarks.  While enabled, every hot kernel launch is
+ * bracketed by a pair of CUDA events recorded on the launching stream (the
+ * events are created once and reused; enabling clears previous records).
+ * psf_kernel_timing_read() synchronises on the recorded events and returns
+ * the number of launches and their summed device time for one kernel class:
+ *   0 pupil fields, 1 stage-1 contraction, 2 stage-2 contraction + |E|^2,
+ *   3 Bessel radial contraction, 4 Bessel radial-to-Cartesian epilogue,
+ *   5 adjoint recomputation + contractions, 6 per-call set-up kernels
+ *   (pupil node table, zoom matrices, J_n operand, emitter tables).
+ * Returns PSF_OK, or PSF_ERR_ARG for an unknown class.  Not thread-safe. */
+int psf_kernel_timing(int enable);
+int psf_kernel_timing_read(int kernel_class, int* launches, double* total_ms);
+
+/* Message of the last error on this thread ("" if none). */
+const char* psf_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int psf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSF_H */

@@ -1,0 +1,167 @@
+"""Python API over libpsf: torch tensors in, torch tensors out.
+
+PyTorch supplies device memory and the current CUDA stream only; every step
+of the PSF computation runs in libpsf's kernels (no fallback path exists).
+"""
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PsfGrid, PsfOptics, check
+
+PRECISIONS = {"fp32": _lib.PSF_PREC_FP32, "split_fp16": _lib.PSF_PREC_SPLIT_FP16,
+              "split_bf16": _lib.PSF_PREC_SPLIT_BF16}
+
+
+def make_optics(d, flags=0):
+    """psf_optics from a parameter dict (keys as in ``workloads``)."""
+    o = PsfOptics()
+    o.NA = d["NA"]
+    o.lambda_ = d["lam"]
+    o.n_i = d["n_i"]
+    o.n_s = d.get("n_s", d["n_i"])
+    o.n_g = d.get("n_g", 1.5)
+    o.n_i_design = d.get("n_i_design", o.n_i)
+    o.n_g_design = d.get("n_g_design", o.n_g)
+    o.t_g = d.get("t_g", 170.0)
+    o.t_g_design = d.get("t_g_design", o.t_g)
+    o.t_i_design = d.get("t_i_design", 150.0)
+    o.depth = d.get("depth", 0.0)
+    px, py = d.get("pol", (1.0, 0.0))
+    px, py = complex(px), complex(py)
+    o.pol[0], o.pol[1], o.pol[2], o.pol[3] = px.real, px.imag, py.real, py.imag
+    o.apodize = 1 if d.get("apodize", True) else 0
+    o.s_env = d.get("s_env", 0.0)
+    o.flags = flags
+    return o
+
+
+class Grid:
+    """psf_grid plus the host z array it points to (kept alive here)."""
+
+    def __init__(self, g):
+        self.z = np.ascontiguousarray(np.asarray(g["z"], dtype=np.float64))
+        self.c = PsfGrid()
+        self.c.nx, self.c.ny = int(g["nx"]), int(g["ny"])
+        self.c.dx, self.c.dy = float(g["dx"]), float(g["dy"])
+        self.c.nz = len(self.z)
+        self.c.z = self.z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _zern_host(zernike):
+    if zernike is None:
+        return None, 0
+    z = np.ascontiguousarray(np.asarray(zernike, dtype=np.float64))
+    return z, z.shape[-1]
+
+
+class Workspace:
+    """Device workspace (torch-allocated bytes) reused across calls."""
+
+    def __init__(self, device=None):
+        self.buf = None
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+
+    def get(self, nbytes):
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8,
+                                   device=self.device)
+        return self.buf
+
+    def status(self, stream=None):
+        lib = _lib.load()
+        return lib.psf_workspace_status(_ptr(self.buf), _stream(stream))
+
+
+def fourier(optics, n_pupil, grid, zernike=None, phase_map=None,
+            precision="fp32", fields=False, out=None, workspace=None,
+            stream=None):
+    """Vectorial PSF z-stack by the Fourier strategy (Eq. 8).
+
+    Returns intensity [nz, nx, ny] (float32, cuda) or (intensity, fields) with
+    fields complex64 [nz, 3, nx, ny].
+    """
+    lib = _lib.load()
+    o = optics if isinstance(optics, PsfOptics) else make_optics(optics)
+    g = grid if isinstance(grid, Grid) else Grid(grid)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+    zh, nzern = _zern_host(zernike)
+    ws = workspace or Workspace()
+    need = lib.psf_fourier_workspace_size(ctypes.byref(o), n_pupil,
+                                          ctypes.byref(g.c), prec)
+    if need == 0:
+        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+    buf = ws.get(need)
+    dev = buf.device
+    I = out if out is not None else torch.empty(
+        (g.c.nz, g.c.nx, g.c.ny), dtype=torch.float32, device=dev)
+    F = torch.empty((g.c.nz, 3, g.c.nx, g.c.ny), dtype=torch.complex64,
+                    device=dev) if fields else None
+    pm = None
+    if phase_map is not None:
+        pm = phase_map if torch.is_tensor(phase_map) else torch.as_tensor(
+            np.asarray(phase_map, dtype=np.float32))
+        pm = pm.to(device=dev, dtype=torch.float32).contiguous()
+    check(lib, lib.psf_fourier_vectorial(
+        ctypes.byref(o), n_pupil, ctypes.byref(g.c),
+        None if zh is None else zh.ctypes.data_as(ctypes.c_void_p), nzern,
+        _ptr(pm), prec, _ptr(I), _ptr(F), _ptr(buf), buf.numel(),
+        _stream(stream)))
+    return (I, F) if fields else I
+
+
+def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
+           project=False, profiles=False, precision="fp32", workspace=None,
+           stream=None):
+    """Batched vectorial PSFs by the Bessel strategy (Eq. 10-11).
+
+    depth [n_em], zernike [n_em, n_zern], z_offsets [n_em + 1] (int32),
+    z [n_slices]: torch tensors on the device (or arrays, copied there).
+    Returns intensity [n_slices, nx, ny] (and profiles [n_slices, 3, n_r]).
+    """
+    lib = _lib.load()
+    flags = _lib.PSF_PROJECT_AXISYMMETRIC if project else 0
+    o = optics if isinstance(optics, PsfOptics) else make_optics(optics, flags)
+    if isinstance(optics, PsfOptics):
+        o.flags = flags
+    prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def dv(a, dt):
+        t = a if torch.is_tensor(a) else torch.as_tensor(np.asarray(a))
+        return t.to(device=dev, dtype=dt).contiguous()
+
+    depth_d = dv(depth, torch.float64)
+    zern_d = dv(zernike, torch.float64) if zernike is not None else None
+    offs_d = dv(z_offsets, torch.int32)
+    z_d = dv(z, torch.float64)
+    n_em = depth_d.numel()
+    n_zern = 0 if zern_d is None else zern_d.shape[-1]
+    n_slices = int(z_d.numel())
+    ws = workspace or Workspace(dev)
+    need = lib.psf_bessel_workspace_size(ctypes.byref(o), n_em, n_slices,
+                                         n_theta, n_r, nx, ny, prec)
+    if need == 0:
+        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+    buf = ws.get(need)
+    I = torch.empty((n_slices, nx, ny), dtype=torch.float32, device=dev)
+    P = torch.empty((n_slices, 3, n_r), dtype=torch.complex64,
+                    device=dev) if profiles else None
+    check(lib, lib.psf_bessel_vectorial(
+        ctypes.byref(o), n_em, _ptr(depth_d), _ptr(zern_d), n_zern,
+        _ptr(offs_d), _ptr(z_d), n_slices, n_theta, n_r, nx, ny, float(dx),
+        float(dy), prec, _ptr(I), _ptr(P), _ptr(buf), buf.numel(),
+        _stream(stream)))
+    return (I, P) if profiles else I

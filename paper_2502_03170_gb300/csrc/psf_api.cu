@@ -1,0 +1,744 @@
+// Host side of libpsf: argument validation, FP64 parameter preparation
+// (Eq. 13-15, Gauss-Legendre nodes), workspace layout and kernel launches.
+// Every exported symbol is declared in include/psf.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "bessel_kernels.cuh"
+#include "fourier_kernels.cuh"
+#include "tc_kernels.cuh"
+#include "timing.cuh"
+
+namespace psf {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int cuda_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(PSF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return PSF_OK;
+}
+
+static bool finite_pos(double v) { return isfinite(v) && v > 0; }
+
+static int check_optics(const psf_optics* o) {
+  if (!o) return fail(PSF_ERR_ARG, "optics is NULL");
+  if (!finite_pos(o->NA) || !finite_pos(o->lambda) || !finite_pos(o->n_i))
+    return fail(PSF_ERR_ARG, "NA, lambda and n_i must be finite and > 0");
+  if (!(o->NA < o->n_i))
+    return fail(PSF_ERR_ARG, "NA (%g) must be below n_i (%g)", o->NA, o->n_i);
+  if (!finite_pos(o->n_s) || !finite_pos(o->n_g) || !finite_pos(o->n_i_design) ||
+      !finite_pos(o->n_g_design))
+    return fail(PSF_ERR_ARG, "refractive indices must be finite and > 0");
+  if (!isfinite(o->t_g) || !isfinite(o->t_g_design) || !isfinite(o->t_i_design) ||
+      !isfinite(o->depth) || !isfinite(o->s_env))
+    return fail(PSF_ERR_ARG, "thicknesses / depth / s_env must be finite");
+  for (int i = 0; i < 4; ++i)
+    if (!isfinite(o->pol[i])) return fail(PSF_ERR_ARG, "polarisation not finite");
+  return PSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 13-14: layers of the Gibson-Lanni optical path, W/(2 pi) in cycles is
+// sum_l t_l sqrt(n_l^2 - n_i^2 sin^2) / lambda.  Eq. 14 (as printed) fixes
+// t_i = t_s + n_i (-t_s/n_s - t_g/n_g + t_g*/n_g* + t_i*/n_i*).
+// ---------------------------------------------------------------------------
+static double immersion_thickness(const psf_optics* o, double ts) {
+  return ts + o->n_i * (-ts / o->n_s - o->t_g / o->n_g +
+                        o->t_g_design / o->n_g_design +
+                        o->t_i_design / o->n_i_design);
+}
+
+static GLLayers gl_layers(const psf_optics* o, double ts) {
+  GLLayers g;
+  g.n = 5;
+  g.t[0] = ts;                              g.n_idx[0] = o->n_s;
+  g.t[1] = immersion_thickness(o, ts);      g.n_idx[1] = o->n_i;
+  g.t[2] = -o->t_i_design;                  g.n_idx[2] = o->n_i_design;
+  g.t[3] = o->t_g;                          g.n_idx[3] = o->n_g;
+  g.t[4] = -o->t_g_design;                  g.n_idx[4] = o->n_g_design;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 15, Noll ordering: j -> (n, m), m > 0 cosine, m < 0 sine.
+// ---------------------------------------------------------------------------
+static void noll_nm(int j, int* n_out, int* m_out) {
+  int n = 0;
+  while ((n + 1) * (n + 2) / 2 < j) ++n;
+  const int k = j - n * (n + 1) / 2 - 1;
+  const int am = (n % 2 == 0) ? 2 * ((k + 1) / 2) : 2 * (k / 2) + 1;
+  *n_out = n;
+  *m_out = am == 0 ? 0 : ((j % 2 == 0) ? am : -am);
+}
+
+static double fact(int n) {
+  double f = 1;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// Radial polynomial coefficients of sqrt(norm) R_n^|m|: out[k] multiplies rho^k.
+static void zernike_radial_coeffs(int n, int am, double* out) {
+  for (int k = 0; k <= kZernMaxOrder; ++k) out[k] = 0;
+  const double norm = am == 0 ? sqrt(n + 1.0) : sqrt(2.0 * (n + 1.0));
+  for (int s = 0; s <= (n - am) / 2; ++s) {
+    const double c = ((s % 2) ? -1.0 : 1.0) * fact(n - s) /
+                     (fact(s) * fact((n + am) / 2 - s) * fact((n - am) / 2 - s));
+    out[n - 2 * s] += norm * c;
+  }
+}
+
+static ZernPoly zernike_poly(const double* c, int n_zern) {
+  ZernPoly z;
+  memset(&z, 0, sizeof(z));
+  z.max_m = -1;
+  double rc[kZernMaxOrder + 1];
+  for (int j = 1; j <= n_zern; ++j) {
+    if (c[j - 1] == 0.0) continue;
+    int n, m;
+    noll_nm(j, &n, &m);
+    const int am = m < 0 ? -m : m;
+    zernike_radial_coeffs(n, am, rc);
+    for (int k = 0; k <= kZernMaxOrder; ++k) {
+      if (m >= 0)
+        z.c[am][k] += c[j - 1] * rc[k];
+      else
+        z.s[am][k] += c[j - 1] * rc[k];
+    }
+    if (am > z.max_m) z.max_m = am;
+  }
+  return z;
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on P_n (three-term
+// recurrence), weights 2 / ((1 - x^2) P_n'(x)^2).
+// ---------------------------------------------------------------------------
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double r = cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = r;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * r * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = n == 1 ? r : p1;
+      const double pm = n == 1 ? 1.0 : p0;
+      dp = n * (r * pn - pm) / (r * r - 1.0);
+      const double dr = pn / dp;
+      r -= dr;
+      if (fabs(dr) < 1e-16) break;
+    }
+    x[i] = -r;
+    x[n - 1 - i] = r;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - r * r) * dp * dp);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Workspace carving
+// ---------------------------------------------------------------------------
+struct Carver {
+  char* base;
+  size_t off;
+  explicit Carver(void* b) : base((char*)b), off(kStatusBytes) {}
+  template <class T>
+  T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+// ===========================================================================
+// Fourier strategy
+// ===========================================================================
+static int fourier_zchunk(int N, int nx, int ny, int nz) {
+  // keep the per-chunk pupil + stage-1 buffers near 64 MB (L2-sized)
+  const double per_z = 3.0 * 8.0 * ((double)N * N + (double)ny * N);
+  int zc = (int)(64.0 * 1048576.0 / per_z);
+  if (zc < 1) zc = 1;
+  if (zc > 32) zc = 32;
+  if (zc > nz) zc = nz;
+  (void)nx;
+  return zc;
+}
+
+struct FourierLayout {
+  NodeTable nodes;
+  float2* zz;
+  float2 *Ax, *Ay;
+  float2 *P, *U;       // FP32 path
+  TcOperands tc;       // split-precision path
+  int zc;
+  size_t bytes;
+};
+
+static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
+                                    int precision) {
+  FourierLayout L;
+  memset(&L, 0, sizeof(L));
+  Carver c(ws);
+  const size_t NN = (size_t)N * N;
+  L.nodes.amp = c.take<float>(6 * NN);
+  L.nodes.wfr = c.take<float>(NN);
+  L.nodes.kh = c.take<float>(NN);
+  L.nodes.kl = c.take<float>(NN);
+  L.zz = c.take<float2>(g->nz);
+  L.zc = fourier_zchunk(N, g->nx, g->ny, g->nz);
+  if (precision == PSF_PREC_FP32) {
+    L.Ax = c.take<float2>((size_t)g->nx * N);
+    L.Ay = c.take<float2>((size_t)g->ny * N);
+    L.P = c.take<float2>((size_t)L.zc * 3 * NN);
+    L.U = c.take<float2>((size_t)L.zc * 3 * g->ny * N);
+  } else {
+    tc_fourier_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.tc);
+  }
+  L.bytes = align_up(c.off, 256);
+  return L;
+}
+
+static int check_fourier_args(const psf_optics* opt, int N, const psf_grid* g,
+                              int precision) {
+  int r = check_optics(opt);
+  if (r) return r;
+  if (N < 2 || N > 4096) return fail(PSF_ERR_ARG, "n_pupil %d outside [2, 4096]", N);
+  if (!g) return fail(PSF_ERR_ARG, "grid is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > 16384 || g->ny > 16384)
+    return fail(PSF_ERR_ARG, "grid sizes must be in [1, 16384] (nz >= 1)");
+  if (!finite_pos(g->dx) || !finite_pos(g->dy))
+    return fail(PSF_ERR_ARG, "pixel pitch must be finite and > 0");
+  if (!g->z) return fail(PSF_ERR_ARG, "grid z list is NULL");
+  for (int i = 0; i < g->nz; ++i)
+    if (!isfinite(g->z[i]) || fabs(g->z[i]) > 1e4)
+      return fail(PSF_ERR_ARG, "z[%d] not finite or beyond 1e4 um", i);
+  if (precision != PSF_PREC_FP32 && precision != PSF_PREC_SPLIT_FP16 &&
+      precision != PSF_PREC_SPLIT_BF16)
+    return fail(PSF_ERR_PRECISION, "unknown precision mode %d", precision);
+  if (precision != PSF_PREC_FP32) {
+    const char* why = tc_fourier_supported(N, g->nx, g->ny);
+    if (why) return fail(PSF_ERR_PRECISION, "split precision: %s", why);
+  }
+  return PSF_OK;
+}
+
+static NodeParams node_params(const psf_optics* opt, int N, const double* zern,
+                              int n_zern, const float* phase_map) {
+  NodeParams p;
+  memset(&p, 0, sizeof(p));
+  p.N = N;
+  p.s_max = opt->NA / opt->n_i;
+  p.inv_lambda = 1.0 / opt->lambda;
+  p.n_i = opt->n_i;
+  p.gl = gl_layers(opt, opt->depth);
+  p.apodize = opt->apodize;
+  p.s_env = opt->s_env;
+  for (int i = 0; i < 4; ++i) p.pol[i] = opt->pol[i];
+  p.zp = zernike_poly(zern, n_zern);
+  p.phase_map = phase_map;
+  return p;
+}
+
+}  // namespace psf
+
+using namespace psf;
+
+extern "C" {
+
+int psf_version(void) { return 100; }
+
+const char* psf_last_error(void) { return g_err; }
+
+int psf_workspace_status(const void* workspace, void* stream) {
+  if (!workspace) return fail(PSF_ERR_ARG, "workspace is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check("stream sync");
+  int st = 0;
+  if (cudaMemcpy(&st, workspace, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_check("status read");
+  return st;
+}
+
+size_t psf_fourier_workspace_size(const psf_optics* opt, int n_pupil,
+                                  const psf_grid* grid, int precision) {
+  if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
+  return fourier_layout(nullptr, n_pupil, grid, precision).bytes;
+}
+
+int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
+                          const psf_grid* grid, const double* zernike,
+                          int n_zern, const float* phase_map, int precision,
+                          float* intensity, void* fields, void* workspace,
+                          size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int r = check_fourier_args(opt, n_pupil, grid, precision);
+  if (r) return r;
+  if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
+  if (n_zern > 0 && !zernike) return fail(PSF_ERR_ARG, "zernike is NULL");
+  for (int j = 0; j < n_zern; ++j)
+    if (!isfinite(zernike[j])) return fail(PSF_ERR_ARG, "zernike[%d] not finite", j);
+  if (!intensity) return fail(PSF_ERR_ARG, "intensity is NULL");
+  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
+  const int N = n_pupil;
+  FourierLayout L = fourier_layout(workspace, N, grid, precision);
+  if (ws_bytes < L.bytes)
+    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  std::vector<float2> zz(grid->nz);
+  for (int i = 0; i < grid->nz; ++i) {
+    const f2x v = split_double(grid->z[i]);
+    zz[i] = make_float2(v.hi, v.lo);
+  }
+  cudaMemsetAsync(workspace, 0, sizeof(int), s);
+  cudaMemcpyAsync(L.zz, zz.data(), zz.size() * sizeof(float2),
+                  cudaMemcpyHostToDevice, s);
+  if ((r = cuda_check("workspace init"))) return r;
+
+  NodeParams np = node_params(opt, N, zernike, n_zern, phase_map);
+  {
+    TimingScope ts(kTimeSetup, s);
+    launch_node_table(np, L.nodes, s);
+  }
+  const double f = opt->NA / opt->lambda;   // k s_max / (2 pi)
+  const double ds = 2.0 * (opt->NA / opt->n_i) / N;
+  const float scale = (float)(ds * ds / (2.0 * kPi));
+  if (precision == PSF_PREC_FP32) {
+    {
+      TimingScope ts(kTimeSetup, s);
+      launch_twiddle(N, grid->nx, grid->dx, f, L.Ax, s);
+    }
+    {
+      TimingScope ts(kTimeSetup, s);
+      launch_twiddle(N, grid->ny, grid->dy, f, L.Ay, s);
+    }
+    for (int z0 = 0; z0 < grid->nz; z0 += L.zc) {
+      const int nzc = grid->nz - z0 < L.zc ? grid->nz - z0 : L.zc;
+      {
+        TimingScope ts(kTimePupil, s);
+        launch_pupil_z_f32(L.nodes, N, L.zz, z0, nzc, L.P, s);
+      }
+      {
+        TimingScope ts(kTimeStage1, s);
+        launch_stage1_f32(L.Ay, L.P, L.U, N, grid->ny, nzc, s);
+      }
+      float2* fz = fields ? (float2*)fields + (size_t)z0 * 3 * grid->nx * grid->ny : nullptr;
+      {
+        TimingScope ts(kTimeStage2, s);
+        launch_stage2_f32(L.Ax, L.U, intensity + (size_t)z0 * grid->nx * grid->ny,
+                          fz, N, grid->nx, grid->ny, nzc, scale, s);
+      }
+    }
+  } else {
+    r = tc_fourier_forward(L.tc, L.nodes, L.zz, N, grid->nx, grid->ny, grid->dx,
+                           grid->dy, grid->nz, L.zc, f, scale, precision,
+                           intensity, (float2*)fields, (int*)workspace, s);
+    if (r) return fail(r, "split-precision launch failed");
+  }
+  return cuda_check("psf_fourier_vectorial launch");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Backward (adjoint of Eq. 8), FP32 contractions, per-z recomputation.
+// ---------------------------------------------------------------------------
+struct BackwardLayout {
+  NodeTable nodes;
+  float2* zz;
+  float2 *Ax, *Ay, *AxH, *AyH;
+  float2 *P, *U, *RT, *V, *Gh;
+  float* gW;
+  float* loss_part;
+  int zc, n_part;
+  size_t bytes;
+};
+
+static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g) {
+  BackwardLayout L;
+  memset(&L, 0, sizeof(L));
+  Carver c(ws);
+  const size_t NN = (size_t)N * N;
+  L.nodes.amp = c.take<float>(6 * NN);
+  L.nodes.wfr = c.take<float>(NN);
+  L.nodes.kh = c.take<float>(NN);
+  L.nodes.kl = c.take<float>(NN);
+  L.zz = c.take<float2>(g->nz);
+  // per-z: P, Gh [3][N][N], U [3][ny][N], RT [3][ny][nx], V [3][N][ny]
+  const double per_z = 3.0 * 8.0 * (2.0 * NN + 2.0 * g->ny * N + (double)g->ny * g->nx);
+  int zc = (int)(96.0 * 1048576.0 / per_z);
+  zc = zc < 1 ? 1 : (zc > 32 ? 32 : zc);
+  if (zc > g->nz) zc = g->nz;
+  L.zc = zc;
+  L.Ax = c.take<float2>((size_t)g->nx * N);
+  L.Ay = c.take<float2>((size_t)g->ny * N);
+  L.AxH = c.take<float2>((size_t)g->nx * N);
+  L.AyH = c.take<float2>((size_t)g->ny * N);
+  L.P = c.take<float2>((size_t)zc * 3 * NN);
+  L.Gh = c.take<float2>((size_t)zc * 3 * NN);
+  L.U = c.take<float2>((size_t)zc * 3 * g->ny * N);
+  L.RT = c.take<float2>((size_t)zc * 3 * g->ny * g->nx);
+  L.V = c.take<float2>((size_t)zc * 3 * N * g->ny);
+  L.gW = c.take<float>(NN);
+  L.n_part = g->nz * stage2_tiles(g->nx, g->ny);
+  L.loss_part = c.take<float>((size_t)L.n_part);
+  L.bytes = align_up(c.off, 256);
+  return L;
+}
+
+static ZernBasis zernike_basis(int n_zern) {
+  ZernBasis zb;
+  memset(&zb, 0, sizeof(zb));
+  zb.n_zern = n_zern;
+  for (int j = 1; j <= n_zern; ++j) {
+    int n, m;
+    noll_nm(j, &n, &m);
+    zb.m[j - 1] = m;
+    zernike_radial_coeffs(n, m < 0 ? -m : m, zb.rc[j - 1]);
+  }
+  return zb;
+}
+
+extern "C" size_t psf_fourier_backward_workspace_size(const psf_optics* opt,
+                                                       int n_pupil,
+                                                       const psf_grid* grid,
+                                                       int precision) {
+  if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
+  if (precision != PSF_PREC_FP32) return 0;
+  return backward_layout(nullptr, n_pupil, grid).bytes;
+}
+
+extern "C" int psf_fourier_vectorial_backward(
+    const psf_optics* opt, int n_pupil, const psf_grid* grid, int batch,
+    const double* zernike, int n_zern, const float* phase_map, int precision,
+    const float* target, const float* grad_intensity, float* loss,
+    float* grad_phase_map, float* grad_zernike, void* workspace,
+    size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int r = check_fourier_args(opt, n_pupil, grid, precision);
+  if (r) return r;
+  if (precision != PSF_PREC_FP32)
+    return fail(PSF_ERR_PRECISION, "backward supports PSF_PREC_FP32");
+  if (batch < 1) return fail(PSF_ERR_ARG, "batch must be >= 1");
+  if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
+  if (n_zern > 0 && !zernike) return fail(PSF_ERR_ARG, "zernike is NULL");
+  for (long long j = 0; j < (long long)batch * n_zern; ++j)
+    if (!isfinite(zernike[j])) return fail(PSF_ERR_ARG, "zernike[%lld] not finite", j);
+  if (!target && !grad_intensity)
+    return fail(PSF_ERR_ARG, "one of target / grad_intensity is required");
+  if (loss && !target) return fail(PSF_ERR_ARG, "loss needs a target");
+  if (!grad_phase_map && !grad_zernike && !loss)
+    return fail(PSF_ERR_ARG, "no output requested");
+  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
+  const int N = n_pupil;
+  BackwardLayout L = backward_layout(workspace, N, grid);
+  if (ws_bytes < L.bytes)
+    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  const size_t NN = (size_t)N * N, vox = (size_t)nz * nx * ny;
+
+  std::vector<float2> zz(nz);
+  for (int i = 0; i < nz; ++i) {
+    const f2x v = split_double(grid->z[i]);
+    zz[i] = make_float2(v.hi, v.lo);
+  }
+  cudaMemsetAsync(workspace, 0, sizeof(int), s);
+  cudaMemcpyAsync(L.zz, zz.data(), zz.size() * sizeof(float2),
+                  cudaMemcpyHostToDevice, s);
+  const double f = opt->NA / opt->lambda;
+  const double ds = 2.0 * (opt->NA / opt->n_i) / N;
+  const float scale = (float)(ds * ds / (2.0 * kPi));
+  launch_twiddle(N, nx, grid->dx, f, L.Ax, s);
+  launch_twiddle(N, ny, grid->dy, f, L.Ay, s);
+  launch_twiddle_adj(N, nx, grid->dx, f, L.AxH, s);
+  launch_twiddle_adj(N, ny, grid->dy, f, L.AyH, s);
+  const ZernBasis zb = zernike_basis(n_zern);
+  const int tiles = stage2_tiles(nx, ny);
+
+  for (int b = 0; b < batch; ++b) {
+    NodeParams np = node_params(opt, N, zernike ? zernike + (size_t)b * n_zern : nullptr,
+                                n_zern, phase_map ? phase_map + (size_t)b * NN : nullptr);
+    launch_node_table(np, L.nodes, s);
+    cudaMemsetAsync(L.gW, 0, NN * sizeof(float), s);
+    const float* Tb = target ? target + (size_t)b * vox : nullptr;
+    const float* Gb = grad_intensity ? grad_intensity + (size_t)b * vox : nullptr;
+    for (int z0 = 0; z0 < nz; z0 += L.zc) {
+      const int nzc = nz - z0 < L.zc ? nz - z0 : L.zc;
+      const size_t zoff = (size_t)z0 * nx * ny;
+      launch_pupil_z_f32(L.nodes, N, L.zz, z0, nzc, L.P, s);
+      launch_stage1_f32(L.Ay, L.P, L.U, N, ny, nzc, s);
+      TimingScope ts(kTimeAdjoint, s);
+      launch_stage2_adjsrc_f32(L.Ax, L.U, Tb ? Tb + zoff : nullptr,
+                               Gb ? Gb + zoff : nullptr, L.RT,
+                               L.loss_part + (size_t)z0 * tiles, N, nx, ny, nzc,
+                               scale, s);
+      // V[p][b] = sum_a conj(Ax[a][p]) R[a][b]    (M = N, N = ny, K = nx)
+      launch_cgemm_nt_f32(L.AxH, 0, L.RT, (long long)ny * nx, L.V,
+                          (long long)N * ny, N, ny, nx, nzc * 3, s);
+      // Gh[p][q] = sum_b V[p][b] conj(Ay[b][q])   (M = N, N = N, K = ny)
+      launch_cgemm_nt_f32(L.V, (long long)N * ny, L.AyH, 0, L.Gh, (long long)NN,
+                          N, N, ny, nzc * 3, s);
+      launch_grad_accum(L.Gh, L.P, L.gW, (int)NN, nzc, s);
+    }
+    if (loss) launch_sum_partials(L.loss_part, L.n_part, loss + b, s);
+    if (grad_phase_map)
+      cudaMemcpyAsync(grad_phase_map + (size_t)b * NN, L.gW, NN * sizeof(float),
+                      cudaMemcpyDeviceToDevice, s);
+    if (grad_zernike) launch_zernike_grad(zb, N, L.gW, grad_zernike + (size_t)b * n_zern, s);
+  }
+  return cuda_check("psf_fourier_vectorial_backward launch");
+}
+
+// ===========================================================================
+// Bessel strategy
+// ===========================================================================
+struct BesselLayout {
+  double* theta_tab;     // 10 x n_theta + kMaxM0 x n_theta doubles
+  float* kappa;          // 2 x n_theta floats
+  float* Bt;
+  EmitterTable et;
+  int* slice_em;
+  float2* zz;
+  float2* prof;
+  int* pix_i0;
+  float* pix_f;
+  float* pix_g;
+  size_t bytes;
+};
+
+static BesselLayout bessel_layout(void* ws, int n_em, int n_slices, int n_theta,
+                                  int n_r, int nx, int ny, bool own_profiles) {
+  BesselLayout L;
+  memset(&L, 0, sizeof(L));
+  Carver c(ws);
+  L.theta_tab = c.take<double>((size_t)(10 + kMaxM0) * n_theta);
+  L.kappa = c.take<float>(2 * (size_t)n_theta);
+  L.Bt = c.take<float>((size_t)3 * n_r * n_theta);
+  L.et.amp = c.take<float>((size_t)n_em * n_theta);
+  L.et.wfr = c.take<float>((size_t)n_em * n_theta);
+  L.et.valid = c.take<int>(n_em);
+  L.slice_em = c.take<int>(n_slices);
+  L.zz = c.take<float2>(n_slices);
+  if (own_profiles) L.prof = c.take<float2>((size_t)n_slices * 3 * n_r);
+  L.pix_i0 = c.take<int>((size_t)nx * ny);
+  L.pix_f = c.take<float>((size_t)nx * ny);
+  L.pix_g = c.take<float>((size_t)nx * ny);
+  L.bytes = align_up(c.off, 256);
+  return L;
+}
+
+static int check_bessel_args(const psf_optics* base, int n_em, int n_slices,
+                             int n_theta, int n_r, int nx, int ny, int precision) {
+  int r = check_optics(base);
+  if (r) return r;
+  if (n_em < 1) return fail(PSF_ERR_ARG, "n_emitters must be >= 1");
+  if (n_slices < 0) return fail(PSF_ERR_ARG, "n_slices must be >= 0");
+  if (n_theta < 2 || n_theta > 880) return fail(PSF_ERR_ARG, "n_theta %d outside [2, 880]", n_theta);
+  if (n_r < 2 || n_r > 4096) return fail(PSF_ERR_ARG, "n_r %d outside [2, 4096]", n_r);
+  if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384)
+    return fail(PSF_ERR_ARG, "nx, ny must be in [1, 16384]");
+  if (precision != PSF_PREC_FP32)
+    return fail(PSF_ERR_PRECISION, "Bessel path supports PSF_PREC_FP32 only");
+  return PSF_OK;
+}
+
+extern "C" size_t psf_bessel_workspace_size(const psf_optics* base, int n_em,
+                                            int n_slices, int n_theta, int n_r,
+                                            int nx, int ny, int precision) {
+  if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
+  return bessel_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, true).bytes;
+}
+
+extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
+                                    const double* depth, const double* zernike,
+                                    int n_zern, const int* z_offsets,
+                                    const double* z, int n_slices, int n_theta,
+                                    int n_r, int nx, int ny, double dx,
+                                    double dy, int precision, float* intensity,
+                                    void* profiles, void* workspace,
+                                    size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int r = check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision);
+  if (r) return r;
+  if (!finite_pos(dx) || !finite_pos(dy)) return fail(PSF_ERR_ARG, "pixel pitch must be > 0");
+  if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
+  if (!depth || !z_offsets || (n_slices > 0 && !z) || (n_zern > 0 && !zernike))
+    return fail(PSF_ERR_ARG, "depth / z_offsets / z / zernike pointer is NULL");
+  if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");
+  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
+  BesselLayout L = bessel_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
+                                 profiles == nullptr);
+  if (ws_bytes < L.bytes)
+    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
+  if (profiles) L.prof = (float2*)profiles;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // Per-theta FP64 table: GL nodes on [0, theta_max]; W_GL affine in t_s.
+  const double s_max = base->NA / base->n_i;
+  const double th_max = asin(s_max);
+  std::vector<double> gx, gw;
+  gauss_legendre(n_theta, gx, gw);
+  std::vector<double> tab((size_t)(10 + kMaxM0) * n_theta, 0.0);
+  std::vector<float> kap(2 * (size_t)n_theta);
+  double* T_th = tab.data();
+  double* T_w = T_th + n_theta;
+  double* T_s = T_w + n_theta;
+  double* T_c = T_s + n_theta;
+  double* T_are = T_c + n_theta;
+  double* T_aim = T_are + n_theta;
+  double* T_bre = T_aim + n_theta;
+  double* T_bim = T_bre + n_theta;
+  double* T_amp = T_bim + n_theta;
+  double* T_zm0 = T_amp + 2 * n_theta;   // slot 9 unused (alignment)
+  const GLLayers L0 = gl_layers(base, 0.0), L1 = gl_layers(base, 1.0);
+  BesselParams bp;
+  memset(&bp, 0, sizeof(bp));
+  int m0_j[kMaxM0], n_m0 = 0;
+  unsigned long long mask[2] = {0, 0};
+  for (int j = 1; j <= n_zern; ++j) {
+    int n, m;
+    noll_nm(j, &n, &m);
+    if (m == 0) {
+      if (n_m0 < kMaxM0) m0_j[n_m0++] = j;
+    } else {
+      mask[(j - 1) >> 6] |= 1ULL << ((j - 1) & 63);
+    }
+  }
+  for (int j = 0; j < n_theta; ++j) {
+    const double th = 0.5 * th_max * (gx[j] + 1.0);
+    const double st = sin(th), ct = cos(th);
+    T_th[j] = th;
+    T_w[j] = 0.5 * th_max * gw[j];
+    T_s[j] = st;
+    T_c[j] = ct;
+    // W/(2 pi) = sum_l t_l(t_s) sqrt(n_l^2 - n_i^2 s^2)/lambda, t_l affine in t_s
+    double a_re = 0, a_im = 0, b_re = 0, b_im = 0;
+    for (int l = 0; l < 5; ++l) {
+      const double arg = L0.n_idx[l] * L0.n_idx[l] - (base->n_i * st) * (base->n_i * st);
+      const double root = sqrt(fabs(arg)) / base->lambda;
+      const double tb = L0.t[l], ta = L1.t[l] - L0.t[l];
+      if (arg >= 0) {
+        a_re += ta * root;
+        b_re += tb * root;
+      } else {
+        a_im += ta * root;
+        b_im += tb * root;
+      }
+    }
+    T_are[j] = a_re;
+    T_aim[j] = a_im;
+    T_bre[j] = b_re;
+    T_bim[j] = b_im;
+    double amp = base->apodize ? sqrt(ct) : 1.0;
+    if (base->s_env > 0) amp *= exp(-(st * st) / (base->s_env * base->s_env));
+    T_amp[j] = amp;
+    const double rho = st / s_max;
+    for (int q = 0; q < n_m0; ++q) {
+      int n, m;
+      noll_nm(m0_j[q], &n, &m);
+      double rc[kZernMaxOrder + 1];
+      zernike_radial_coeffs(n, 0, rc);
+      double v = 0;
+      for (int k = kZernMaxOrder; k >= 0; --k) v = v * rho + rc[k];
+      T_zm0[(size_t)q * n_theta + j] = v;
+    }
+    const f2x kv = split_double(base->n_i * ct / base->lambda);
+    kap[j] = kv.hi;
+    kap[n_theta + j] = kv.lo;
+  }
+  ThetaTable tt;
+  tt.theta = L.theta_tab;
+  tt.w = L.theta_tab + n_theta;
+  tt.sin_t = tt.w + n_theta;
+  tt.cos_t = tt.sin_t + n_theta;
+  tt.a_re = tt.cos_t + n_theta;
+  tt.a_im = tt.a_re + n_theta;
+  tt.b_re = tt.a_im + n_theta;
+  tt.b_im = tt.b_re + n_theta;
+  tt.amp0 = tt.b_im + n_theta;
+  tt.zm0 = tt.amp0 + 2 * n_theta;
+  tt.kh = L.kappa;
+  tt.kl = L.kappa + n_theta;
+
+  bp.n_theta = n_theta;
+  bp.n_r = n_r;
+  bp.nx = nx;
+  bp.ny = ny;
+  bp.n_em = n_em;
+  bp.n_slices = n_slices;
+  bp.n_zern = n_zern;
+  bp.k = 2.0 * kPi * base->n_i / base->lambda;
+  bp.r_max = sqrt(0.25 * (nx - 1) * (nx - 1) * dx * dx + 0.25 * (ny - 1) * (ny - 1) * dy * dy);
+  bp.dr = bp.r_max > 0 ? bp.r_max / (n_r - 1) : 1.0;
+  bp.dx = dx;
+  bp.dy = dy;
+  bp.n_m0 = n_m0;
+  for (int q = 0; q < n_m0; ++q) bp.m0_j[q] = m0_j[q];
+  bp.nonaxis_mask[0] = mask[0];
+  bp.nonaxis_mask[1] = mask[1];
+  bp.project = (base->flags & PSF_PROJECT_AXISYMMETRIC) ? 1 : 0;
+  for (int i = 0; i < 4; ++i) bp.pol[i] = base->pol[i];
+
+  cudaMemsetAsync(workspace, 0, sizeof(int), s);
+  cudaMemcpyAsync(L.theta_tab, tab.data(), tab.size() * sizeof(double),
+                  cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(L.kappa, kap.data(), kap.size() * sizeof(float),
+                  cudaMemcpyHostToDevice, s);
+  if ((r = cuda_check("workspace init"))) return r;
+
+  {
+    TimingScope ts(kTimeSetup, s);
+    launch_bessel_jmat(bp, tt, L.Bt, s);
+  }
+  {
+    TimingScope ts(kTimeSetup, s);
+    launch_bessel_emitters(bp, tt, depth, n_zern > 0 ? zernike : nullptr, L.et,
+                           (int*)workspace, s);
+  }
+  if (n_slices > 0) {
+    // slices no emitter claims keep emitter -1 and are skipped
+    cudaMemsetAsync(L.slice_em, 0xFF, (size_t)n_slices * sizeof(int), s);
+    {
+      TimingScope ts(kTimeSetup, s);
+      launch_slice_map(bp, z_offsets, z, L.slice_em, L.zz, (int*)workspace, s);
+    }
+    {
+      TimingScope ts(kTimeSetup, s);
+      launch_pixel_table(bp, L.pix_i0, L.pix_f, L.pix_g, s);
+    }
+    {
+      TimingScope ts(kTimeBesselRadial, s);
+      launch_bessel_profiles_f32(bp, tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
+    }
+    {
+      TimingScope ts(kTimeBesselEpilogue, s);
+      launch_bessel_intensity(bp, L.prof, L.slice_em, L.et.valid, L.pix_i0,
+                              L.pix_f, L.pix_g, intensity, s);
+    }
+  }
+  return cuda_check("psf_bessel_vectorial launch");
+}

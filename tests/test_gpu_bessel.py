@@ -1,0 +1,88 @@
+"""Bessel strategy on the GPU (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bessel as ob
+from paper_2502_03170_gb300 import _lib, api
+from paper_2502_03170_gb300 import workloads as W
+
+from .gpu_helpers import max_rel, oracle_optics
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def small_batch(seed=7, nz=(3, 1, 4, 2, 5), with_m_nonzero=True):
+    g = np.random.default_rng(seed)
+    n_em = len(nz)
+    depth = g.uniform(0.0, 5.0, n_em)
+    zern = np.zeros((n_em, 21))
+    zern[:, 3] = g.normal(0, 0.2, n_em)
+    zern[:, 10] = g.normal(0, 0.1, n_em)
+    if with_m_nonzero:
+        zern[:, 5] = g.normal(0, 0.1, n_em)
+    offs = np.zeros(n_em + 1, dtype=np.int32)
+    offs[1:] = np.cumsum(nz)
+    z = np.concatenate([np.sort(g.uniform(-1.2, 1.2, n)) for n in nz])
+    return depth, zern, offs, z
+
+
+def per_stack_max_rel(I, Ir, offs):
+    return max(max_rel(I[a:b], Ir[a:b]) for a, b in zip(offs[:-1], offs[1:]) if b > a)
+
+
+@pytest.mark.parametrize("pol", [W.CIRCULAR, (1.0, 0.0), (0.6, 0.48 + 0.64j)])
+def test_small_batch_parity(lib, pol):
+    d = dict(W.optics_gibson_lanni(0.0), pol=pol)
+    depth, zern, offs, z = small_batch()
+    nt, nr, nx, ny, dx, dy = 64, 48, 20, 17, 0.03, 0.025
+    I, P = api.bessel(d, depth, zern, offs, z, nt, nr, nx, ny, dx, dy,
+                      project=True, profiles=True)
+    torch.cuda.synchronize()
+    I, P = I.cpu().numpy(), P.cpu().numpy()
+    opt = oracle_optics(d)
+    Ir = ob.psf_bessel_batch(opt, depth, zern, offs, z, nt, nr, nx, ny, dx, dy,
+                             project=True)
+    Pr = ob.profiles_batch(opt, depth, zern, offs, z, nt, nr, nx, ny, dx, dy,
+                           project=True)
+    assert per_stack_max_rel(I, Ir, offs) <= TOL
+    assert max_rel(P, Pr) <= TOL
+
+
+def test_not_axisymmetric_status(lib):
+    d = W.optics_gibson_lanni(0.0)
+    depth, zern, offs, z = small_batch()
+    zern[:, 5] = 0.0
+    zern[2, 5] = 0.1                      # emitter 2 has an m != 0 term
+    ws = api.Workspace()
+    I = api.bessel(d, depth, zern, offs, z, 32, 32, 8, 8, 0.03, 0.03,
+                   project=False, workspace=ws)
+    assert ws.status() == _lib.PSF_ERR_NOT_AXISYMMETRIC
+    I2 = api.bessel(d, depth, zern, offs, z, 32, 32, 8, 8, 0.03, 0.03,
+                    project=True, workspace=ws)
+    assert ws.status() == _lib.PSF_OK
+    I, I2 = I.cpu().numpy(), I2.cpu().numpy()
+    for e in (0, 1, 3, 4):
+        a, b = offs[e], offs[e + 1]
+        assert np.array_equal(I[a:b], I2[a:b])
+
+
+def test_bessel_config_full_size_sampled(lib):
+    """The batched workload (4096 emitters, uneven stacks, 200 theta nodes,
+    256 radii, 128^2 px) in one call; sampled emitters recomputed by the
+    oracle."""
+    c = W.bessel()
+    I = api.bessel(c["optics"], c["depth"], c["zernike"], c["z_offsets"], c["z"],
+                   c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"],
+                   project=True)
+    torch.cuda.synchronize()
+    opt = oracle_optics(c["optics"])
+    offs = c["z_offsets"]
+    for e in (0, 1733, 4095):
+        a, b = int(offs[e]), int(offs[e + 1])
+        Ie = I[a:b].cpu().numpy()
+        Ir = ob.psf_bessel_batch(opt, c["depth"], c["zernike"], offs, c["z"],
+                                 c["n_theta"], c["n_r"], c["nx"], c["ny"],
+                                 c["dx"], c["dy"], project=True, emitters=[e])
+        assert max_rel(Ie, Ir) <= TOL, e

@@ -1,0 +1,94 @@
+"""Host-side checks of libpsf (no GPU needed): the library builds for sm_103a,
+loads, exports every function include/psf.h declares, and rejects bad
+arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from paper_2502_03170_gb300 import _lib, api
+from paper_2502_03170_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(psf_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def cpu_lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2502_03170_gb300 import build
+    build.build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(cpu_lib):
+    names = declared_functions()
+    assert "psf_fourier_vectorial" in names and "psf_bessel_vectorial" in names
+    for n in sorted(names):
+        assert hasattr(cpu_lib, n), n
+    assert set(_lib.PROTOTYPES) == names
+    assert cpu_lib.psf_version() >= 100
+
+
+def test_host_validation(cpu_lib):
+    o = api.make_optics(W.optics_plain())
+    g = api.Grid(dict(nx=8, ny=8, dx=0.02, dy=0.02, z=[0.0, 0.1]))
+    size = cpu_lib.psf_fourier_workspace_size(ctypes.byref(o), 16,
+                                              ctypes.byref(g.c), 0)
+    assert size > 0
+    bad = api.make_optics(dict(W.optics_plain(), NA=1.6))
+    assert cpu_lib.psf_fourier_workspace_size(ctypes.byref(bad), 16,
+                                              ctypes.byref(g.c), 0) == 0
+    # NA >= n_i is rejected before any launch
+    r = cpu_lib.psf_fourier_vectorial(ctypes.byref(bad), 16, ctypes.byref(g.c),
+                                      None, 0, None, 0, ctypes.c_void_p(16),
+                                      None, ctypes.c_void_p(256), 1 << 30, None)
+    assert r == _lib.PSF_ERR_ARG
+    assert b"NA" in cpu_lib.psf_last_error()
+    # missing intensity, too-small workspace, unknown precision
+    assert cpu_lib.psf_fourier_vectorial(ctypes.byref(o), 16, ctypes.byref(g.c),
+                                         None, 0, None, 0, None, None,
+                                         ctypes.c_void_p(256), 1 << 30,
+                                         None) == _lib.PSF_ERR_ARG
+    assert cpu_lib.psf_fourier_vectorial(ctypes.byref(o), 16, ctypes.byref(g.c),
+                                         None, 0, None, 0, ctypes.c_void_p(16),
+                                         None, ctypes.c_void_p(256), 64,
+                                         None) == _lib.PSF_ERR_WORKSPACE
+    assert cpu_lib.psf_fourier_vectorial(ctypes.byref(o), 16, ctypes.byref(g.c),
+                                         None, 0, None, 7, ctypes.c_void_p(16),
+                                         None, ctypes.c_void_p(256), 1 << 30,
+                                         None) == _lib.PSF_ERR_PRECISION
+    zbad = np.zeros(67)
+    assert cpu_lib.psf_fourier_vectorial(
+        ctypes.byref(o), 16, ctypes.byref(g.c), zbad.ctypes.data_as(ctypes.c_void_p),
+        67, None, 0, ctypes.c_void_p(16), None, ctypes.c_void_p(256), 1 << 30,
+        None) == _lib.PSF_ERR_ARG
+    # Bessel: n_theta out of range, non-FP32 precision
+    assert cpu_lib.psf_bessel_workspace_size(ctypes.byref(o), 4, 16, 1, 64, 8,
+                                             8, 0) == 0
+    assert cpu_lib.psf_bessel_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
+                                             8, 8, 0) > 0
+    r = cpu_lib.psf_bessel_vectorial(ctypes.byref(o), 4, None, None, 0, None,
+                                     None, 16, 64, 64, 8, 8, 0.02, 0.02, 0,
+                                     ctypes.c_void_p(16), None,
+                                     ctypes.c_void_p(256), 1 << 30, None)
+    assert r == _lib.PSF_ERR_ARG
+    # backward: needs a target or an upstream gradient
+    r = cpu_lib.psf_fourier_vectorial_backward(
+        ctypes.byref(o), 16, ctypes.byref(g.c), 1, None, 0, None, 0, None,
+        None, None, ctypes.c_void_p(16), None, ctypes.c_void_p(256), 1 << 30,
+        None)
+    assert r == _lib.PSF_ERR_ARG
