@@ -109,7 +109,8 @@ def radial_grid(n_r, nx, ny, dx, dy):
 def interpolate(prof, r_max, rho):
     """Linear interpolation of complex profiles [..., n_r] at radii rho."""
     n_r = prof.shape[-1]
-    t = rho * ((n_r - 1) / r_max)
+    # r_max = 0 (a single pixel on the axis): every r_i is 0, use cell 0
+    t = rho * ((n_r - 1) / r_max) if r_max > 0 else np.zeros_like(rho)
     i0 = np.clip(np.floor(t).astype(np.int64), 0, n_r - 2)
     f = t - i0
     return prof[..., i0] * (1.0 - f) + prof[..., i0 + 1] * f

@@ -27,7 +27,8 @@ __global__ void k_bessel_jmat(BesselParams p, ThetaTable t, float* Bt) {
     jn_v = j1(x);
     g = st * st;
   } else {
-    jn_v = jn(2, x);
+    // J_2(0) = 0 exactly (the library routine is not used at x = 0)
+    jn_v = x > 0.0 ? jn(2, x) : 0.0;
     g = st * (ct - 1.0);
   }
   Bt[idx] = (float)(t.w[j] * g * jn_v);
@@ -128,7 +129,7 @@ __global__ void k_pixel_table(BesselParams p, int* i0, float* f, float* g) {
   const double x = (a - 0.5 * (p.nx - 1)) * p.dx;
   const double y = (b - 0.5 * (p.ny - 1)) * p.dy;
   const double rho = sqrt(x * x + y * y);
-  const double tt = rho / p.dr;
+  const double tt = p.dr > 0 ? rho / p.dr : 0.0;   // r_max = 0: all r_i = 0
   int c = (int)floor(tt);
   c = c < 0 ? 0 : (c > p.n_r - 2 ? p.n_r - 2 : c);
   i0[idx] = c;

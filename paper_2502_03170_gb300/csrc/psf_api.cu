@@ -28,6 +28,9 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Sets the thread's last-error message (for entry points in other files).
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 static int cuda_check(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
@@ -693,7 +696,7 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   bp.n_zern = n_zern;
   bp.k = 2.0 * kPi * base->n_i / base->lambda;
   bp.r_max = sqrt(0.25 * (nx - 1) * (nx - 1) * dx * dx + 0.25 * (ny - 1) * (ny - 1) * dy * dy);
-  bp.dr = bp.r_max > 0 ? bp.r_max / (n_r - 1) : 1.0;
+  bp.dr = bp.r_max / (n_r - 1);
   bp.dx = dx;
   bp.dy = dy;
   bp.n_m0 = n_m0;

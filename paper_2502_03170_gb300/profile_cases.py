@@ -1,0 +1,52 @@
+"""Small, self-contained invocations of single hot kernels for profiling.
+
+    python -m paper_2502_03170_gb300.profile_cases <case> [--precision P]
+
+Each case runs one warm-up call and one measured call of the library on
+cuda:0 with sizes small enough for a full ncu capture (well under a few GB on
+the device), then exits.  Cases:
+
+* ``fourier``  - 256^2 pupil, 512^2 px at 10 nm, 16 planes, Gibson-Lanni +
+  Zernike (one z-chunk of the benchmark stack).
+* ``bessel``   - 256 emitters of the batched Bessel workload (about 600 MB
+  of output, above the 126 MB L2).
+"""
+import argparse
+
+import numpy as np
+import torch
+
+from . import _lib, api
+from . import workloads as W
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["fourier", "bessel"])
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--nz", type=int, default=16)
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    if args.case == "fourier":
+        c = W.fourier(nz=args.nz)
+        g = api.Grid(c["grid"])
+        ws = api.Workspace()
+        out = torch.empty((g.c.nz, g.c.nx, g.c.ny), device="cuda")
+        for _ in range(2):
+            api.fourier(c["optics"], c["n_pupil"], g, zernike=c["zernike"],
+                        precision=args.precision, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all()
+    else:
+        c = W.bessel(n_emitters=256)
+        for _ in range(2):
+            I = api.bessel(c["optics"], c["depth"], c["zernike"], c["z_offsets"],
+                           c["z"], c["n_theta"], c["n_r"], c["nx"], c["ny"],
+                           c["dx"], c["dy"], project=True)
+        torch.cuda.synchronize()
+        assert torch.isfinite(I).all()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main()

@@ -50,6 +50,26 @@ def test_small_batch_parity(lib, pol):
     assert max_rel(P, Pr) <= TOL
 
 
+@pytest.mark.parametrize("nx,ny,nr", [(21, 15, 32), (1, 1, 2), (9, 40, 300)])
+def test_odd_grids_and_centre_pixel(lib, nx, ny, nr):
+    """Odd grids put a pixel on the axis (r = 0, J_1 = J_2 = 0) and make the
+    interpolation use the first radial cell; n_r = 2 is the smallest grid."""
+    d = dict(W.optics_gibson_lanni(0.0), pol=(0.6, 0.48 + 0.64j))
+    depth, zern, offs, z = small_batch(seed=3, nz=(2, 3))
+    I, P = api.bessel(d, depth, zern, offs, z, 40, nr, nx, ny, 0.021, 0.019,
+                      project=True, profiles=True)
+    torch.cuda.synchronize()
+    I, P = I.cpu().numpy(), P.cpu().numpy()
+    assert np.all(np.isfinite(P))
+    opt = oracle_optics(d)
+    Ir = ob.psf_bessel_batch(opt, depth, zern, offs, z, 40, nr, nx, ny, 0.021,
+                             0.019, project=True)
+    Pr = ob.profiles_batch(opt, depth, zern, offs, z, 40, nr, nx, ny, 0.021,
+                           0.019, project=True)
+    assert per_stack_max_rel(I, Ir, offs) <= TOL
+    assert max_rel(P, Pr) <= TOL
+
+
 def test_not_axisymmetric_status(lib):
     d = W.optics_gibson_lanni(0.0)
     depth, zern, offs, z = small_batch()
