@@ -130,6 +130,37 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
                           float* intensity, void* fields, void* workspace,
                           size_t ws_bytes, void* stream);
 
+/* Fixed size of the library-owned scratch array used by
+ * psf_fourier_vectorial_noalloc() (24 MiB). */
+#define PSF_NOALLOC_SCRATCH_BYTES (24u << 20)
+
+/* psf_fourier_vectorial() for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment convenience.
+ *
+ * Some callers cannot hand the library a workspace: their host application
+ * owns all device memory through its own allocator (a framework's caching
+ * allocator, an imaging application that gives plug-ins a fixed budget), or
+ * they run latency-critical loops in which cudaMalloc, which can synchronise
+ * the device, is not allowed.  This entry point allocates nothing: it uses a
+ * file-scope device array of PSF_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library keeps until the process exits.  The caller still owns
+ * and passes the inputs and outputs (same meaning as in
+ * psf_fourier_vectorial(); contractions in PSF_PREC_FP32).
+ *   - Sizes whose workspace would exceed the array are rejected with
+ *     PSF_ERR_WORKSPACE and a message giving both sizes; nothing is launched.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the previous call's
+ *     contents; every call rewrites what it reads.  Calls whose executions
+ *     overlap on the GPU (other streams, other host threads) race on the
+ *     array and give undefined results: serialise them.
+ *   - Device-side status (psf_workspace_status) is not available here. */
+int psf_fourier_vectorial_noalloc(const psf_optics* opt, int n_pupil,
+                                  const psf_grid* grid, const double* zernike,
+                                  int n_zern, const float* phase_map,
+                                  float* intensity, void* fields, void* stream);
+
 /* Workspace for psf_fourier_vectorial_backward(). */
 size_t psf_fourier_backward_workspace_size(const psf_optics* opt, int n_pupil,
                                            const psf_grid* grid, int precision);

@@ -1,0 +1,83 @@
+// psf_fourier_vectorial_noalloc: the Fourier forward for callers that cannot
+// allocate device memory themselves.
+//
+// Some hosts own every byte of device memory through their own allocator (a
+// deep-learning framework's caching allocator, an imaging application that
+// hands plug-ins a fixed memory budget), and some latency-critical loops must
+// not call cudaMalloc at all because it can synchronise the whole device.
+// Such callers still own their inputs and outputs, but cannot provide the
+// scratch workspace psf_fourier_vectorial() needs.  This entry point takes
+// that scratch from one fixed-size array in device memory that belongs to the
+// library instead, and otherwise runs the same kernels.
+//
+// The array is a file-scope __device__ variable, so every GPU on which the
+// library is loaded holds PSF_NOALLOC_SCRATCH_BYTES of it until the process
+// exits.  Host code cannot use the array's name as a device address: its
+// address is looked up once per device with cudaGetSymbolAddress.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "psf_common.cuh"
+
+namespace psf {
+void set_last_error(const char* msg);
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[PSF_NOALLOC_SCRATCH_BYTES];
+
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of the scratch array on the current device (set-up on the
+// first call for that device).
+int scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    psf::set_last_error("noalloc: no usable current CUDA device");
+    return PSF_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      psf::set_last_error("noalloc: cudaGetSymbolAddress of the scratch array failed");
+      return PSF_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return PSF_OK;
+}
+
+}  // namespace
+
+extern "C" int psf_fourier_vectorial_noalloc(const psf_optics* opt, int n_pupil,
+                                             const psf_grid* grid,
+                                             const double* zernike, int n_zern,
+                                             const float* phase_map,
+                                             float* intensity, void* fields,
+                                             void* stream) {
+  const size_t need = psf_fourier_workspace_size(opt, n_pupil, grid, PSF_PREC_FP32);
+  if (need == 0) return PSF_ERR_ARG;   // message set by the size query
+  if (need > (size_t)PSF_NOALLOC_SCRATCH_BYTES) {
+    char msg[200];
+    snprintf(msg, sizeof(msg),
+             "noalloc: these sizes need %zu bytes of scratch; the fixed array "
+             "holds %zu (use psf_fourier_vectorial with a workspace)",
+             need, (size_t)PSF_NOALLOC_SCRATCH_BYTES);
+    psf::set_last_error(msg);
+    return PSF_ERR_WORKSPACE;
+  }
+  void* scratch = nullptr;
+  const int r = scratch_address(&scratch);
+  if (r != PSF_OK) return r;
+  return psf_fourier_vectorial(opt, n_pupil, grid, zernike, n_zern, phase_map,
+                               PSF_PREC_FP32, intensity, fields, scratch,
+                               (size_t)PSF_NOALLOC_SCRATCH_BYTES, stream);
+}
