@@ -316,6 +316,11 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(out.numel() * 4)},
         "gpu_launches": launches,
+        "kernel_ms_per_step": {
+            name: round(counts[k][1] / args.steps, 5)
+            for k, name in enumerate(["pupil", "stage1", "stage2", "bessel_radial",
+                                      "bessel_epilogue", "adjoint", "setup"])
+            if counts[k][0]},
         "roofline": roof,
         "clocks": clk.summary(),
     }

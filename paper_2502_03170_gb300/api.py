@@ -102,7 +102,13 @@ def fourier(optics, n_pupil, grid, zernike=None, phase_map=None,
     need = lib.psf_fourier_workspace_size(ctypes.byref(o), n_pupil,
                                           ctypes.byref(g.c), prec)
     if need == 0:
-        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+        # validation failed: the call without a workspace returns its code
+        # (arguments are checked before anything is launched)
+        code = lib.psf_fourier_vectorial(
+            ctypes.byref(o), n_pupil, ctypes.byref(g.c), None, 0, None, prec,
+            ctypes.c_void_p(16), None, None, 0, None)
+        raise _lib.PsfError(code if code else _lib.PSF_ERR_ARG,
+                            lib.psf_last_error().decode())
     buf = ws.get(need)
     dev = buf.device
     I = out if out is not None else torch.empty(

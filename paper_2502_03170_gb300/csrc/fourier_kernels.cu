@@ -51,7 +51,7 @@ __global__ void k_node_table(NodeParams p, NodeTable t) {
     double cm = 1.0, sm = 0.0;
     for (int m = 0; m <= p.zp.max_m; ++m) {
       double pc = 0.0, ps = 0.0;
-      for (int k = kZernMaxOrder; k >= 0; --k) {
+      for (int k = p.zp.deg; k >= 0; --k) {
         pc = pc * rn + p.zp.c[m][k];
         ps = ps * rn + p.zp.s[m][k];
       }

@@ -12,6 +12,7 @@ namespace psf {
 constexpr int kZernMaxOrder = 10;   // Noll j <= 66
 struct ZernPoly {
   int max_m;                                   // -1: no Zernike term
+  int deg;                                     // highest power of rho present
   double c[kZernMaxOrder + 1][kZernMaxOrder + 1];
   double s[kZernMaxOrder + 1][kZernMaxOrder + 1];
 };

@@ -79,6 +79,31 @@ static GLLayers gl_layers(const psf_optics* o, double ts) {
   return g;
 }
 
+// Layers with the same index share one root: t_a sqrt(n^2 - .) + t_b sqrt(n^2 - .)
+// = (t_a + t_b) sqrt(n^2 - .).  Design layers equal to the actual ones cancel.
+static GLLayers merge_layers(const GLLayers& in) {
+  GLLayers g;
+  g.n = 0;
+  for (int l = 0; l < in.n; ++l) {
+    int k = 0;
+    while (k < g.n && g.n_idx[k] != in.n_idx[l]) ++k;
+    if (k == g.n) {
+      g.n_idx[g.n] = in.n_idx[l];
+      g.t[g.n++] = in.t[l];
+    } else {
+      g.t[k] += in.t[l];
+    }
+  }
+  int w = 0;
+  for (int l = 0; l < g.n; ++l)
+    if (g.t[l] != 0.0) {
+      g.t[w] = g.t[l];
+      g.n_idx[w++] = g.n_idx[l];
+    }
+  g.n = w;
+  return g;
+}
+
 // ---------------------------------------------------------------------------
 // Eq. 15, Noll ordering: j -> (n, m), m > 0 cosine, m < 0 sine.
 // ---------------------------------------------------------------------------
@@ -126,6 +151,7 @@ static ZernPoly zernike_poly(const double* c, int n_zern) {
         z.s[am][k] += c[j - 1] * rc[k];
     }
     if (am > z.max_m) z.max_m = am;
+    if (n > z.deg) z.deg = n;
   }
   return z;
 }
@@ -218,6 +244,7 @@ static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
     L.P = c.take<float2>((size_t)L.zc * 3 * NN);
     L.U = c.take<float2>((size_t)L.zc * 3 * g->ny * N);
   } else {
+    L.zc = tc_fourier_zchunk(N, g->nx, g->ny, g->nz);
     tc_fourier_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.tc);
   }
   L.bytes = align_up(c.off, 256);
@@ -256,7 +283,7 @@ static NodeParams node_params(const psf_optics* opt, int N, const double* zern,
   p.s_max = opt->NA / opt->n_i;
   p.inv_lambda = 1.0 / opt->lambda;
   p.n_i = opt->n_i;
-  p.gl = gl_layers(opt, opt->depth);
+  p.gl = merge_layers(gl_layers(opt, opt->depth));
   p.apodize = opt->apodize;
   p.s_env = opt->s_env;
   for (int i = 0; i < 4; ++i) p.pol[i] = opt->pol[i];
@@ -357,7 +384,8 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
     }
   } else {
     r = tc_fourier_forward(L.tc, L.nodes, L.zz, N, grid->nx, grid->ny, grid->dx,
-                           grid->dy, grid->nz, L.zc, f, scale, precision,
+                           grid->dy, grid->nz, L.zc, f, scale,
+                           tc_pupil_amplitude_bound(np), precision,
                            intensity, (float2*)fields, (int*)workspace, s);
     if (r) return fail(r, "split-precision launch failed");
   }
