@@ -171,6 +171,7 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ws = api.Workspace(dev)
 
+    h2d_fn = None
     if args.workload == "fourier":
         c = W.fourier(seed_salt=rank)
         g = api.Grid(c["grid"])
@@ -194,28 +195,35 @@ def run_gpu(args, rank, world, local_rank):
     else:
         c = W.bessel(seed_salt=rank)
         opt = api.make_optics(c["optics"], _lib.PSF_PROJECT_AXISYMMETRIC)
+        prec = api.PRECISIONS[args.precision]
         nsl = int(c["z_offsets"][-1])
         dv = lambda a, dt: torch.as_tensor(np.asarray(a)).to(dev, dt).contiguous()
         depth_d, zern_d = dv(c["depth"], torch.float64), dv(c["zernike"], torch.float64)
         offs_d, z_d = dv(c["z_offsets"], torch.int32), dv(c["z"], torch.float64)
         out = torch.empty((nsl, c["nx"], c["ny"]), dtype=torch.float32, device=dev)
         need = lib.psf_bessel_workspace_size(ctypes.byref(opt), c["n_emitters"], nsl,
-                                             c["n_theta"], c["n_r"], c["nx"], c["ny"], 0)
+                                             c["n_theta"], c["n_r"], c["nx"], c["ny"], prec)
         buf = ws.get(need)
+        # pinned host copies of the per-emitter inputs (end-to-end timing)
+        host_in = [(t.cpu().pin_memory(), t) for t in (depth_d, zern_d, offs_d, z_d)]
+
+        def h2d_fn():
+            for h, d_ in host_in:
+                d_.copy_(h, non_blocking=True)
 
         def step(o=out):
             _lib.check(lib, lib.psf_bessel_vectorial(
                 ctypes.byref(opt), c["n_emitters"], api._ptr(depth_d),
                 api._ptr(zern_d), 21, api._ptr(offs_d), api._ptr(z_d), nsl,
-                c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"], 0,
+                c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"], prec,
                 api._ptr(o), None, api._ptr(buf), buf.numel(), api._stream()))
         voxels = nsl * c["nx"] * c["ny"]
-        h2d = 0
+        h2d = sum(h.numel() * h.element_size() for h, _ in host_in)
         dom_class = 4                   # radial -> Cartesian epilogue (HBM write)
         dom_work = 4.0 * voxels         # algorithmic bytes written per step
         cfg = {"workload": "bessel_vectorial_batched", "n_emitters": c["n_emitters"],
                "n_slices": nsl, "n_theta": c["n_theta"], "n_r": c["n_r"],
-               "nx": c["nx"], "ny": c["ny"], "dx_um": 0.020, "precision": "fp32"}
+               "nx": c["nx"], "ny": c["ny"], "dx_um": 0.020, "precision": args.precision}
 
     def barrier():
         if world > 1:
@@ -260,6 +268,8 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev2[i][0].record(stream)
+        if h2d_fn is not None:
+            h2d_fn()
         step()
         host.copy_(out, non_blocking=True)
         ev2[i][1].record(stream)
@@ -328,7 +338,53 @@ def run_gpu(args, rank, world, local_rank):
         result["dtype"] = "f16x2 (split hi+lo, f32 accumulate)"
     elif args.precision == "split_bf16":
         result["dtype"] = "bf16x2 (split hi+lo, f32 accumulate)"
+    if world == 1 and args.workload == "fourier":
+        result["accuracy"] = fourier_accuracy(out.cpu().numpy(), c)
+        result["variants"] = fourier_variants(args, c, g, opt, N, ws, flush, stream)
     return result, rank
+
+
+def fourier_accuracy(I, c, planes=(0, 64, 127)):
+    """max |I - I_ref| / max |I_ref| on sampled planes, oracle in FP64."""
+    from oracle import fourier as of
+    from oracle.optics import Optics
+    opt = Optics.from_dict(c["optics"])
+    zs = np.asarray(c["grid"]["z"])
+    worst = 0.0
+    for iz in planes:
+        Ir = of.psf_fourier(opt, c["n_pupil"], dict(c["grid"], z=[zs[iz]]),
+                            zernike=c["zernike"])[0]
+        worst = max(worst, float(np.max(np.abs(I[iz] - Ir)) / np.max(Ir)))
+    return {"max_rel_err_vs_fp64_oracle": worst, "planes_checked": list(planes)}
+
+
+def fourier_variants(args, c, g, opt, N, ws, flush, stream, steps=5):
+    """Every contraction precision on the same stack: voxels/s and error."""
+    import torch
+
+    from paper_2502_03170_gb300 import api
+    out = {}
+    for prec in ("fp32", "split_fp16", "split_bf16"):
+        o = torch.empty((g.c.nz, g.c.nx, g.c.ny), dtype=torch.float32,
+                        device=flush.device)
+        for _ in range(2):
+            api.fourier(opt, N, g, zernike=c["zernike"], precision=prec, out=o,
+                        workspace=ws)
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            api.fourier(opt, N, g, zernike=c["zernike"], precision=prec, out=o,
+                        workspace=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        acc = fourier_accuracy(o.cpu().numpy(), c, planes=(64,))
+        out[prec] = {"voxels_per_s": g.c.nz * g.c.nx * g.c.ny / (ms / steps * 1e-3),
+                     "ms_per_stack": ms / steps,
+                     "max_rel_err": acc["max_rel_err_vs_fp64_oracle"]}
+    return out
 
 
 def main():
@@ -338,7 +394,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier", choices=["fourier", "bessel"])
-    ap.add_argument("--precision", default="fp32",
+    ap.add_argument("--precision", default="split_fp16",
                     choices=["fp32", "split_fp16", "split_bf16"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()

@@ -50,7 +50,8 @@ void launch_bessel_jmat(const BesselParams& p, ThetaTable t, float* Bt,
 __global__ void k_bessel_emitters(BesselParams p, ThetaTable t,
                                   const double* __restrict__ depth,
                                   const double* __restrict__ zern,
-                                  EmitterTable et, int* status) {
+                                  EmitterTable et, int* status,
+                                  unsigned* amp_max) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)p.n_em * p.n_theta) return;
   const int e = (int)(idx / p.n_theta), j = (int)(idx - (long long)e * p.n_theta);
@@ -65,6 +66,7 @@ __global__ void k_bessel_emitters(BesselParams p, ThetaTable t,
   double amp = t.amp0[j];
   if (dec != 0.0) amp *= exp(-2.0 * kPi * dec);
   et.amp[idx] = (float)amp;
+  if (amp_max) atomicMax(amp_max, __float_as_uint((float)amp));   // amp >= 0
   et.wfr[idx] = (float)w;
   if (j == 0) {
     int ok = 1;
@@ -83,10 +85,12 @@ __global__ void k_bessel_emitters(BesselParams p, ThetaTable t,
 
 void launch_bessel_emitters(const BesselParams& p, ThetaTable t,
                             const double* depth, const double* zern,
-                            EmitterTable e, int* status, cudaStream_t s) {
+                            EmitterTable e, int* status, unsigned* amp_max,
+                            cudaStream_t s) {
   const long long n = (long long)p.n_em * p.n_theta;
   k_bessel_emitters<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, t, depth,
-                                                                 zern, e, status);
+                                                                 zern, e, status,
+                                                                 amp_max);
 }
 
 // ---------------------------------------------------------------------------

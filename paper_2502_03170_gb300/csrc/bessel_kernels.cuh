@@ -50,9 +50,11 @@ struct EmitterTable {
 
 void launch_bessel_jmat(const BesselParams& p, ThetaTable t, float* Bt,
                         cudaStream_t s);
+// amp_max (nullable): running maximum of the amplitudes (float bits).
 void launch_bessel_emitters(const BesselParams& p, ThetaTable t,
                             const double* depth, const double* zern,
-                            EmitterTable e, int* status, cudaStream_t s);
+                            EmitterTable e, int* status, unsigned* amp_max,
+                            cudaStream_t s);
 void launch_slice_map(const BesselParams& p, const int* z_offsets,
                       const double* z, int* slice_em, float2* zz, int* status,
                       cudaStream_t s);
@@ -66,5 +68,18 @@ void launch_bessel_intensity(const BesselParams& p, const float2* prof,
                              const int* slice_em, const int* valid,
                              const int* pix_i0, const float* pix_f,
                              const float* pix_g, float* I, cudaStream_t s);
+
+// Mirror epilogue.  The four pixels (a, b), (nx-1-a, b), (a, ny-1-b),
+// (nx-1-a, ny-1-b) share their radius, hence the interpolated profiles and
+// the terms alpha, beta of |E|^2; only the sign of sin 2phi differs.  Each
+// thread interpolates one pixel of the quarter a < nx/2, b < ny/2 and writes
+// its four mirrors.  qtab [nx/2][ny/2]: (i0 as int bits, f, S1 cos 2phi,
+// S2 sin 2phi) of the quarter pixels (FP64 geometry, once per call).
+bool bessel_mirror_fit(int nx, int ny, int n_r);
+void launch_quarter_table(const BesselParams& p, float4* qtab, cudaStream_t s);
+void launch_bessel_intensity_mirror(const BesselParams& p, const float2* prof,
+                                    const int* slice_em, const int* valid,
+                                    const float4* qtab, float* I,
+                                    cudaStream_t s);
 
 }  // namespace psf

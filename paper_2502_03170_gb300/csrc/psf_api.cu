@@ -558,17 +558,23 @@ struct BesselLayout {
   int* pix_i0;
   float* pix_f;
   float* pix_g;
+  float4* qtab;
+  TcBessel tc;           // split-precision operands
   size_t bytes;
 };
 
 static BesselLayout bessel_layout(void* ws, int n_em, int n_slices, int n_theta,
-                                  int n_r, int nx, int ny, bool own_profiles) {
+                                  int n_r, int nx, int ny, bool own_profiles,
+                                  int precision) {
   BesselLayout L;
   memset(&L, 0, sizeof(L));
   Carver c(ws);
   L.theta_tab = c.take<double>((size_t)(10 + kMaxM0) * n_theta);
   L.kappa = c.take<float>(2 * (size_t)n_theta);
-  L.Bt = c.take<float>((size_t)3 * n_r * n_theta);
+  if (precision == PSF_PREC_FP32)
+    L.Bt = c.take<float>((size_t)3 * n_r * n_theta);
+  else
+    tc_bessel_carve(c.base, &c.off, n_theta, n_r, n_slices, &L.tc);
   L.et.amp = c.take<float>((size_t)n_em * n_theta);
   L.et.wfr = c.take<float>((size_t)n_em * n_theta);
   L.et.valid = c.take<int>(n_em);
@@ -578,6 +584,7 @@ static BesselLayout bessel_layout(void* ws, int n_em, int n_slices, int n_theta,
   L.pix_i0 = c.take<int>((size_t)nx * ny);
   L.pix_f = c.take<float>((size_t)nx * ny);
   L.pix_g = c.take<float>((size_t)nx * ny);
+  L.qtab = c.take<float4>((size_t)(nx / 2) * (ny / 2) + 1);
   L.bytes = align_up(c.off, 256);
   return L;
 }
@@ -592,8 +599,9 @@ static int check_bessel_args(const psf_optics* base, int n_em, int n_slices,
   if (n_r < 2 || n_r > 4096) return fail(PSF_ERR_ARG, "n_r %d outside [2, 4096]", n_r);
   if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384)
     return fail(PSF_ERR_ARG, "nx, ny must be in [1, 16384]");
-  if (precision != PSF_PREC_FP32)
-    return fail(PSF_ERR_PRECISION, "Bessel path supports PSF_PREC_FP32 only");
+  if (precision != PSF_PREC_FP32 && precision != PSF_PREC_SPLIT_FP16 &&
+      precision != PSF_PREC_SPLIT_BF16)
+    return fail(PSF_ERR_PRECISION, "unknown precision mode %d", precision);
   return PSF_OK;
 }
 
@@ -601,7 +609,8 @@ extern "C" size_t psf_bessel_workspace_size(const psf_optics* base, int n_em,
                                             int n_slices, int n_theta, int n_r,
                                             int nx, int ny, int precision) {
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
-  return bessel_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, true).bytes;
+  return bessel_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, true,
+                       precision).bytes;
 }
 
 extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
@@ -622,7 +631,7 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   BesselLayout L = bessel_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
-                                 profiles == nullptr);
+                                 profiles == nullptr, precision);
   if (ws_bytes < L.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
   if (profiles) L.prof = (float2*)profiles;
@@ -741,14 +750,21 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
                   cudaMemcpyHostToDevice, s);
   if ((r = cuda_check("workspace init"))) return r;
 
+  const bool split = precision != PSF_PREC_FP32;
+  double max_w = 0.0;
+  for (int j = 0; j < n_theta; ++j) max_w = fmax(max_w, T_w[j]);
   {
     TimingScope ts(kTimeSetup, s);
-    launch_bessel_jmat(bp, tt, L.Bt, s);
+    if (split)
+      tc_bessel_jmat(bp, tt, max_w, precision, L.tc, s);
+    else
+      launch_bessel_jmat(bp, tt, L.Bt, s);
   }
+  if (split) cudaMemsetAsync(L.tc.amp_max, 0, sizeof(unsigned), s);
   {
     TimingScope ts(kTimeSetup, s);
     launch_bessel_emitters(bp, tt, depth, n_zern > 0 ? zernike : nullptr, L.et,
-                           (int*)workspace, s);
+                           (int*)workspace, split ? L.tc.amp_max : nullptr, s);
   }
   if (n_slices > 0) {
     // slices no emitter claims keep emitter -1 and are skipped
@@ -761,14 +777,28 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
       TimingScope ts(kTimeSetup, s);
       launch_pixel_table(bp, L.pix_i0, L.pix_f, L.pix_g, s);
     }
-    {
+    if (split) {
+      r = tc_bessel_contract(bp, tt, L.et, L.slice_em, L.zz, max_w, precision, L.tc,
+                             L.prof, (int*)workspace, s);
+      if (r) return fail(r, "split-precision Bessel contraction launch failed");
+    } else {
       TimingScope ts(kTimeBesselRadial, s);
       launch_bessel_profiles_f32(bp, tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
     }
     {
-      TimingScope ts(kTimeBesselEpilogue, s);
-      launch_bessel_intensity(bp, L.prof, L.slice_em, L.et.valid, L.pix_i0,
-                              L.pix_f, L.pix_g, intensity, s);
+      if (bessel_mirror_fit(nx, ny, n_r) && ((uintptr_t)intensity & 15) == 0) {
+        {
+          TimingScope ts(kTimeSetup, s);
+          launch_quarter_table(bp, L.qtab, s);
+        }
+        TimingScope ts(kTimeBesselEpilogue, s);
+        launch_bessel_intensity_mirror(bp, L.prof, L.slice_em, L.et.valid, L.qtab,
+                                       intensity, s);
+      } else {
+        TimingScope ts(kTimeBesselEpilogue, s);
+        launch_bessel_intensity(bp, L.prof, L.slice_em, L.et.valid, L.pix_i0,
+                                L.pix_f, L.pix_g, intensity, s);
+      }
     }
   }
   return cuda_check("psf_bessel_vectorial launch");

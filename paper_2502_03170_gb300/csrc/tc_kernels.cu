@@ -70,7 +70,28 @@ struct Params {
   float2* F;            // [planes][3][nx][ny] or null
   int nx, ny;
   int* status;
+  // mode 2 (Bessel radial contraction): D rows = (n, i) rows of the J_n
+  // operand, D columns = (slice, re/im) interleaved; prof[slice][row] complex
+  float2* prof;
+  int rows_total;       // 3 N_r
+  int n_slices;
+  const float* scale_ptr;   // device scalar: 1 / (S_B S_F)
+  int m_fastest;        // tile order: consecutive tiles share the B tile
 };
+
+// Tile index -> (plane, m-tile, n-tile).
+PSF_D void decode_tile(const Params& p, int t, int& plane, int& mt, int& nt) {
+  const int tpp = p.m_tiles * p.n_tiles;
+  plane = t / tpp;
+  const int rem = t - plane * tpp;
+  if (p.m_fastest) {
+    nt = rem / p.m_tiles;
+    mt = rem - nt * p.m_tiles;
+  } else {
+    mt = rem / p.n_tiles;
+    nt = rem - mt * p.n_tiles;
+  }
+}
 
 // --------------------------------------------------------------------------
 // PTX wrappers
@@ -271,9 +292,8 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
     bool ok = true;
     int issued = 0;
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int plane = t / tiles_per_plane;
-      const int rem = t - plane * tiles_per_plane;
-      const int mt = rem / p.n_tiles, nt = rem - (rem / p.n_tiles) * p.n_tiles;
+      int plane, mt, nt;
+      decode_tile(p, t, plane, mt, nt);
       for (int kc = 0; kc < p.k_chunks; ++kc) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.status)) {
           ok = false;
@@ -283,10 +303,16 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
         mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
         tma_load_2d(base, &mapA_hi, kc * BK, mt * BM, full_bar(stage));
         tma_load_2d(base + A_BYTES, &mapA_lo, kc * BK, mt * BM, full_bar(stage));
-        tma_load_3d(base + 2 * A_BYTES, &mapB_hi, kc * BK, nt * BOUT, plane * 3,
-                    full_bar(stage));
-        tma_load_3d(base + 2 * A_BYTES + B_BYTES, &mapB_lo, kc * BK, nt * BOUT,
-                    plane * 3, full_bar(stage));
+        if (p.mode == 2) {
+          tma_load_2d(base + 2 * A_BYTES, &mapB_hi, kc * BK, nt * BN, full_bar(stage));
+          tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mapB_lo, kc * BK, nt * BN,
+                      full_bar(stage));
+        } else {
+          tma_load_3d(base + 2 * A_BYTES, &mapB_hi, kc * BK, nt * BOUT, plane * 3,
+                      full_bar(stage));
+          tma_load_3d(base + 2 * A_BYTES + B_BYTES, &mapB_lo, kc * BK, nt * BOUT,
+                      plane * 3, full_bar(stage));
+        }
         ++issued;
         if (++stage == STAGES) {
           stage = 0;
@@ -365,12 +391,28 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) break;
       tmem_fence_after();
-      const int plane = t / tiles_per_plane;
-      const int rem = t - plane * tiles_per_plane;
-      const int mt = rem / p.n_tiles, nt = rem - (rem / p.n_tiles) * p.n_tiles;
+      int plane, mt, nt;
+      decode_tile(p, t, plane, mt, nt);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * ACC_COL);
       const int mo = mt * BOUT + oi;           // output index along m
-      if (p.mode == 0) {
+      if (p.mode == 2) {
+        // Bessel: prof[s][row] = scale * (D[row][2k], D[row][2k+1]), s = nt*96 + k
+        const int grow = mt * BM + row;
+        const float sc = *p.scale_ptr;
+        for (int h = 0; h < BN / 32; ++h) {
+          uint32_t r[32];
+          tmem_ld32(tbase + (uint32_t)(h * 32), r);
+          if (grow < p.rows_total) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int s = nt * (BN / 2) + h * 16 + k;
+              if (s < p.n_slices)
+                p.prof[(size_t)s * p.rows_total + grow] =
+                    make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
+            }
+          }
+        }
+      } else if (p.mode == 0) {
         // stage 1: U[plane][c][b = mo][part * N + p] = split(out_scale * D)
         const bool row_ok = mo < p.m_out;
         for (int c = 0; c < 3; ++c) {
@@ -804,6 +846,176 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     if (r) return r;
   }
   return PSF_OK;
+}
+
+// ==========================================================================
+// Bessel radial contraction on the split-precision path
+// ==========================================================================
+namespace tc {
+
+PSF_D void split16d(double v, int bf16, uint16_t& hi, uint16_t& lo) {
+  if (bf16) {
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
+  } else {
+    const __half h = __double2half(v);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__double2half(v - (double)__half2float(h)));
+  }
+}
+
+// B[(n, i)][j] = S_B w_j g_n(theta_j) J_n(k r_i sin theta_j) (Eq. 11), FP64,
+// columns j >= n_theta zero.
+__global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
+                                    int bf16, int Kp, uint16_t* hi, uint16_t* lo) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int rows = 3 * p.n_r;
+  if (idx >= (long long)rows * Kp) return;
+  const int row = (int)(idx / Kp), j = (int)(idx - (long long)row * Kp);
+  double v = 0.0;
+  if (j < p.n_theta) {
+    const int n = row / p.n_r, i = row - n * p.n_r;
+    const double st = t.sin_t[j], ct = t.cos_t[j];
+    const double x = p.k * (i * p.dr) * st;
+    double jn_v, g;
+    if (n == 0) {
+      jn_v = j0(x);
+      g = st * (1.0 + ct);
+    } else if (n == 1) {
+      jn_v = j1(x);
+      g = st * st;
+    } else {
+      jn_v = x > 0.0 ? jn(2, x) : 0.0;   // J_2(0) = 0
+      g = st * (ct - 1.0);
+    }
+    v = sB * t.w[j] * g * jn_v;
+  }
+  uint16_t h, l;
+  split16d(v, bf16, h, l);
+  hi[idx] = h;
+  lo[idx] = l;
+}
+
+// F rows (s, re) and (s, im): S_F amp e^{2 pi i (wfr + n_i z_s cos / lambda)};
+// S_F is the power of two that keeps the largest |F0| below 2^14.
+__global__ void k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable et,
+                                    const int* __restrict__ slice_em,
+                                    const float2* __restrict__ zz,
+                                    const unsigned* __restrict__ amp_max, int Kp,
+                                    int bf16, float sB, uint16_t* hi, uint16_t* lo,
+                                    float* out_scale) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)p.n_slices * Kp) return;
+  const float am = __uint_as_float(*amp_max);
+  const float sF = am > 0.f ? exp2f(floorf(log2f(16384.f / am))) : 1.f;
+  if (idx == 0) *out_scale = 1.f / (sB * sF);
+  const int s = (int)(idx / Kp), j = (int)(idx - (long long)s * Kp);
+  const int e = slice_em[s];
+  float2 v = make_float2(0.f, 0.f);
+  if (j < p.n_theta && e >= 0) {
+    const size_t ej = (size_t)e * p.n_theta + j;
+    const float2 z = zz[s];
+    const float2 c = cis_cycles(frac_mul_add(f2x{t.kh[j], t.kl[j]}, f2x{z.x, z.y}, et.wfr[ej]));
+    const float a = sF * et.amp[ej];
+    v = make_float2(a * c.x, a * c.y);
+  }
+  const size_t r0 = (size_t)(2 * s) * Kp + j, r1 = r0 + Kp;
+  uint16_t h, l;
+  split16(v.x, bf16, h, l);
+  hi[r0] = h;
+  lo[r0] = l;
+  split16(v.y, bf16, h, l);
+  hi[r1] = h;
+  lo[r1] = l;
+}
+
+}  // namespace tc
+
+int tc_bessel_kp(int n_theta) { return (n_theta + 7) / 8 * 8; }
+
+void tc_bessel_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
+                     TcBessel* out) {
+  auto take = [&](size_t bytes) -> char* {
+    *off = align_up(*off, 1024);
+    char* p = base ? base + *off : nullptr;
+    *off += bytes;
+    return p;
+  };
+  const size_t Kp = tc_bessel_kp(n_theta);
+  out->B_hi = (uint16_t*)take(3 * (size_t)n_r * Kp * 2);
+  out->B_lo = (uint16_t*)take(3 * (size_t)n_r * Kp * 2);
+  out->F_hi = (uint16_t*)take(2 * (size_t)n_slices * Kp * 2 + 2);
+  out->F_lo = (uint16_t*)take(2 * (size_t)n_slices * Kp * 2 + 2);
+  out->amp_max = (unsigned*)take(sizeof(unsigned));
+  out->out_scale = (float*)take(sizeof(float));
+}
+
+static float bessel_sB(double max_w) {
+  // |B| <= max_j w_j * |g_n| (<= 2) * |J_n| (<= 1)
+  return pow2_scale(2.0 * max_w, 16384.0);
+}
+
+void tc_bessel_jmat(const BesselParams& p, ThetaTable t, double max_w,
+                    int precision, const TcBessel& ops, cudaStream_t s) {
+  const int Kp = tc_bessel_kp(p.n_theta);
+  const long long n = 3LL * p.n_r * Kp;
+  tc::k_bessel_jmat_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      p, t, (double)bessel_sB(max_w), precision == PSF_PREC_SPLIT_BF16 ? 1 : 0, Kp,
+      ops.B_hi, ops.B_lo);
+}
+
+int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
+                       const int* slice_em, const float2* zz, double max_w,
+                       int precision, const TcBessel& ops, float2* prof,
+                       int* status, cudaStream_t s) {
+  using namespace tc;
+  const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
+  const int Kp = tc_bessel_kp(p.n_theta);
+  const float sB = bessel_sB(max_w);
+  {
+    TimingScope ts(kTimeSetup, s);
+    const long long n = (long long)p.n_slices * Kp;
+    k_bessel_fgen_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        p, t, et, slice_em, zz, ops.amp_max, Kp, bf16, sB, ops.F_hi, ops.F_lo,
+        ops.out_scale);
+  }
+  // K extent = n_theta (columns past it read as zero), row pitch Kp
+  auto map2 = [&](CUtensorMap* m, const uint16_t* base, int rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)p.n_theta, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void*)base, dims, strides, box,
+              es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              SWZ == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  CUtensorMap mBh, mBl, mFh, mFl;
+  const int rows = 3 * p.n_r;
+  if (!(map2(&mBh, ops.B_hi, rows, BM) && map2(&mBl, ops.B_lo, rows, BM) &&
+        map2(&mFh, ops.F_hi, 2 * p.n_slices, BN) && map2(&mFl, ops.F_lo, 2 * p.n_slices, BN)))
+    return PSF_ERR_CUDA;
+  Params q;
+  memset(&q, 0, sizeof(q));
+  q.planes = 1;
+  q.m_tiles = ceil_div(rows, BM);
+  q.n_tiles = ceil_div(2 * p.n_slices, BN);
+  q.k_chunks = ceil_div(p.n_theta, BK);
+  q.idesc = make_idesc(bf16);
+  q.mode = 2;
+  q.bf16 = bf16;
+  q.prof = prof;
+  q.rows_total = rows;
+  q.n_slices = p.n_slices;
+  q.scale_ptr = ops.out_scale;
+  q.m_fastest = 1;
+  q.status = status;
+  TimingScope ts(kTimeBesselRadial, s);
+  return launch_gemm(mBh, mBl, mFh, mFl, q, s);
 }
 
 }  // namespace psf

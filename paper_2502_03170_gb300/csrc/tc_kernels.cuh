@@ -11,9 +11,33 @@
 //     hi.hi + lo.hi + hi.lo accumulate in FP32 in TMEM.
 #pragma once
 
+#include "bessel_kernels.cuh"
 #include "fourier_kernels.cuh"
 
 namespace psf {
+
+// Split-precision operands of the Bessel radial contraction
+//   prof[s][(n, i)] = sum_j B[(n, i)][j] F[j][s]  (real B, complex F):
+// B rows (n, i) x K columns (theta nodes, padded to Kp = 8k), F rows
+// (s, re/im) interleaved, both split hi + lo.
+struct TcBessel {
+  uint16_t *B_hi, *B_lo;     // [3 N_r][Kp]
+  uint16_t *F_hi, *F_lo;     // [2 n_slices][Kp]
+  unsigned* amp_max;         // device max of |F0| (float bits), zeroed per call
+  float* out_scale;          // device 1 / (S_B S_F)
+};
+
+int tc_bessel_kp(int n_theta);
+void tc_bessel_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
+                     TcBessel* out);
+// J_n operand in split form (per call).
+void tc_bessel_jmat(const BesselParams& p, ThetaTable t, double max_w,
+                    int precision, const TcBessel& ops, cudaStream_t s);
+// F operand from the per-emitter table and the contraction into prof.
+int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
+                       const int* slice_em, const float2* zz, double max_w,
+                       int precision, const TcBessel& ops, float2* prof,
+                       int* status, cudaStream_t s);
 
 struct TcOperands {
   uint16_t *Ax_hi, *Ax_lo;   // [2 nx][2 N] zoom-matrix blocks

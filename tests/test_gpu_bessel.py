@@ -1,4 +1,8 @@
-"""Bessel strategy on the GPU (through the C ABI) against the FP64 oracle."""
+"""Bessel strategy on the GPU (through the C ABI) against the FP64 oracle.
+
+Tolerance per stack: max |I - I_ref| / max |I_ref| <= 1e-5 for the FP32 and
+split-fp16 radial contractions, 1e-4 for split-bf16 (16 significant bits per
+operand); the complex profiles are held to the same bounds."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +14,8 @@ from paper_2502_03170_gb300 import workloads as W
 from .gpu_helpers import max_rel, oracle_optics
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-5
+TOL = {"fp32": 1e-5, "split_fp16": 1e-5, "split_bf16": 1e-4}
+PRECS = ["fp32", "split_fp16", "split_bf16"]
 
 
 def small_batch(seed=7, nz=(3, 1, 4, 2, 5), with_m_nonzero=True):
@@ -32,13 +37,14 @@ def per_stack_max_rel(I, Ir, offs):
     return max(max_rel(I[a:b], Ir[a:b]) for a, b in zip(offs[:-1], offs[1:]) if b > a)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("pol", [W.CIRCULAR, (1.0, 0.0), (0.6, 0.48 + 0.64j)])
-def test_small_batch_parity(lib, pol):
+def test_small_batch_parity(lib, pol, prec):
     d = dict(W.optics_gibson_lanni(0.0), pol=pol)
     depth, zern, offs, z = small_batch()
     nt, nr, nx, ny, dx, dy = 64, 48, 20, 17, 0.03, 0.025
     I, P = api.bessel(d, depth, zern, offs, z, nt, nr, nx, ny, dx, dy,
-                      project=True, profiles=True)
+                      project=True, profiles=True, precision=prec)
     torch.cuda.synchronize()
     I, P = I.cpu().numpy(), P.cpu().numpy()
     opt = oracle_optics(d)
@@ -46,28 +52,34 @@ def test_small_batch_parity(lib, pol):
                              project=True)
     Pr = ob.profiles_batch(opt, depth, zern, offs, z, nt, nr, nx, ny, dx, dy,
                            project=True)
-    assert per_stack_max_rel(I, Ir, offs) <= TOL
-    assert max_rel(P, Pr) <= TOL
+    assert per_stack_max_rel(I, Ir, offs) <= TOL[prec]
+    assert max_rel(P, Pr) <= TOL[prec]
 
 
-@pytest.mark.parametrize("nx,ny,nr", [(21, 15, 32), (1, 1, 2), (9, 40, 300)])
-def test_odd_grids_and_centre_pixel(lib, nx, ny, nr):
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16"])
+@pytest.mark.parametrize("nx,ny,nr,nt", [(21, 15, 32, 40), (1, 1, 2, 40),
+                                         (9, 40, 300, 40), (24, 40, 64, 40),
+                                         (2, 8, 2, 7), (16, 8, 1024, 130)])
+def test_odd_grids_and_centre_pixel(lib, nx, ny, nr, nt, prec):
     """Odd grids put a pixel on the axis (r = 0, J_1 = J_2 = 0) and make the
-    interpolation use the first radial cell; n_r = 2 is the smallest grid."""
+    interpolation use the first radial cell; n_r = 2 is the smallest grid.
+    Even grids with ny % 8 == 0 take the mirror-symmetric epilogue (an
+    elliptical Jones vector makes its sin 2phi sign flips visible); theta
+    counts that are not multiples of the 64-wide K tile leave a ragged tail."""
     d = dict(W.optics_gibson_lanni(0.0), pol=(0.6, 0.48 + 0.64j))
     depth, zern, offs, z = small_batch(seed=3, nz=(2, 3))
-    I, P = api.bessel(d, depth, zern, offs, z, 40, nr, nx, ny, 0.021, 0.019,
-                      project=True, profiles=True)
+    I, P = api.bessel(d, depth, zern, offs, z, nt, nr, nx, ny, 0.021, 0.019,
+                      project=True, profiles=True, precision=prec)
     torch.cuda.synchronize()
     I, P = I.cpu().numpy(), P.cpu().numpy()
     assert np.all(np.isfinite(P))
     opt = oracle_optics(d)
-    Ir = ob.psf_bessel_batch(opt, depth, zern, offs, z, 40, nr, nx, ny, 0.021,
+    Ir = ob.psf_bessel_batch(opt, depth, zern, offs, z, nt, nr, nx, ny, 0.021,
                              0.019, project=True)
-    Pr = ob.profiles_batch(opt, depth, zern, offs, z, 40, nr, nx, ny, 0.021,
+    Pr = ob.profiles_batch(opt, depth, zern, offs, z, nt, nr, nx, ny, 0.021,
                            0.019, project=True)
-    assert per_stack_max_rel(I, Ir, offs) <= TOL
-    assert max_rel(P, Pr) <= TOL
+    assert per_stack_max_rel(I, Ir, offs) <= TOL[prec]
+    assert max_rel(P, Pr) <= TOL[prec]
 
 
 def test_not_axisymmetric_status(lib):
@@ -88,14 +100,15 @@ def test_not_axisymmetric_status(lib):
         assert np.array_equal(I[a:b], I2[a:b])
 
 
-def test_bessel_config_full_size_sampled(lib):
+@pytest.mark.parametrize("prec", PRECS)
+def test_bessel_config_full_size_sampled(lib, prec):
     """The batched workload (4096 emitters, uneven stacks, 200 theta nodes,
     256 radii, 128^2 px) in one call; sampled emitters recomputed by the
     oracle."""
     c = W.bessel()
     I = api.bessel(c["optics"], c["depth"], c["zernike"], c["z_offsets"], c["z"],
                    c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"],
-                   project=True)
+                   project=True, precision=prec)
     torch.cuda.synchronize()
     opt = oracle_optics(c["optics"])
     offs = c["z_offsets"]
@@ -105,4 +118,6 @@ def test_bessel_config_full_size_sampled(lib):
         Ir = ob.psf_bessel_batch(opt, c["depth"], c["zernike"], offs, c["z"],
                                  c["n_theta"], c["n_r"], c["nx"], c["ny"],
                                  c["dx"], c["dy"], project=True, emitters=[e])
-        assert max_rel(Ie, Ir) <= TOL, e
+        assert max_rel(Ie, Ir) <= TOL[prec], e
+    del I
+    torch.cuda.empty_cache()
