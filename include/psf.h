@@ -209,7 +209,8 @@ size_t psf_bessel_workspace_size(const psf_optics* base, int n_emitters,
  * each pixel radius; E from Eq. 10 with the Jones vector of `base`.
  *   depth, zernike, z_offsets, z : DEVICE arrays (double, double, int, double)
  *   n_slices   = z_offsets[n_emitters] (host copy, for sizing)
- *   intensity  device float [n_slices][nx][ny] (packed)
+ *   intensity  device float [n_slices][nx][ny] (packed); may be NULL when
+ *              profiles is given (profiles only, no Cartesian epilogue)
  *   profiles   device complex64 [n_slices][3][n_r] (I_0, I_1, I_2) or NULL
  * A non-zero m != 0 coefficient without PSF_PROJECT_AXISYMMETRIC marks the
  * workspace status PSF_ERR_NOT_AXISYMMETRIC and that emitter's slices are not
@@ -221,6 +222,69 @@ int psf_bessel_vectorial(const psf_optics* base, int n_emitters,
                          double dy, int precision, float* intensity,
                          void* profiles, void* workspace, size_t ws_bytes,
                          void* stream);
+
+/* ========================================================================== */
+/* Learned surrogate of the Bessel profiles (not in the paper; motivated by   */
+/* its learning-based applications, Sec. 6).                                  */
+/* ========================================================================== */
+/* An MLP 23 -> 256 -> 256 -> 256 -> 256 -> 1536 with SiLU on the hidden
+ * layers maps a query q = (c_1..c_21 [rad], depth t_s [um], defocus z [um])
+ * to the complex profiles I_0, I_1, I_2 of Eq. 11 at the 256 radii of the
+ * Bessel path (out[b] = complex64 [3][256] viewed as float [1536]); an error
+ * head 256 -> 1 on the last hidden layer predicts log10 of the relative L2
+ * error of out[b].  The network sees q as c / 0.05, d = t_s / 5 - 1,
+ * u = z / 2 and the Fourier features sin/cos(2 pi f_k u), f_k = 0.5 16^(k/23),
+ * and sin/cos(2 pi g_k d), g_k = 0.5 40^(k/23), k = 0..23 (119 inputs padded
+ * to 120).  Weights live in FP32 (master) with BF16 copies; every GEMM runs on
+ * tcgen05 in BF16 with FP32 accumulation; hidden activations and
+ * pre-activations are stored in BF16.
+ *
+ * state: caller-owned device block of psf_mlp_state_bytes() bytes holding the
+ *   FP32 parameters (packed W_0 [256][120] (input padded), b_0, W_1, b_1,
+ *   W_2, b_2, W_3, b_3, W_4 [1536][256], b_4, error head w_e [256], b_e),
+ *   the Adam moments and the BF16 weight copies.
+ * query [B][23], target / out [B][1536]: device float. */
+#define PSF_MLP_IN 23
+#define PSF_MLP_OUT 1536
+size_t psf_mlp_param_count(void);
+size_t psf_mlp_state_bytes(void);
+/* Deterministic initialisation from seed (uniform fan-in scaled weights,
+ * zero biases, zero moments). */
+int psf_mlp_init(void* state, unsigned long long seed, void* stream);
+size_t psf_mlp_workspace_size(int batch);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step = 1, 2, ... for the
+ * bias correction) on L = (1/B) sum_b |out_b - t_b|^2 / |t_b|^2 for the
+ * trunk and (1/B) sum_b (e_b - log10(rel_err_b))^2 for the error head (whose
+ * gradient does not flow into the trunk).  loss: device float [2] or NULL. */
+int psf_mlp_train_step(void* state, const float* query, const float* target,
+                       int batch, float lr, int step, float* loss, void* ws,
+                       size_t ws_bytes, void* stream);
+/* Gradients of the same losses at the current parameters (packed like the
+ * parameters, device float [param_count]); the state is not changed. */
+int psf_mlp_gradients(void* state, const float* query, const float* target,
+                      int batch, float* grads, float* loss, void* ws,
+                      size_t ws_bytes, void* stream);
+/* Inference: out [B][1536]; err_log10 [B] (predicted log10 relative error)
+ * or NULL.  Sizes: 1 <= batch <= 1048576. */
+int psf_mlp_forward(const void* state, const float* query, int batch, float* out,
+                    float* err_log10, void* ws, size_t ws_bytes, void* stream);
+int psf_mlp_get_params(const void* state, float* params, void* stream);
+int psf_mlp_set_params(void* state, const float* params, void* stream);
+
+/* Profiles of `batch` queries by the surrogate, with the Bessel path as the
+ * fallback: queries whose predicted relative error, doubled as a safety
+ * margin, exceeds max_rel_err (or is not finite) are
+ * recomputed by psf_bessel_vectorial (geometry of `base`, n_theta Gauss-
+ * Legendre nodes, 256 radii up to the corner radius of the nx x ny grid at
+ * dx, dy) and their outputs replaced.  Synchronises the stream once (to size
+ * the fallback batch); *n_fallback receives its size. */
+size_t psf_surrogate_workspace_size(const psf_optics* base, int batch,
+                                    int n_theta, int nx, int ny, int precision);
+int psf_surrogate_profiles(const void* state, const psf_optics* base,
+                           const float* query, int batch, double max_rel_err,
+                           int n_theta, int nx, int ny, double dx, double dy,
+                           int precision, float* out, int* n_fallback, void* ws,
+                           size_t ws_bytes, void* stream);
 
 /* ========================================================================== */
 /* Status and diagnostics.                                                    */

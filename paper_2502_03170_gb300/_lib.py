@@ -74,6 +74,19 @@ PROTOTYPES = {
     "psf_kernel_timing": (_I, [_I]),
     "psf_kernel_timing_read": (_I, [_I, ctypes.POINTER(_I),
                                     ctypes.POINTER(ctypes.c_double)]),
+    "psf_mlp_param_count": (_S, []),
+    "psf_mlp_state_bytes": (_S, []),
+    "psf_mlp_init": (_I, [_P, ctypes.c_ulonglong, _P]),
+    "psf_mlp_workspace_size": (_S, [_I]),
+    "psf_mlp_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float, _I, _P, _P, _S,
+                                _P]),
+    "psf_mlp_gradients": (_I, [_P, _P, _P, _I, _P, _P, _P, _S, _P]),
+    "psf_mlp_forward": (_I, [_P, _P, _I, _P, _P, _P, _S, _P]),
+    "psf_mlp_get_params": (_I, [_P, _P, _P]),
+    "psf_mlp_set_params": (_I, [_P, _P, _P]),
+    "psf_surrogate_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I]),
+    "psf_surrogate_profiles": (_I, [_P, _OPT, _P, _I, _D, _I, _I, _I, _D, _D,
+                                    _I, _P, ctypes.POINTER(_I), _P, _S, _P]),
     "psf_bessel_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I, _I]),
     "psf_bessel_vectorial": (_I, [_OPT, _I, _P, _P, _I, _P, _P, _I, _I, _I,
                                   _I, _I, _D, _D, _I, _P, _P, _P, _S, _P]),

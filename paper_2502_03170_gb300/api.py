@@ -130,7 +130,7 @@ def fourier(optics, n_pupil, grid, zernike=None, phase_map=None,
 
 def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
            project=False, profiles=False, precision="fp32", workspace=None,
-           stream=None):
+           stream=None, intensity=True):
     """Batched vectorial PSFs by the Bessel strategy (Eq. 10-11).
 
     depth [n_em], zernike [n_em, n_zern], z_offsets [n_em + 1] (int32),
@@ -162,7 +162,8 @@ def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
     if need == 0:
         raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
     buf = ws.get(need)
-    I = torch.empty((n_slices, nx, ny), dtype=torch.float32, device=dev)
+    I = torch.empty((n_slices, nx, ny), dtype=torch.float32,
+                    device=dev) if intensity else None
     P = torch.empty((n_slices, 3, n_r), dtype=torch.complex64,
                     device=dev) if profiles else None
     check(lib, lib.psf_bessel_vectorial(
@@ -170,4 +171,6 @@ def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
         _ptr(offs_d), _ptr(z_d), n_slices, n_theta, n_r, nx, ny, float(dx),
         float(dy), prec, _ptr(I), _ptr(P), _ptr(buf), buf.numel(),
         _stream(stream)))
+    if not intensity:
+        return P
     return (I, P) if profiles else I

@@ -628,7 +628,8 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
   if (!depth || !z_offsets || (n_slices > 0 && !z) || (n_zern > 0 && !zernike))
     return fail(PSF_ERR_ARG, "depth / z_offsets / z / zernike pointer is NULL");
-  if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");
+  if (!intensity && !profiles && n_slices > 0)
+    return fail(PSF_ERR_ARG, "intensity and profiles are both NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   BesselLayout L = bessel_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
                                  profiles == nullptr, precision);
@@ -786,7 +787,9 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
       launch_bessel_profiles_f32(bp, tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
     }
     {
-      if (bessel_mirror_fit(nx, ny, n_r) && ((uintptr_t)intensity & 15) == 0) {
+      if (!intensity) {
+        // profiles only: no radial -> Cartesian epilogue
+      } else if (bessel_mirror_fit(nx, ny, n_r) && ((uintptr_t)intensity & 15) == 0) {
         {
           TimingScope ts(kTimeSetup, s);
           launch_quarter_table(bp, L.qtab, s);
