@@ -68,18 +68,22 @@ def axisymmetric_coeffs(zernike, project):
     return z
 
 
-def pupil_function(opt, theta, zernike=None, project=False):
-    """F0(theta) = A(theta) exp(i W(theta)), W = W_GL + m=0 Zernike terms."""
+def pupil_function(opt, theta, zernike=None, project=False, w0=None):
+    """F0(theta) = A(theta) exp(i W(theta)), W = W_GL + m=0 Zernike terms
+    (+ an optional free radial phase w0(theta) at the nodes, radians)."""
     sin_t = np.sin(theta)
     cos_t = np.cos(theta)
     w = gibson_lanni_phase(opt, sin_t)
     z = axisymmetric_coeffs(zernike, project)
     if z is not None and len(z):
         w = w + zernike_phase(z, sin_t / opt.s_max, np.zeros_like(theta))
+    if w0 is not None:
+        w = w + np.asarray(w0, dtype=np.float64)
     return amplitude(opt, cos_t, sin_t) * np.exp(1j * w)
 
 
-def profiles(opt, n_theta, r, zs, zernike=None, project=False, rule="gl"):
+def profiles(opt, n_theta, r, zs, zernike=None, project=False, rule="gl",
+             w0=None):
     """I_n(r_i, z) of Eq. 11 for n = 0, 1, 2 -> complex array [nz, 3, len(r)]."""
     if rule == "gl":
         th, wt = gl_rule(n_theta, opt.theta_max)
@@ -89,7 +93,7 @@ def profiles(opt, n_theta, r, zs, zernike=None, project=False, rule="gl"):
         th, wt = riemann_rule(n_theta, opt.theta_max)
     sin_t, cos_t = np.sin(th), np.cos(th)
     g = (sin_t * (1.0 + cos_t), sin_t * sin_t, sin_t * (cos_t - 1.0))
-    f0 = pupil_function(opt, th, zernike, project)
+    f0 = pupil_function(opt, th, zernike, project, w0)
     arg = opt.k * np.outer(np.asarray(r, dtype=np.float64), sin_t)  # [nr, nth]
     zs = np.asarray(zs, dtype=np.float64)
     out = np.empty((len(zs), 3, arg.shape[0]), dtype=np.complex128)
@@ -139,10 +143,10 @@ def pixel_polar(nx, ny, dx, dy):
 
 
 def field_bessel(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike=None,
-                 project=False):
+                 project=False, w0=None):
     """E [nz, 3, nx, ny] by profiles on the radial grid + interpolation."""
     r, r_max = radial_grid(n_r, nx, ny, dx, dy)
-    prof = profiles(opt, n_theta, r, zs, zernike, project)
+    prof = profiles(opt, n_theta, r, zs, zernike, project, w0=w0)
     rho, cos_p, sin_p = pixel_polar(nx, ny, dx, dy)
     E = np.empty((len(zs), 3, nx, ny), dtype=np.complex128)
     for iz in range(len(zs)):
@@ -164,14 +168,15 @@ def field_bessel_direct(opt, n_theta, nx, ny, dx, dy, zs, zernike=None,
 
 
 def psf_bessel(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike=None,
-               project=False):
-    E = field_bessel(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, project)
+               project=False, w0=None):
+    E = field_bessel(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, project, w0)
     return np.sum(E.real ** 2 + E.imag ** 2, axis=1)
 
 
 def psf_bessel_batch(opt, depths, zernikes, z_offsets, zs, n_theta, n_r, nx,
-                     ny, dx, dy, project=False, emitters=None):
-    """Batched emitters (each its own depth, Zernike row and z sub-list).
+                     ny, dx, dy, project=False, emitters=None, phase_theta=None):
+    """Batched emitters (each its own depth, Zernike row and z sub-list; with
+    ``phase_theta`` [n_em, n_theta] also a free radial phase at the nodes).
 
     Returns the packed intensity [z_offsets[-1], nx, ny] (or only the slices of
     the listed ``emitters``, concatenated in that order).
@@ -183,13 +188,14 @@ def psf_bessel_batch(opt, depths, zernikes, z_offsets, zs, n_theta, n_r, nx,
     for e in sel:
         o = opt.with_depth(depths[e])
         zc = None if zernikes is None else zernikes[e]
+        w0 = None if phase_theta is None else phase_theta[e]
         out.append(psf_bessel(o, n_theta, n_r, nx, ny, dx, dy,
-                              zs[z_offsets[e]:z_offsets[e + 1]], zc, project))
+                              zs[z_offsets[e]:z_offsets[e + 1]], zc, project, w0))
     return np.concatenate(out, axis=0)
 
 
 def profiles_batch(opt, depths, zernikes, z_offsets, zs, n_theta, n_r, nx, ny,
-                   dx, dy, project=False, emitters=None):
+                   dx, dy, project=False, emitters=None, phase_theta=None):
     """Complex profiles [sum z, 3, n_r] of the batched emitters (packed)."""
     r, _ = radial_grid(n_r, nx, ny, dx, dy)
     z_offsets = np.asarray(z_offsets)
@@ -199,6 +205,7 @@ def profiles_batch(opt, depths, zernikes, z_offsets, zs, n_theta, n_r, nx, ny,
     for e in sel:
         o = opt.with_depth(depths[e])
         zc = None if zernikes is None else zernikes[e]
+        w0 = None if phase_theta is None else phase_theta[e]
         out.append(profiles(o, n_theta, r, zs[z_offsets[e]:z_offsets[e + 1]],
-                            zc, project))
+                            zc, project, w0=w0))
     return np.concatenate(out, axis=0)

@@ -1,6 +1,6 @@
 """Small, self-contained invocations of single hot kernels for profiling.
 
-    python -m paper_2502_03170_gb300.profile_cases <case> [--precision P]
+    python -m paper_2502_03170_gb300.profile_cases <case> [--precision P] [--nz NZ]
 
 Each case runs one warm-up call and one measured call of the library on
 cuda:0 with sizes small enough for a full ncu capture (well under a few GB on
@@ -42,7 +42,7 @@ def main():
         for _ in range(2):
             I = api.bessel(c["optics"], c["depth"], c["zernike"], c["z_offsets"],
                            c["z"], c["n_theta"], c["n_r"], c["nx"], c["ny"],
-                           c["dx"], c["dy"], project=True)
+                           c["dx"], c["dy"], project=True, precision=args.precision)
         torch.cuda.synchronize()
         assert torch.isfinite(I).all()
     print("ok")
