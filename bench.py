@@ -34,6 +34,38 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
 N_SM = 152
 FP32_LANES_PER_SM = 128
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work
+# of the dominant kernels, from one ncu capture each (profiles/ has the
+# command and the figures).  A figure holds only for the source it was taken
+# on: when the kernel's sources hash differently, traffic is reported as null.
+PROFILED_TRAFFIC = {
+    # 13-plane z-chunk (256^2 pupil, 512^2 px): 43.05 MB read + 0.32 MB written
+    "stage2_contraction_intensity": dict(
+        bytes_per_unit=(43.046e6 + 0.316e6) / 13, unit="plane",
+        sources=("tc_kernels.cu", "tc_kernels.cuh", "tc_ptx.cuh"),
+        sha256_16="a8d98e5b0528b495", precision="split_fp16"),
+    # 9442 slices of 128^2 px: 58.33 MB read + 557.0 MB written
+    "bessel_radial_to_cartesian": dict(
+        bytes_per_unit=(58.325e6 + 557.009e6) / 9442, unit="slice",
+        sources=("bessel_epilogue.cu", "bessel_kernels.cuh", "psf_common.cuh"),
+        sha256_16="4e7983811f09d1ff", precision=None),
+}
+
+
+def profiled_traffic(kernel, units_per_launch, precision):
+    """Per-launch DRAM bytes from the capture, or None if the kernel changed."""
+    import hashlib
+    e = PROFILED_TRAFFIC.get(kernel)
+    if e is None or (e["precision"] and e["precision"] != precision):
+        return None
+    h = hashlib.sha256()
+    for f in e["sources"]:
+        with open(os.path.join(ROOT, "paper_2502_03170_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != e["sha256_16"]:
+        return None
+    return e["bytes_per_unit"] * units_per_launch
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -214,7 +246,7 @@ def run_gpu(args, rank, world, local_rank):
         def step(o=out):
             _lib.check(lib, lib.psf_bessel_vectorial(
                 ctypes.byref(opt), c["n_emitters"], api._ptr(depth_d),
-                api._ptr(zern_d), 21, api._ptr(offs_d), api._ptr(z_d), nsl,
+                api._ptr(zern_d), 21, None, api._ptr(offs_d), api._ptr(z_d), nsl,
                 c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"], prec,
                 api._ptr(o), None, api._ptr(buf), buf.numel(), api._stream()))
         voxels = nsl * c["nx"] * c["ny"]
@@ -278,11 +310,8 @@ def run_gpu(args, rank, world, local_rank):
     ms_e2e = max(sum(a.elapsed_time(b) for a, b in ev2), 1e3 * t_host)
 
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+        from paper_2502_03170_gb300 import shard
+        ms, ms_e2e = shard.max_over_ranks([ms, ms_e2e], device=dev)
 
     ms_step = ms / args.steps
     value = world * voxels / (ms_step * 1e-3)
@@ -302,10 +331,15 @@ def run_gpu(args, rank, world, local_rank):
         bound, unit = "hbm", "GB/s"
         peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
         achieved = dom_work * args.steps / (t_dom * 1e-3) / 1e9 if t_dom else None
+    kname = {2: "stage2_contraction_intensity", 4: "bessel_radial_to_cartesian"}[dom_class]
+    per_step = max(n_dom // max(args.steps, 1), 1)
+    units = (cfg["nz"] if dom_class == 2 else cfg["n_slices"]) / per_step
+    traffic = profiled_traffic(kname, units, args.precision)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": {2: "stage2_contraction_intensity",
-                       4: "bessel_radial_to_cartesian"}[dom_class],
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram read + write, scaled by units)",
+            "kernel": kname,
             "launches": n_dom // max(args.steps, 1),
             "avg_launch_ms": t_dom / max(n_dom, 1),
             "peak_source": "%s (MEASURED_PEAKS.json)" % peaks_src

@@ -199,15 +199,18 @@ size_t psf_bessel_workspace_size(const psf_optics* base, int n_emitters,
                                  int ny, int precision);
 
 /* Every emitter e has depth t_s = depth[e], Zernike row zernike[e][0..n_zern)
- * (only m = 0 terms enter, Sec. 3.4) and defocus planes
+ * (only m = 0 terms enter, Sec. 3.4), an optional free radial phase
+ * phase_theta[e][j] at the theta nodes and defocus planes
  * z[z_offsets[e] .. z_offsets[e+1]).  Per slice:
  *   I_n(r_i, z) = sum_j w_j g_n(theta_j) J_n(k r_i sin theta_j)
  *                 A(theta_j) e^{i(W_e(theta_j) + k z cos theta_j)},
+ * W_e = W_GL(t_s) (Eq. 13-14) + sum_{m=0} c_j Z_j (Eq. 15) + phase_theta[e],
  * g_0 = sin(1+cos), g_1 = sin^2, g_2 = sin(cos-1) (Eq. 11), Gauss-Legendre
  * nodes theta_j on [0, asin(NA/n_i)]; r_i = i r_max/(n_r-1) with r_max the
  * corner radius of the output grid; complex linear interpolation of I_n at
  * each pixel radius; E from Eq. 10 with the Jones vector of `base`.
  *   depth, zernike, z_offsets, z : DEVICE arrays (double, double, int, double)
+ *   phase_theta  device float [n_emitters][n_theta] (radians) or NULL
  *   n_slices   = z_offsets[n_emitters] (host copy, for sizing)
  *   intensity  device float [n_slices][nx][ny] (packed); may be NULL when
  *              profiles is given (profiles only, no Cartesian epilogue)
@@ -217,11 +220,54 @@ size_t psf_bessel_workspace_size(const psf_optics* base, int n_emitters,
  * written.  Sizes: n_theta in [2, 880], n_r in [2, 4096].                 */
 int psf_bessel_vectorial(const psf_optics* base, int n_emitters,
                          const double* depth, const double* zernike, int n_zern,
-                         const int* z_offsets, const double* z, int n_slices,
-                         int n_theta, int n_r, int nx, int ny, double dx,
-                         double dy, int precision, float* intensity,
-                         void* profiles, void* workspace, size_t ws_bytes,
-                         void* stream);
+                         const float* phase_theta, const int* z_offsets,
+                         const double* z, int n_slices, int n_theta, int n_r,
+                         int nx, int ny, double dx, double dy, int precision,
+                         float* intensity, void* profiles, void* workspace,
+                         size_t ws_bytes, void* stream);
+
+/* Workspace for psf_bessel_vectorial_backward() (0 if the arguments are
+ * invalid; the backward takes nx, ny <= 4096). */
+size_t psf_bessel_backward_workspace_size(const psf_optics* base, int n_emitters,
+                                          int n_slices, int n_theta, int n_r,
+                                          int nx, int ny, int precision);
+
+/* Gradient of L = sum_{slices, pixels} g(I) through Eq. 10-11 (same inputs as
+ * psf_bessel_vectorial; the profiles are recomputed, nothing is stored).
+ * With target != NULL the loss is sum (I - T)^2 per emitter, otherwise
+ * dL/dI = grad_intensity.  The adjoint, with G = dL/dI and the complex
+ * gradient g_X = dL/dRe X + i dL/dIm X:
+ *   g_E_c = 2 G E_c;  g_I_n through the conjugate of Eq. 10 and the transposed
+ *   radial interpolation;  g_F = sum_n B_n^T g_I_n (B_n the J_n operand);
+ *   Q_j = sum_{z of e} conj(g_F(theta_j, z)) F(theta_j, z);
+ *   dL/dW_0(theta_j) = -Im Q_j,
+ *   dL/dc_q  = sum_j Z_q(sin theta_j / s_max) dL/dW_0(theta_j)  (m = 0 Noll q;
+ *              0 for m != 0, which do not enter the spherical form),
+ *   dL/dt_s  = sum_j Re(i D_j Q_j), D_j = dW_GL/dt_s (Eq. 13 with t_i from
+ *              Eq. 14; complex where a layer is evanescent).
+ * Every reduction runs in a fixed order (bitwise reproducible).
+ *   target, grad_intensity  device float [n_slices][nx][ny] (one non-NULL)
+ *   loss              device float [n_emitters] or NULL (target only)
+ *   grad_phase_theta  device float [n_emitters][n_theta] or NULL
+ *   grad_zernike      device float [n_emitters][n_zern] or NULL
+ *   grad_depth        device float [n_emitters] or NULL  (per um)
+ * precision: PSF_PREC_FP32 runs the recomputation and the adjoint contraction
+ * in FP32; the split modes recompute the profiles on tensor cores in that
+ * split and, where the grid's mirror groups fit in shared memory (up to about
+ * 150 x 150 pixels), contract g_F on tensor cores in split BF16 (hi + lo,
+ * FP32 accumulation).  An emitter rejected as non-axisymmetric (workspace
+ * status) gets zero gradients. */
+int psf_bessel_vectorial_backward(const psf_optics* base, int n_emitters,
+                                  const double* depth, const double* zernike,
+                                  int n_zern, const float* phase_theta,
+                                  const int* z_offsets, const double* z,
+                                  int n_slices, int n_theta, int n_r, int nx,
+                                  int ny, double dx, double dy, int precision,
+                                  const float* target,
+                                  const float* grad_intensity, float* loss,
+                                  float* grad_phase_theta, float* grad_zernike,
+                                  float* grad_depth, void* workspace,
+                                  size_t ws_bytes, void* stream);
 
 /* ========================================================================== */
 /* Learned surrogate of the Bessel profiles (not in the paper; motivated by   */

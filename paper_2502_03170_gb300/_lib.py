@@ -88,8 +88,13 @@ PROTOTYPES = {
     "psf_surrogate_profiles": (_I, [_P, _OPT, _P, _I, _D, _I, _I, _I, _D, _D,
                                     _I, _P, ctypes.POINTER(_I), _P, _S, _P]),
     "psf_bessel_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I, _I]),
-    "psf_bessel_vectorial": (_I, [_OPT, _I, _P, _P, _I, _P, _P, _I, _I, _I,
-                                  _I, _I, _D, _D, _I, _P, _P, _P, _S, _P]),
+    "psf_bessel_vectorial": (_I, [_OPT, _I, _P, _P, _I, _P, _P, _P, _I, _I,
+                                  _I, _I, _I, _D, _D, _I, _P, _P, _P, _S, _P]),
+    "psf_bessel_backward_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I,
+                                                _I]),
+    "psf_bessel_vectorial_backward": (_I, [_OPT, _I, _P, _P, _I, _P, _P, _P,
+                                           _I, _I, _I, _I, _I, _D, _D, _I, _P,
+                                           _P, _P, _P, _P, _P, _P, _S, _P]),
 }
 
 _lib = None

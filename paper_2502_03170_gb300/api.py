@@ -128,34 +128,50 @@ def fourier(optics, n_pupil, grid, zernike=None, phase_map=None,
     return (I, F) if fields else I
 
 
+class _BesselArgs:
+    """Device copies of the per-emitter inputs of a Bessel call."""
+
+    def __init__(self, optics, depth, zernike, z_offsets, z, project, phase_theta):
+        flags = _lib.PSF_PROJECT_AXISYMMETRIC if project else 0
+        o = optics if isinstance(optics, PsfOptics) else make_optics(optics, flags)
+        if isinstance(optics, PsfOptics):
+            o.flags = flags
+        self.o = o
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+        def dv(a, dt):
+            if a is None:
+                return None
+            t = a if torch.is_tensor(a) else torch.as_tensor(np.asarray(a))
+            return t.detach().to(device=self.dev, dtype=dt).contiguous()
+
+        self.depth = dv(depth, torch.float64)
+        self.zern = dv(zernike, torch.float64)
+        self.offs = dv(z_offsets, torch.int32)
+        self.z = dv(z, torch.float64)
+        self.phase = dv(phase_theta, torch.float32)
+        self.n_em = self.depth.numel()
+        self.n_zern = 0 if self.zern is None else self.zern.shape[-1]
+        self.n_slices = int(self.z.numel())
+
+
 def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
            project=False, profiles=False, precision="fp32", workspace=None,
-           stream=None, intensity=True):
+           stream=None, intensity=True, phase_theta=None):
     """Batched vectorial PSFs by the Bessel strategy (Eq. 10-11).
 
     depth [n_em], zernike [n_em, n_zern], z_offsets [n_em + 1] (int32),
-    z [n_slices]: torch tensors on the device (or arrays, copied there).
+    z [n_slices]: torch tensors on the device (or arrays, copied there);
+    phase_theta [n_em, n_theta] (optional): free radial phase at the
+    Gauss-Legendre nodes, radians.
     Returns intensity [n_slices, nx, ny] (and profiles [n_slices, 3, n_r]).
     """
     lib = _lib.load()
-    flags = _lib.PSF_PROJECT_AXISYMMETRIC if project else 0
-    o = optics if isinstance(optics, PsfOptics) else make_optics(optics, flags)
-    if isinstance(optics, PsfOptics):
-        o.flags = flags
+    a = _BesselArgs(optics, depth, zernike, z_offsets, z, project, phase_theta)
+    o, dev = a.o, a.dev
     prec = PRECISIONS[precision] if isinstance(precision, str) else precision
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    def dv(a, dt):
-        t = a if torch.is_tensor(a) else torch.as_tensor(np.asarray(a))
-        return t.to(device=dev, dtype=dt).contiguous()
-
-    depth_d = dv(depth, torch.float64)
-    zern_d = dv(zernike, torch.float64) if zernike is not None else None
-    offs_d = dv(z_offsets, torch.int32)
-    z_d = dv(z, torch.float64)
-    n_em = depth_d.numel()
-    n_zern = 0 if zern_d is None else zern_d.shape[-1]
-    n_slices = int(z_d.numel())
+    depth_d, zern_d, offs_d, z_d = a.depth, a.zern, a.offs, a.z
+    n_em, n_zern, n_slices = a.n_em, a.n_zern, a.n_slices
     ws = workspace or Workspace(dev)
     need = lib.psf_bessel_workspace_size(ctypes.byref(o), n_em, n_slices,
                                          n_theta, n_r, nx, ny, prec)
@@ -168,9 +184,49 @@ def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
                     device=dev) if profiles else None
     check(lib, lib.psf_bessel_vectorial(
         ctypes.byref(o), n_em, _ptr(depth_d), _ptr(zern_d), n_zern,
-        _ptr(offs_d), _ptr(z_d), n_slices, n_theta, n_r, nx, ny, float(dx),
-        float(dy), prec, _ptr(I), _ptr(P), _ptr(buf), buf.numel(),
+        _ptr(a.phase), _ptr(offs_d), _ptr(z_d), n_slices, n_theta, n_r, nx, ny,
+        float(dx), float(dy), prec, _ptr(I), _ptr(P), _ptr(buf), buf.numel(),
         _stream(stream)))
     if not intensity:
         return P
     return (I, P) if profiles else I
+
+
+def bessel_backward(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx,
+                    dy, target=None, grad_intensity=None, project=False,
+                    phase_theta=None, precision="fp32", workspace=None, stream=None):
+    """Gradients of a Bessel-strategy z-stack loss (adjoint of Eq. 10-11).
+
+    With ``target`` [n_slices, nx, ny] the loss per emitter is sum (I - T)^2;
+    otherwise ``grad_intensity`` = dL/dI.  Returns a dict with ``loss`` [n_em]
+    (target only), ``grad_phase_theta`` [n_em, n_theta], ``grad_zernike``
+    [n_em, n_zern] (zero for m != 0 terms) and ``grad_depth`` [n_em].
+    ``precision`` selects the recomputation (and, for the split modes, the
+    tensor-core adjoint contraction)."""
+    lib = _lib.load()
+    a = _BesselArgs(optics, depth, zernike, z_offsets, z, project, phase_theta)
+    dev = a.dev
+    prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+    need = lib.psf_bessel_backward_workspace_size(
+        ctypes.byref(a.o), a.n_em, a.n_slices, n_theta, n_r, nx, ny, prec)
+    if need == 0:
+        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+    buf = (workspace or Workspace(dev)).get(need)
+
+    def f32(t):
+        if t is None:
+            return None
+        t = t if torch.is_tensor(t) else torch.as_tensor(np.asarray(t))
+        return t.detach().to(device=dev, dtype=torch.float32).contiguous()
+
+    T, G = f32(target), f32(grad_intensity)
+    loss = torch.empty(a.n_em, device=dev) if T is not None else None
+    gW = torch.empty((a.n_em, n_theta), device=dev)
+    gc = torch.empty((a.n_em, a.n_zern), device=dev) if a.n_zern else None
+    gd = torch.empty(a.n_em, device=dev)
+    check(lib, lib.psf_bessel_vectorial_backward(
+        ctypes.byref(a.o), a.n_em, _ptr(a.depth), _ptr(a.zern), a.n_zern,
+        _ptr(a.phase), _ptr(a.offs), _ptr(a.z), a.n_slices, n_theta, n_r, nx, ny,
+        float(dx), float(dy), prec, _ptr(T), _ptr(G), _ptr(loss), _ptr(gW), _ptr(gc),
+        _ptr(gd), _ptr(buf), buf.numel(), _stream(stream)))
+    return dict(loss=loss, grad_phase_theta=gW, grad_zernike=gc, grad_depth=gd)

@@ -1,8 +1,12 @@
-"""Differentiable Fourier-strategy PSF: torch.autograd.Function over the
-libpsf forward (Eq. 8) and its hand-written adjoint.
+"""Differentiable PSFs: torch.autograd.Functions over the libpsf forwards
+(Eq. 8, Eq. 10-11) and their hand-written adjoints.
 
-Gradients flow to the pupil phase map W_0 and to the Zernike coefficients of
-Eq. 15; the backward recomputes each z-plane instead of storing pupil fields.
+Fourier strategy: gradients flow to the pupil phase map W_0 and to the
+Zernike coefficients of Eq. 15; the backward recomputes each z-plane instead
+of storing pupil fields.  Bessel strategy: gradients flow to a free radial
+phase W_0(theta) at the Gauss-Legendre nodes, the m = 0 Zernike coefficients
+and the emitter depths (Eq. 13-14); the backward recomputes the radial
+profiles.
 """
 import ctypes
 
@@ -90,3 +94,35 @@ class FourierPSF(torch.autograd.Function):
 
 def fourier_psf(phase_map, zernike, optics, n_pupil, grid, precision="fp32"):
     return FourierPSF.apply(phase_map, zernike, optics, n_pupil, grid, precision)
+
+
+class BesselPSF(torch.autograd.Function):
+    """I = psf(depth, c, W_0(theta)) for batched emitters (packed slices);
+    differentiable in all three."""
+
+    @staticmethod
+    def forward(ctx, depth, zernike, phase_theta, optics, z_offsets, z, n_theta,
+                n_r, nx, ny, dx, dy):
+        I = api.bessel(optics, depth.detach(), zernike.detach(), z_offsets, z,
+                       n_theta, n_r, nx, ny, dx, dy, project=True,
+                       phase_theta=phase_theta.detach())
+        ctx.save_for_backward(depth, zernike, phase_theta)
+        ctx.cfg = (optics, z_offsets, z, n_theta, n_r, nx, ny, dx, dy)
+        return I
+
+    @staticmethod
+    def backward(ctx, grad_I):
+        depth, zernike, phase_theta = ctx.saved_tensors
+        optics, z_offsets, z, n_theta, n_r, nx, ny, dx, dy = ctx.cfg
+        g = api.bessel_backward(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx,
+                                ny, dx, dy, grad_intensity=grad_I.contiguous(),
+                                project=True, phase_theta=phase_theta)
+        return (g["grad_depth"].to(depth.dtype), g["grad_zernike"].to(zernike.dtype),
+                g["grad_phase_theta"].to(phase_theta.dtype),
+                None, None, None, None, None, None, None, None, None)
+
+
+def bessel_psf(depth, zernike, phase_theta, optics, z_offsets, z, n_theta, n_r, nx, ny,
+               dx, dy):
+    return BesselPSF.apply(depth, zernike, phase_theta, optics, z_offsets, z, n_theta,
+                           n_r, nx, ny, dx, dy)

@@ -42,7 +42,8 @@ void launch_bessel_jmat(const BesselParams& p, ThetaTable t, float* Bt,
 
 // ---------------------------------------------------------------------------
 // Per-emitter integrand F0(theta) = A(theta) e^{i W_e(theta)} (Eq. 12):
-// W_e = W_GL(t_s = depth[e]) + sum over m = 0 Noll terms c_{e,j} Z_j.
+// W_e = W_GL(t_s = depth[e]) + sum over m = 0 Noll terms c_{e,j} Z_j
+//       (+ the free radial phase W_0[e][j] at the node, when given).
 // FP64 phase, reduced mod one cycle.  Thread (e, j); j == 0 also checks that
 // no m != 0 coefficient is set (the spherical form needs an axisymmetric
 // pupil, Sec. 3.4) unless projection was requested.
@@ -50,6 +51,7 @@ void launch_bessel_jmat(const BesselParams& p, ThetaTable t, float* Bt,
 __global__ void k_bessel_emitters(BesselParams p, ThetaTable t,
                                   const double* __restrict__ depth,
                                   const double* __restrict__ zern,
+                                  const float* __restrict__ w0,
                                   EmitterTable et, int* status,
                                   unsigned* amp_max) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -61,6 +63,7 @@ __global__ void k_bessel_emitters(BesselParams p, ThetaTable t,
   double wz = 0.0;
   for (int q = 0; q < p.n_m0; ++q)
     wz += zern[(size_t)e * p.n_zern + p.m0_j[q] - 1] * t.zm0[q * p.n_theta + j];
+  if (w0) wz += (double)w0[idx];
   w += wz * (0.5 / kPi);
   w -= rint(w);
   double amp = t.amp0[j];
@@ -85,11 +88,11 @@ __global__ void k_bessel_emitters(BesselParams p, ThetaTable t,
 
 void launch_bessel_emitters(const BesselParams& p, ThetaTable t,
                             const double* depth, const double* zern,
-                            EmitterTable e, int* status, unsigned* amp_max,
-                            cudaStream_t s) {
+                            const float* w0, EmitterTable e, int* status,
+                            unsigned* amp_max, cudaStream_t s) {
   const long long n = (long long)p.n_em * p.n_theta;
   k_bessel_emitters<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, t, depth,
-                                                                 zern, e, status,
+                                                                 zern, w0, e, status,
                                                                  amp_max);
 }
 

@@ -50,11 +50,12 @@ struct EmitterTable {
 
 void launch_bessel_jmat(const BesselParams& p, ThetaTable t, float* Bt,
                         cudaStream_t s);
+// w0 (nullable): free radial phase [n_em][n_theta] in radians.
 // amp_max (nullable): running maximum of the amplitudes (float bits).
 void launch_bessel_emitters(const BesselParams& p, ThetaTable t,
                             const double* depth, const double* zern,
-                            EmitterTable e, int* status, unsigned* amp_max,
-                            cudaStream_t s);
+                            const float* w0, EmitterTable e, int* status,
+                            unsigned* amp_max, cudaStream_t s);
 void launch_slice_map(const BesselParams& p, const int* z_offsets,
                       const double* z, int* slice_em, float2* zz, int* status,
                       cudaStream_t s);

@@ -8,6 +8,7 @@
 
 #include <vector>
 
+#include "bessel_backward.cuh"
 #include "bessel_kernels.cuh"
 #include "fourier_kernels.cuh"
 #include "tc_kernels.cuh"
@@ -565,15 +566,15 @@ struct BesselLayout {
 
 static BesselLayout bessel_layout(void* ws, int n_em, int n_slices, int n_theta,
                                   int n_r, int nx, int ny, bool own_profiles,
-                                  int precision) {
+                                  int precision, bool fp32_bt = false) {
   BesselLayout L;
   memset(&L, 0, sizeof(L));
   Carver c(ws);
   L.theta_tab = c.take<double>((size_t)(10 + kMaxM0) * n_theta);
   L.kappa = c.take<float>(2 * (size_t)n_theta);
-  if (precision == PSF_PREC_FP32)
+  if (precision == PSF_PREC_FP32 || fp32_bt)
     L.Bt = c.take<float>((size_t)3 * n_r * n_theta);
-  else
+  if (precision != PSF_PREC_FP32)
     tc_bessel_carve(c.base, &c.off, n_theta, n_r, n_slices, &L.tc);
   L.et.amp = c.take<float>((size_t)n_em * n_theta);
   L.et.wfr = c.take<float>((size_t)n_em * n_theta);
@@ -613,31 +614,23 @@ extern "C" size_t psf_bessel_workspace_size(const psf_optics* base, int n_em,
                        precision).bytes;
 }
 
-extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
-                                    const double* depth, const double* zernike,
-                                    int n_zern, const int* z_offsets,
-                                    const double* z, int n_slices, int n_theta,
-                                    int n_r, int nx, int ny, double dx,
-                                    double dy, int precision, float* intensity,
-                                    void* profiles, void* workspace,
-                                    size_t ws_bytes, void* stream) {
-  g_err[0] = 0;
-  int r = check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision);
-  if (r) return r;
-  if (!finite_pos(dx) || !finite_pos(dy)) return fail(PSF_ERR_ARG, "pixel pitch must be > 0");
-  if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
-  if (!depth || !z_offsets || (n_slices > 0 && !z) || (n_zern > 0 && !zernike))
-    return fail(PSF_ERR_ARG, "depth / z_offsets / z / zernike pointer is NULL");
-  if (!intensity && !profiles && n_slices > 0)
-    return fail(PSF_ERR_ARG, "intensity and profiles are both NULL");
-  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
-  BesselLayout L = bessel_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
-                                 profiles == nullptr, precision);
-  if (ws_bytes < L.bytes)
-    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
-  if (profiles) L.prof = (float2*)profiles;
-  cudaStream_t s = (cudaStream_t)stream;
+// Host-side tables of one Bessel call and the setup launches shared by the
+// forward and the adjoint: per-theta FP64 table, J_n operand, per-emitter
+// integrand table, slice map and pixel table.
+struct BesselRun {
+  BesselParams bp;
+  ThetaTable tt;
+  double max_w;
+  bool split;
+};
 
+static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
+                          const double* zernike, int n_zern, const float* phase_theta,
+                          const int* z_offsets, const double* z, int n_slices,
+                          int n_theta, int n_r, int nx, int ny, double dx, double dy,
+                          int precision, bool fp32_operand, BesselLayout& L,
+                          void* workspace, BesselRun* R, cudaStream_t s) {
+  int r;
   // Per-theta FP64 table: GL nodes on [0, theta_max]; W_GL affine in t_s.
   const double s_max = base->NA / base->n_i;
   const double th_max = asin(s_max);
@@ -656,7 +649,7 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   double* T_amp = T_bim + n_theta;
   double* T_zm0 = T_amp + 2 * n_theta;   // slot 9 unused (alignment)
   const GLLayers L0 = gl_layers(base, 0.0), L1 = gl_layers(base, 1.0);
-  BesselParams bp;
+  BesselParams& bp = R->bp;
   memset(&bp, 0, sizeof(bp));
   int m0_j[kMaxM0], n_m0 = 0;
   unsigned long long mask[2] = {0, 0};
@@ -711,7 +704,7 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
     kap[j] = kv.hi;
     kap[n_theta + j] = kv.lo;
   }
-  ThetaTable tt;
+  ThetaTable& tt = R->tt;
   tt.theta = L.theta_tab;
   tt.w = L.theta_tab + n_theta;
   tt.sin_t = tt.w + n_theta;
@@ -751,9 +744,11 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
                   cudaMemcpyHostToDevice, s);
   if ((r = cuda_check("workspace init"))) return r;
 
-  const bool split = precision != PSF_PREC_FP32;
+  R->split = !fp32_operand && precision != PSF_PREC_FP32;
+  const bool split = R->split;
   double max_w = 0.0;
   for (int j = 0; j < n_theta; ++j) max_w = fmax(max_w, T_w[j]);
+  R->max_w = max_w;
   {
     TimingScope ts(kTimeSetup, s);
     if (split)
@@ -764,8 +759,8 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   if (split) cudaMemsetAsync(L.tc.amp_max, 0, sizeof(unsigned), s);
   {
     TimingScope ts(kTimeSetup, s);
-    launch_bessel_emitters(bp, tt, depth, n_zern > 0 ? zernike : nullptr, L.et,
-                           (int*)workspace, split ? L.tc.amp_max : nullptr, s);
+    launch_bessel_emitters(bp, tt, depth, n_zern > 0 ? zernike : nullptr, phase_theta,
+                           L.et, (int*)workspace, split ? L.tc.amp_max : nullptr, s);
   }
   if (n_slices > 0) {
     // slices no emitter claims keep emitter -1 and are skipped
@@ -778,31 +773,300 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
       TimingScope ts(kTimeSetup, s);
       launch_pixel_table(bp, L.pix_i0, L.pix_f, L.pix_g, s);
     }
-    if (split) {
-      r = tc_bessel_contract(bp, tt, L.et, L.slice_em, L.zz, max_w, precision, L.tc,
+  }
+  return cuda_check("Bessel setup launch");
+}
+
+static int check_bessel_call(const psf_optics* base, int n_em, const double* depth,
+                             const double* zernike, int n_zern, const int* z_offsets,
+                             const double* z, int n_slices, int n_theta, int n_r, int nx,
+                             int ny, double dx, double dy, int precision) {
+  int r = check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision);
+  if (r) return r;
+  if (!finite_pos(dx) || !finite_pos(dy)) return fail(PSF_ERR_ARG, "pixel pitch must be > 0");
+  if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
+  if (!depth || !z_offsets || (n_slices > 0 && !z) || (n_zern > 0 && !zernike))
+    return fail(PSF_ERR_ARG, "depth / z_offsets / z / zernike pointer is NULL");
+  return PSF_OK;
+}
+
+extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
+                                    const double* depth, const double* zernike,
+                                    int n_zern, const float* phase_theta,
+                                    const int* z_offsets, const double* z, int n_slices,
+                                    int n_theta, int n_r, int nx, int ny, double dx,
+                                    double dy, int precision, float* intensity,
+                                    void* profiles, void* workspace,
+                                    size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
+                            n_theta, n_r, nx, ny, dx, dy, precision);
+  if (r) return r;
+  if (!intensity && !profiles && n_slices > 0)
+    return fail(PSF_ERR_ARG, "intensity and profiles are both NULL");
+  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
+  BesselLayout L = bessel_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
+                                 profiles == nullptr, precision);
+  if (ws_bytes < L.bytes)
+    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
+  if (profiles) L.prof = (float2*)profiles;
+  cudaStream_t s = (cudaStream_t)stream;
+  BesselRun R;
+  r = bessel_prepare(base, n_em, depth, zernike, n_zern, phase_theta, z_offsets, z,
+                     n_slices, n_theta, n_r, nx, ny, dx, dy, precision, false, L,
+                     workspace, &R, s);
+  if (r) return r;
+  const BesselParams& bp = R.bp;
+  if (n_slices > 0) {
+    if (R.split) {
+      r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, precision, L.tc,
                              L.prof, (int*)workspace, s);
       if (r) return fail(r, "split-precision Bessel contraction launch failed");
     } else {
       TimingScope ts(kTimeBesselRadial, s);
-      launch_bessel_profiles_f32(bp, tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
+      launch_bessel_profiles_f32(bp, R.tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
     }
-    {
-      if (!intensity) {
-        // profiles only: no radial -> Cartesian epilogue
-      } else if (bessel_mirror_fit(nx, ny, n_r) && ((uintptr_t)intensity & 15) == 0) {
-        {
-          TimingScope ts(kTimeSetup, s);
-          launch_quarter_table(bp, L.qtab, s);
-        }
-        TimingScope ts(kTimeBesselEpilogue, s);
-        launch_bessel_intensity_mirror(bp, L.prof, L.slice_em, L.et.valid, L.qtab,
-                                       intensity, s);
-      } else {
-        TimingScope ts(kTimeBesselEpilogue, s);
-        launch_bessel_intensity(bp, L.prof, L.slice_em, L.et.valid, L.pix_i0,
-                                L.pix_f, L.pix_g, intensity, s);
+    if (!intensity) {
+      // profiles only: no radial -> Cartesian epilogue
+    } else if (bessel_mirror_fit(nx, ny, n_r) && ((uintptr_t)intensity & 15) == 0) {
+      {
+        TimingScope ts(kTimeSetup, s);
+        launch_quarter_table(bp, L.qtab, s);
       }
+      TimingScope ts(kTimeBesselEpilogue, s);
+      launch_bessel_intensity_mirror(bp, L.prof, L.slice_em, L.et.valid, L.qtab,
+                                     intensity, s);
+    } else {
+      TimingScope ts(kTimeBesselEpilogue, s);
+      launch_bessel_intensity(bp, L.prof, L.slice_em, L.et.valid, L.pix_i0,
+                              L.pix_f, L.pix_g, intensity, s);
     }
   }
   return cuda_check("psf_bessel_vectorial launch");
+}
+
+// ---------------------------------------------------------------------------
+// Bessel adjoint
+// ---------------------------------------------------------------------------
+struct BesselBwdLayout {
+  BesselLayout fwd;      // forward tables + FP32 J_n operand + own profiles
+  float2* gF;            // [n_slices][n_theta]
+  float* loss_slice;     // [n_slices]
+  PixGroup* groups;      // [n_groups], cell-sorted
+  int* cell_start;       // [n_r]
+  int2* gpc;             // [n_groups] natural order: (sorted position, cell)
+  float4* gfg;           // [n_groups] natural order: (f, gc, gs, 0)
+  float* sorted_f;       // [n_groups]
+  bool sorted_form;      // two-pass epilogue + tensor-core contraction
+  TcBesselAdj tc;
+  size_t bytes;
+};
+
+static size_t n_pix_groups(int nx, int ny) {
+  return (size_t)((nx + 1) / 2) * (size_t)((ny + 1) / 2);
+}
+
+static BesselBwdLayout bessel_bwd_layout(void* ws, int n_em, int n_slices, int n_theta,
+                                         int n_r, int nx, int ny, int precision) {
+  BesselBwdLayout B;
+  memset(&B, 0, sizeof(B));
+  B.fwd = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, true, precision, true);
+  Carver c(ws);
+  c.off = B.fwd.bytes;
+  B.gF = c.take<float2>((size_t)n_slices * n_theta);
+  B.loss_slice = c.take<float>((size_t)n_slices + 1);
+  B.groups = c.take<PixGroup>(n_pix_groups(nx, ny));
+  B.cell_start = c.take<int>((size_t)n_r);
+  B.gpc = c.take<int2>(n_pix_groups(nx, ny));
+  B.gfg = c.take<float4>(n_pix_groups(nx, ny));
+  B.sorted_f = c.take<float>(n_pix_groups(nx, ny));
+  BesselParams q;
+  memset(&q, 0, sizeof(q));
+  q.nx = nx;
+  q.ny = ny;
+  q.n_r = n_r;
+  B.sorted_form = bessel_adj_sorted_fits(q);
+  if (B.sorted_form && precision != PSF_PREC_FP32)
+    tc_bessel_adj_carve(c.base, &c.off, n_theta, n_r, n_slices, &B.tc);
+  B.bytes = align_up(c.off, 256);
+  return B;
+}
+
+// Pixels grouped by shared radius (a pixel and its mirrors), sorted by
+// interpolation cell with a stable counting sort: the adjoint visits every
+// cell's pixels in this fixed order.  FP64 geometry, same rule as the forward
+// pixel table.
+struct PixTables {
+  std::vector<PixGroup> sorted;    // cell-sorted groups
+  std::vector<int> start;          // [n_r]
+  std::vector<int2> pc;            // natural order: (sorted position, cell)
+  std::vector<float4> fg;          // natural order: (f, gc, gs, 0)
+  std::vector<float> sorted_f;
+};
+
+static void build_pix_groups(int nx, int ny, double dx, double dy, int n_r, double dr,
+                             const double* pol, PixTables& T) {
+  std::vector<PixGroup>& out = T.sorted;
+  std::vector<int>& start = T.start;
+  const int ha = (nx + 1) / 2, hb = (ny + 1) / 2;
+  const double S1 = pol[0] * pol[0] + pol[1] * pol[1] - pol[2] * pol[2] - pol[3] * pol[3];
+  const double S2 = 2.0 * (pol[0] * pol[2] + pol[1] * pol[3]);
+  std::vector<PixGroup> g((size_t)ha * hb);
+  std::vector<int> count(n_r, 0);
+  for (int a = 0; a < ha; ++a)
+    for (int b = 0; b < hb; ++b) {
+      PixGroup& q = g[(size_t)a * hb + b];
+      const double x = (a - 0.5 * (nx - 1)) * dx;
+      const double y = (b - 0.5 * (ny - 1)) * dy;
+      const double rho = sqrt(x * x + y * y);
+      const double tt = dr > 0 ? rho / dr : 0.0;
+      int c = (int)floor(tt);
+      c = c < 0 ? 0 : (c > n_r - 2 ? n_r - 2 : c);
+      q.cell = c;
+      q.f = (float)(tt - c);
+      double c2 = 1.0, s2 = 0.0;
+      if (rho > 0) {
+        c2 = (x * x - y * y) / (rho * rho);
+        s2 = 2.0 * x * y / (rho * rho);
+      }
+      q.gc = (float)(S1 * c2);
+      q.gs = (float)(S2 * s2);
+      const int a2 = nx - 1 - a, b2 = ny - 1 - b;
+      q.pix[0] = a * ny + b;
+      q.pix[1] = a2 != a ? a2 * ny + b : -1;
+      q.pix[2] = b2 != b ? a * ny + b2 : -1;
+      q.pix[3] = (a2 != a && b2 != b) ? a2 * ny + b2 : -1;
+      ++count[c];
+    }
+  start.assign(n_r, 0);
+  for (int c = 1; c < n_r; ++c) start[c] = start[c - 1] + count[c - 1];
+  out.resize(g.size());
+  T.pc.resize(g.size());
+  T.fg.resize(g.size());
+  T.sorted_f.resize(g.size());
+  std::vector<int> pos(start.begin(), start.end());
+  for (size_t i = 0; i < g.size(); ++i) {
+    const PixGroup& q = g[i];
+    const int k = pos[q.cell]++;
+    out[k] = q;
+    T.pc[i] = make_int2(k, q.cell);
+    T.fg[i] = make_float4(q.f, q.gc, q.gs, 0.f);
+    T.sorted_f[k] = q.f;
+  }
+}
+
+extern "C" size_t psf_bessel_backward_workspace_size(const psf_optics* base, int n_em,
+                                                     int n_slices, int n_theta, int n_r,
+                                                     int nx, int ny, int precision) {
+  if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
+  if (nx > 4096 || ny > 4096 || n_r > 4096) return 0;
+  return bessel_bwd_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, precision).bytes;
+}
+
+extern "C" int psf_bessel_vectorial_backward(
+    const psf_optics* base, int n_em, const double* depth, const double* zernike,
+    int n_zern, const float* phase_theta, const int* z_offsets, const double* z,
+    int n_slices, int n_theta, int n_r, int nx, int ny, double dx, double dy,
+    int precision, const float* target, const float* grad_intensity, float* loss,
+    float* grad_phase_theta, float* grad_zernike, float* grad_depth, void* workspace,
+    size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
+                            n_theta, n_r, nx, ny, dx, dy, precision);
+  if (r) return r;
+  if (nx > 4096 || ny > 4096)
+    return fail(PSF_ERR_ARG, "the Bessel adjoint takes nx, ny <= 4096");
+  if (n_slices > 0 && !target && !grad_intensity)
+    return fail(PSF_ERR_ARG, "target and grad_intensity are both NULL");
+  if (loss && !target) return fail(PSF_ERR_ARG, "loss needs a target");
+  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
+  BesselBwdLayout B = bessel_bwd_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
+                                        precision);
+  if (ws_bytes < B.bytes)
+    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, B.bytes);
+  BesselLayout& L = B.fwd;
+  cudaStream_t s = (cudaStream_t)stream;
+  BesselRun R;
+  r = bessel_prepare(base, n_em, depth, zernike, n_zern, phase_theta, z_offsets, z,
+                     n_slices, n_theta, n_r, nx, ny, dx, dy, precision, false, L, workspace,
+                     &R, s);
+  if (r) return r;
+  const BesselParams& bp = R.bp;
+  const bool split = R.split;
+  if (split) {
+    // the adjoint contraction takes the J_n operand unscaled in FP32 as well
+    TimingScope ts(kTimeSetup, s);
+    launch_bessel_jmat(bp, R.tt, L.Bt, s);
+  }
+  if (n_slices > 0) {
+    PixTables pt;
+    build_pix_groups(nx, ny, dx, dy, n_r, bp.dr, bp.pol, pt);
+    const size_t ng = pt.sorted.size();
+    const bool sorted_form = B.sorted_form;
+    const bool tc_adj = sorted_form && split;
+    if (sorted_form) {
+      cudaMemcpyAsync(B.gpc, pt.pc.data(), ng * sizeof(int2), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(B.gfg, pt.fg.data(), ng * sizeof(float4), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(B.sorted_f, pt.sorted_f.data(), ng * sizeof(float),
+                      cudaMemcpyHostToDevice, s);
+    } else {
+      cudaMemcpyAsync(B.groups, pt.sorted.data(), ng * sizeof(PixGroup),
+                      cudaMemcpyHostToDevice, s);
+    }
+    cudaMemcpyAsync(B.cell_start, pt.start.data(), pt.start.size() * sizeof(int),
+                    cudaMemcpyHostToDevice, s);
+    // recompute the profiles (per-z recomputation: nothing of the forward is stored)
+    if (split) {
+      r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, precision, L.tc,
+                             L.prof, (int*)workspace, s);
+      if (r) return fail(r, "split-precision Bessel contraction launch failed");
+    } else {
+      TimingScope ts(kTimeBesselRadial, s);
+      launch_bessel_profiles_f32(bp, R.tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
+    }
+    {
+      TimingScope ts(kTimeAdjoint, s);
+      const float* src = target ? target : grad_intensity;
+      const bool staged = sorted_form && bessel_adj_staged_fits(bp, src);
+      if (tc_adj) {
+        if (staged)
+          launch_bessel_adj_epilogue_staged(bp, L.prof, L.slice_em, L.et.valid, B.gpc, B.gfg,
+                                            B.sorted_f, B.cell_start, target,
+                                            target ? nullptr : grad_intensity, B.loss_slice,
+                                            B.tc.G_hi, B.tc.G_lo, B.tc.kp, (int*)workspace,
+                                            s);
+        else
+          launch_bessel_adj_epilogue_sorted(bp, L.prof, L.slice_em, L.et.valid, B.gpc,
+                                            B.gfg, B.sorted_f, B.cell_start, target,
+                                            target ? nullptr : grad_intensity, B.loss_slice,
+                                            B.tc.G_hi, B.tc.G_lo, B.tc.kp, s);
+        r = tc_bessel_adj_contract(bp, L.Bt, B.tc, B.gF, (int*)workspace, s);
+        if (r) return fail(r, "tensor-core adjoint contraction launch failed");
+      } else if (sorted_form) {
+        if (staged)
+          launch_bessel_adj_epilogue_staged(bp, L.prof, L.slice_em, L.et.valid, B.gpc, B.gfg,
+                                            B.sorted_f, B.cell_start, target,
+                                            target ? nullptr : grad_intensity, B.loss_slice,
+                                            nullptr, nullptr, 0, (int*)workspace, s);
+        else
+          launch_bessel_adj_epilogue_sorted(bp, L.prof, L.slice_em, L.et.valid, B.gpc,
+                                            B.gfg, B.sorted_f, B.cell_start, target,
+                                            target ? nullptr : grad_intensity, B.loss_slice,
+                                            nullptr, nullptr, 0, s);
+        launch_bessel_adj_contract(bp, L.Bt, L.prof, B.gF, s);
+      } else {
+        launch_bessel_adj_epilogue(bp, L.prof, L.slice_em, L.et.valid, B.groups,
+                                   B.cell_start, target, target ? nullptr : grad_intensity,
+                                   B.loss_slice, s);
+        launch_bessel_adj_contract(bp, L.Bt, L.prof, B.gF, s);
+      }
+    }
+  }
+  {
+    TimingScope ts(kTimeAdjoint, s);
+    launch_bessel_adj_reduce(bp, R.tt, L.et, z_offsets, L.zz, B.gF,
+                             (target && n_slices > 0) ? B.loss_slice : nullptr, loss,
+                             grad_phase_theta, grad_zernike, grad_depth, s);
+  }
+  return cuda_check("psf_bessel_vectorial_backward launch");
 }

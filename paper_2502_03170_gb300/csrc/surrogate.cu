@@ -138,7 +138,7 @@ extern "C" int psf_surrogate_profiles(const void* state, const psf_optics* base,
                                                   L.z);
     psf_optics o = *base;
     o.flags |= PSF_PROJECT_AXISYMMETRIC;
-    r = psf_bessel_vectorial(&o, h, L.depth, L.zern, 21, L.offs, L.z, h, n_theta, kNR, nx,
+    r = psf_bessel_vectorial(&o, h, L.depth, L.zern, 21, nullptr, L.offs, L.z, h, n_theta, kNR, nx,
                              ny, dx, dy, precision, nullptr, L.prof, L.bessel, L.bessel_ws,
                              stream);
     if (r) return r;

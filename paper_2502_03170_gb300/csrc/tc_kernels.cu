@@ -789,9 +789,87 @@ __global__ void k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable e
   lo[r1] = l;
 }
 
+// Adjoint operand: A[j][row] = Bt[j][row] (FP32 J_n operand, theta-major)
+// split into BF16 hi + lo with row pitch kp (columns >= rows zero); thread 0
+// also stores the unit output scale of the contraction.
+__global__ void k_bessel_adj_bt_split(const float* __restrict__ Bt, int n_theta, int rows,
+                                      int kp, uint16_t* hi, uint16_t* lo, float* scale) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx == 0) *scale = 1.f;
+  if (idx >= (long long)n_theta * kp) return;
+  const int j = (int)(idx / kp), q = (int)(idx - (long long)j * kp);
+  const float v = q < rows ? Bt[(size_t)j * rows + q] : 0.f;
+  uint16_t h, l;
+  split16(v, 1, h, l);
+  hi[idx] = h;
+  lo[idx] = l;
+}
+
 }  // namespace tc
 
 int tc_bessel_kp(int n_theta) { return (n_theta + 7) / 8 * 8; }
+
+void tc_bessel_adj_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
+                         TcBesselAdj* out) {
+  auto take = [&](size_t bytes) -> char* {
+    *off = align_up(*off, 1024);
+    char* p = base ? base + *off : nullptr;
+    *off += bytes;
+    return p;
+  };
+  out->kp = tc_bessel_kp(3 * n_r);
+  const size_t kp = out->kp;
+  out->A_hi = (uint16_t*)take((size_t)n_theta * kp * 2);
+  out->A_lo = (uint16_t*)take((size_t)n_theta * kp * 2);
+  out->G_hi = (uint16_t*)take(2 * (size_t)n_slices * kp * 2 + 2);
+  out->G_lo = (uint16_t*)take(2 * (size_t)n_slices * kp * 2 + 2);
+  out->scale = (float*)take(sizeof(float));
+}
+
+int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesselAdj& ops,
+                           float2* gF, int* status, cudaStream_t s) {
+  using namespace tc;
+  const int rows = 3 * p.n_r, kp = ops.kp;
+  {
+    const long long n = (long long)p.n_theta * kp;
+    k_bessel_adj_bt_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        Bt, p.n_theta, rows, kp, ops.A_hi, ops.A_lo, ops.scale);
+  }
+  // K extent = 3 N_r (columns past it read as zero), row pitch kp
+  auto map2 = [&](CUtensorMap* m, const uint16_t* base, int nrows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)nrows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void*)base, dims, strides, box,
+              es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              SWZ == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  CUtensorMap mAh, mAl, mGh, mGl;
+  if (!(map2(&mAh, ops.A_hi, p.n_theta, BM) && map2(&mAl, ops.A_lo, p.n_theta, BM) &&
+        map2(&mGh, ops.G_hi, 2 * p.n_slices, BN) && map2(&mGl, ops.G_lo, 2 * p.n_slices, BN)))
+    return PSF_ERR_CUDA;
+  Params q;
+  memset(&q, 0, sizeof(q));
+  q.planes = 1;
+  q.m_tiles = ceil_div(p.n_theta, BM);
+  q.n_tiles = ceil_div(2 * p.n_slices, BN);
+  q.k_chunks = ceil_div(rows, BK);
+  q.idesc = make_idesc(1);
+  q.mode = 2;
+  q.bf16 = 1;
+  q.prof = gF;                 // gF[s][j]: "rows" of this contraction are theta nodes
+  q.rows_total = p.n_theta;
+  q.n_slices = p.n_slices;
+  q.scale_ptr = ops.scale;
+  q.m_fastest = 1;
+  q.status = status;
+  return launch_gemm(mAh, mAl, mGh, mGl, q, s);
+}
 
 void tc_bessel_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
                      TcBessel* out) {

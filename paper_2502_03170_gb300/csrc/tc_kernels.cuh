@@ -39,6 +39,21 @@ int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
                        int precision, const TcBessel& ops, float2* prof,
                        int* status, cudaStream_t s);
 
+// Split-precision operands of the Bessel adjoint contraction
+//   g_F[s][j] = sum_row Bt[j][row] g_P[s][row]   (real Bt, complex g_P):
+// A rows j x K columns (3 N_r, pitch kp), g_P rows (s, re/im), BF16 hi + lo.
+struct TcBesselAdj {
+  int kp;
+  uint16_t *A_hi, *A_lo;     // [n_theta][kp]
+  uint16_t *G_hi, *G_lo;     // [2 n_slices][kp]
+  float* scale;              // device 1.0 (BF16 needs no pre-scaling)
+};
+void tc_bessel_adj_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
+                         TcBesselAdj* out);
+// A operand from the FP32 J_n operand, then the contraction into gF.
+int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesselAdj& ops,
+                           float2* gF, int* status, cudaStream_t s);
+
 struct TcOperands {
   uint16_t *Ax_hi, *Ax_lo;   // [2 nx][2 N] zoom-matrix blocks
   uint16_t *Ay_hi, *Ay_lo;   // [2 ny][2 N]

@@ -80,6 +80,16 @@ PSF_D void mbar_drain_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// Contiguous global -> shared copy on the TMA engine (addresses 16-byte
+// aligned, bytes a multiple of 16), completing on mbarrier `bar`.
+PSF_D void bulk_load_1d(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"((uint64_t)src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 PSF_D void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                        uint32_t bar) {
   asm volatile(

@@ -10,6 +10,8 @@ the device), then exits.  Cases:
   Zernike (one z-chunk of the benchmark stack).
 * ``bessel``   - 256 emitters of the batched Bessel workload (about 600 MB
   of output, above the 126 MB L2).
+* ``bessel_backward`` - the adjoint of the same 256 emitters with a seeded
+  dL/dI (about 600 MB of input).
 """
 import argparse
 
@@ -22,7 +24,7 @@ from . import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fourier", "bessel"])
+    ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward"])
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--nz", type=int, default=16)
     args = ap.parse_args()
@@ -37,6 +39,20 @@ def main():
                         precision=args.precision, out=out, workspace=ws)
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
+    elif args.case == "bessel_backward":
+        c = W.bessel(n_emitters=256)
+        n_sl = int(c["z_offsets"][-1])
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(7)
+        G = torch.randn((n_sl, c["nx"], c["ny"]), device="cuda", generator=gen)
+        for _ in range(2):
+            r = api.bessel_backward(c["optics"], c["depth"], c["zernike"],
+                                    c["z_offsets"], c["z"], c["n_theta"], c["n_r"],
+                                    c["nx"], c["ny"], c["dx"], c["dy"],
+                                    grad_intensity=G, project=True,
+                                    precision=args.precision)
+        torch.cuda.synchronize()
+        assert torch.isfinite(r["grad_phase_theta"]).all()
     else:
         c = W.bessel(n_emitters=256)
         for _ in range(2):

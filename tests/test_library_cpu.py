@@ -81,11 +81,30 @@ def test_host_validation(cpu_lib):
                                              8, 0) == 0
     assert cpu_lib.psf_bessel_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
                                              8, 8, 0) > 0
-    r = cpu_lib.psf_bessel_vectorial(ctypes.byref(o), 4, None, None, 0, None,
+    r = cpu_lib.psf_bessel_vectorial(ctypes.byref(o), 4, None, None, 0, None, None,
                                      None, 16, 64, 64, 8, 8, 0.02, 0.02, 0,
                                      ctypes.c_void_p(16), None,
                                      ctypes.c_void_p(256), 1 << 30, None)
     assert r == _lib.PSF_ERR_ARG
+    # Bessel backward: precision modes, grid limit, needs a target or dL/dI
+    assert cpu_lib.psf_bessel_backward_workspace_size(ctypes.byref(o), 4, 16, 64,
+                                                      64, 8, 8, 0) > 0
+    assert cpu_lib.psf_bessel_backward_workspace_size(ctypes.byref(o), 4, 16, 64,
+                                                      64, 8, 8, 1) > 0
+    assert cpu_lib.psf_bessel_backward_workspace_size(ctypes.byref(o), 4, 16, 64,
+                                                      64, 8, 8, 7) == 0
+    assert cpu_lib.psf_bessel_backward_workspace_size(ctypes.byref(o), 4, 16, 64,
+                                                      64, 8192, 8, 0) == 0
+    d = ctypes.c_void_p(16)
+    args = [ctypes.byref(o), 4, d, None, 0, None, d, d, 16, 64, 64, 8, 8, 0.02,
+            0.02]
+    tail = [ctypes.c_void_p(256), 1 << 30, None]
+    assert cpu_lib.psf_bessel_vectorial_backward(
+        *args, 7, d, None, None, None, None, None, *tail) == _lib.PSF_ERR_PRECISION
+    assert cpu_lib.psf_bessel_vectorial_backward(
+        *args, 0, None, None, None, None, None, None, *tail) == _lib.PSF_ERR_ARG
+    assert cpu_lib.psf_bessel_vectorial_backward(
+        *args, 0, None, d, d, None, None, None, *tail) == _lib.PSF_ERR_ARG   # loss w/o target
     # backward: needs a target or an upstream gradient
     r = cpu_lib.psf_fourier_vectorial_backward(
         ctypes.byref(o), 16, ctypes.byref(g.c), 1, None, 0, None, 0, None,
