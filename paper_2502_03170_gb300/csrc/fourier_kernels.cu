@@ -412,39 +412,84 @@ void launch_grad_accum(const float2* Gh, const float2* P, float* gW, int NN,
   k_grad_accum<<<ceil_div(NN, 256), 256, 0, s>>>(Gh, P, gW, NN, nzc);
 }
 
-__global__ void k_zernike_grad(ZernBasis zb, int N, const float* __restrict__ gW,
-                               float* grad_c) {
-  __shared__ double red[256];
-  const int j = blockIdx.x;            // 0-based Noll index - 1
+// Zernike basis on the pupil nodes, once per call: Zt[j][p][q] = Z_{j+1}(u_p, v_q)
+// (Eq. 15).  FP64 radial polynomial; cos(m phi) and sin(m phi) are the real
+// and imaginary parts of ((u + i v) / rho)^m, so no trigonometric call.
+__global__ void k_zernike_table(ZernBasis zb, int N, float* __restrict__ Zt) {
+  const long long NN = (long long)N * N;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)zb.n_zern * NN) return;
+  const int j = (int)(idx / NN);
+  const int i = (int)(idx - (long long)j * NN);
+  const int ip = i / N, iq = i - (i / N) * N;
   const int m = zb.m[j], am = m < 0 ? -m : m;
-  double acc = 0.0;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const float g = gW[idx];
-    if (g == 0.f) continue;
-    const int ip = idx / N, iq = idx - (idx / N) * N;
-    const double u = (double)(2 * ip + 1 - N) / N, v = (double)(2 * iq + 1 - N) / N;
-    const double rn = sqrt(u * u + v * v);
-    double r = 0.0;
-    for (int k = 10; k >= 0; --k) r = r * rn + zb.rc[j][k];
-    double ang = 1.0;
-    if (am > 0) {
-      const double phi = atan2(v, u);
-      ang = m > 0 ? cos(am * phi) : sin(am * phi);
+  const double u = (double)(2 * ip + 1 - N) / N, v = (double)(2 * iq + 1 - N) / N;
+  const double rn = sqrt(u * u + v * v);
+  double r = 0.0;
+  for (int k = kZernMaxOrder; k >= 0; --k) r = r * rn + zb.rc[j][k];
+  double ang = 1.0;
+  if (am > 0 && rn == 0.0) {
+    ang = 0.0;                                    // odd N: the centre node
+  } else if (am > 0) {
+    const double c = u / rn, sn = v / rn;
+    double cr = 1.0, ci = 0.0;
+    for (int k = 0; k < am; ++k) {
+      const double t = cr * c - ci * sn;
+      ci = cr * sn + ci * c;
+      cr = t;
     }
-    acc += r * ang * (double)g;
+    ang = m > 0 ? cr : ci;
   }
+  Zt[idx] = (float)(r * ang);
+}
+
+void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s) {
+  const long long n = (long long)zb.n_zern * N * N;
+  if (n > 0) k_zernike_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(zb, N, Zt);
+}
+
+// dL/dc_j = sum_{p,q} Z_j[p][q] dL/dW_0[p][q] for `nb` pupils at once: CTA
+// (j, k, part) sums its contiguous 1/kZgParts of the nodes in FP64 (fixed
+// order), then one thread per (k, j) adds the parts in order.
+constexpr int kZgParts = 16;
+
+__global__ void k_zernike_grad_part(const float* __restrict__ Zt, int NN,
+                                    const float* __restrict__ gW, double* part) {
+  __shared__ double red[256];
+  const int j = blockIdx.x, k = blockIdx.y, sp = blockIdx.z;
+  const int i0 = (int)((long long)NN * sp / kZgParts), i1 = (int)((long long)NN * (sp + 1) / kZgParts);
+  const float* z = Zt + (size_t)j * NN;
+  const float* g = gW + (size_t)k * NN;
+  double acc = 0.0;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += (double)z[i] * (double)g[i];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int st = 128; st > 0; st >>= 1) {
     if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) grad_c[j] = (float)red[0];
+  if (threadIdx.x == 0) part[((size_t)k * gridDim.x + j) * kZgParts + sp] = red[0];
 }
 
-void launch_zernike_grad(const ZernBasis& zb, int N, const float* gW,
-                         float* grad_c, cudaStream_t s) {
-  if (zb.n_zern > 0) k_zernike_grad<<<zb.n_zern, 256, 0, s>>>(zb, N, gW, grad_c);
+__global__ void k_zernike_grad_fin(const double* __restrict__ part, int n_zern, int nb,
+                                   float* grad_c) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_zern * nb) return;
+  double v = 0.0;
+  for (int sp = 0; sp < kZgParts; ++sp) v += part[(size_t)t * kZgParts + sp];
+  grad_c[t] = (float)v;          // t = k * n_zern + j
+}
+
+size_t zernike_grad_part_bytes(int n_zern, int nb) {
+  return (size_t)n_zern * nb * kZgParts * sizeof(double);
+}
+
+void launch_zernike_grad(const ZernBasis& zb, int N, const float* Zt, const float* gW,
+                         int nb, double* part, float* grad_c, cudaStream_t s) {
+  if (zb.n_zern <= 0 || nb <= 0) return;
+  k_zernike_grad_part<<<dim3(zb.n_zern, nb, kZgParts), 256, 0, s>>>(Zt, N * N, gW, part);
+  k_zernike_grad_fin<<<ceil_div(zb.n_zern * nb, 128), 128, 0, s>>>(part, zb.n_zern, nb,
+                                                                   grad_c);
 }
 
 __global__ void k_sum_partials(const float* __restrict__ part, int n, float* out) {

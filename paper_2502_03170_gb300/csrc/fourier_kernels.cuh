@@ -99,15 +99,20 @@ int stage2_tiles(int nx, int ny);
 void launch_grad_accum(const float2* Gh, const float2* P, float* gW, int NN,
                        int nzc, cudaStream_t s);
 
-// grad_c[j-1] = sum_{p,q} Z_j[p][q] gW[p][q] (fixed-order reduction),
-// Z_j on the pupil grid in FP64 from per-j radial coefficients.
+// Zernike basis of the pupil grid and the chain rule of Eq. 15:
+// Zt[j][p][q] = Z_{j+1}(u_p, v_q) (FP64 evaluation, once per call), then
+// grad_c[j] = sum_{p,q} Zt[j][p][q] gW[p][q] (fixed-order reduction).
 struct ZernBasis {
   int n_zern;
   int m[66];                    // signed azimuthal order (Noll)
   double rc[66][11];            // radial coefficients (normalised)
 };
-void launch_zernike_grad(const ZernBasis& zb, int N, const float* gW,
-                         float* grad_c, cudaStream_t s);
+void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s);
+// nb pupils: gW [nb][N][N] -> grad_c [nb][n_zern]; part: scratch of
+// zernike_grad_part_bytes(n_zern, nb) bytes.
+size_t zernike_grad_part_bytes(int n_zern, int nb);
+void launch_zernike_grad(const ZernBasis& zb, int N, const float* Zt, const float* gW,
+                         int nb, double* part, float* grad_c, cudaStream_t s);
 
 // loss = sum of partials[0..n) in fixed order.
 void launch_sum_partials(const float* part, int n, float* out, cudaStream_t s);

@@ -406,19 +406,32 @@ struct BackwardLayout {
   float* gW;
   float* loss_part;
   int zc, n_part;
+  TcBwdOperands tc;      // split-precision path
+  float* Zt;             // [n_zern][N][N] Zernike basis (once per call)
+  double* zpart;         // partial sums of the Zernike gradient
   size_t bytes;
 };
 
-static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g) {
+static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g,
+                                      int precision = PSF_PREC_FP32, int n_zern = 66) {
   BackwardLayout L;
   memset(&L, 0, sizeof(L));
   Carver c(ws);
   const size_t NN = (size_t)N * N;
+  L.Zt = c.take<float>((size_t)n_zern * NN);
   L.nodes.amp = c.take<float>(6 * NN);
   L.nodes.wfr = c.take<float>(NN);
   L.nodes.kh = c.take<float>(NN);
   L.nodes.kl = c.take<float>(NN);
   L.zz = c.take<float2>(g->nz);
+  if (precision != PSF_PREC_FP32) {
+    L.zc = tc_fourier_bwd_zchunk(N, g->nx, g->ny, g->nz);
+    tc_fourier_bwd_carve(c.base, &c.off, N, g->nx, g->ny, g->nz, L.zc, &L.tc);
+    L.zpart = (double*)c.take<char>(zernike_grad_part_bytes(n_zern, L.tc.group));
+    L.bytes = align_up(c.off, 256);
+    return L;
+  }
+  L.zpart = (double*)c.take<char>(zernike_grad_part_bytes(n_zern, 1));
   // per-z: P, Gh [3][N][N], U [3][ny][N], RT [3][ny][nx], V [3][N][ny]
   const double per_z = 3.0 * 8.0 * (2.0 * NN + 2.0 * g->ny * N + (double)g->ny * g->nx);
   int zc = (int)(96.0 * 1048576.0 / per_z);
@@ -459,8 +472,9 @@ extern "C" size_t psf_fourier_backward_workspace_size(const psf_optics* opt,
                                                        const psf_grid* grid,
                                                        int precision) {
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
-  if (precision != PSF_PREC_FP32) return 0;
-  return backward_layout(nullptr, n_pupil, grid).bytes;
+  if (precision != PSF_PREC_FP32 && tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
+    return 0;
+  return backward_layout(nullptr, n_pupil, grid, precision).bytes;
 }
 
 extern "C" int psf_fourier_vectorial_backward(
@@ -472,8 +486,10 @@ extern "C" int psf_fourier_vectorial_backward(
   g_err[0] = 0;
   int r = check_fourier_args(opt, n_pupil, grid, precision);
   if (r) return r;
-  if (precision != PSF_PREC_FP32)
-    return fail(PSF_ERR_PRECISION, "backward supports PSF_PREC_FP32");
+  if (precision != PSF_PREC_FP32) {
+    if (const char* why = tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
+      return fail(PSF_ERR_ARG, "%s", why);
+  }
   if (batch < 1) return fail(PSF_ERR_ARG, "batch must be >= 1");
   if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
   if (n_zern > 0 && !zernike) return fail(PSF_ERR_ARG, "zernike is NULL");
@@ -486,7 +502,7 @@ extern "C" int psf_fourier_vectorial_backward(
     return fail(PSF_ERR_ARG, "no output requested");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   const int N = n_pupil;
-  BackwardLayout L = backward_layout(workspace, N, grid);
+  BackwardLayout L = backward_layout(workspace, N, grid, precision);   // sized for 66 terms
   if (ws_bytes < L.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
   cudaStream_t s = (cudaStream_t)stream;
@@ -504,11 +520,49 @@ extern "C" int psf_fourier_vectorial_backward(
   const double f = opt->NA / opt->lambda;
   const double ds = 2.0 * (opt->NA / opt->n_i) / N;
   const float scale = (float)(ds * ds / (2.0 * kPi));
+  if (precision != PSF_PREC_FP32) {
+    // tensor-core adjoint (split precision), one pupil at a time
+    const ZernBasis zb = zernike_basis(n_zern);
+    {
+      TimingScope ts(kTimeSetup, s);
+      if ((r = tc_fourier_bwd_setup(L.tc, N, nx, ny, grid->dx, grid->dy, f, precision, s)))
+        return fail(r, "split-precision adjoint setup failed");
+      if (grad_zernike) launch_zernike_table(zb, N, L.Zt, s);
+    }
+    // groups of pupils share one pass over their planes (flat over (pupil, z))
+    const int gp = L.tc.group;
+    double amp_bound = 0.0;
+    for (int b0 = 0; b0 < batch; b0 += gp) {
+      const int nb = batch - b0 < gp ? batch - b0 : gp;
+      for (int k = 0; k < nb; ++k) {
+        const int b = b0 + k;
+        NodeParams np = node_params(opt, N, zernike ? zernike + (size_t)b * n_zern : nullptr,
+                                    n_zern, phase_map ? phase_map + (size_t)b * NN : nullptr);
+        if (b == 0) amp_bound = tc_pupil_amplitude_bound(np);   // phase-independent
+        NodeTable t = L.nodes;
+        t.wfr = L.tc.wfr + (size_t)k * NN;
+        TimingScope ts(kTimeSetup, s);
+        launch_node_table(np, t, s);
+      }
+      const float* Tb = target ? target + (size_t)b0 * vox : nullptr;
+      const float* Gb = grad_intensity ? grad_intensity + (size_t)b0 * vox : nullptr;
+      float* gWb = grad_phase_map ? grad_phase_map + (size_t)b0 * NN : L.tc.gW;
+      r = tc_fourier_backward(L.tc, L.nodes, L.zz, N, nx, ny, nz, nb, L.zc, scale, amp_bound,
+                              precision, Tb, Gb, gWb, loss ? loss + b0 : nullptr,
+                              (int*)workspace, s);
+      if (r) return fail(r, "split-precision adjoint launch failed");
+      if (grad_zernike)
+        launch_zernike_grad(zb, N, L.Zt, gWb, nb, L.zpart, grad_zernike + (size_t)b0 * n_zern,
+                            s);
+    }
+    return cuda_check("psf_fourier_vectorial_backward launch");
+  }
   launch_twiddle(N, nx, grid->dx, f, L.Ax, s);
   launch_twiddle(N, ny, grid->dy, f, L.Ay, s);
   launch_twiddle_adj(N, nx, grid->dx, f, L.AxH, s);
   launch_twiddle_adj(N, ny, grid->dy, f, L.AyH, s);
   const ZernBasis zb = zernike_basis(n_zern);
+  if (grad_zernike) launch_zernike_table(zb, N, L.Zt, s);
   const int tiles = stage2_tiles(nx, ny);
 
   for (int b = 0; b < batch; ++b) {
@@ -540,7 +594,8 @@ extern "C" int psf_fourier_vectorial_backward(
     if (grad_phase_map)
       cudaMemcpyAsync(grad_phase_map + (size_t)b * NN, L.gW, NN * sizeof(float),
                       cudaMemcpyDeviceToDevice, s);
-    if (grad_zernike) launch_zernike_grad(zb, N, L.gW, grad_zernike + (size_t)b * n_zern, s);
+    if (grad_zernike)
+      launch_zernike_grad(zb, N, L.Zt, L.gW, 1, L.zpart, grad_zernike + (size_t)b * n_zern, s);
   }
   return cuda_check("psf_fourier_vectorial_backward launch");
 }

@@ -76,6 +76,15 @@ struct Params {
   int n_slices;
   const float* scale_ptr;   // device scalar: 1 / (S_B S_F)
   int m_fastest;        // tile order: consecutive tiles share the B tile
+  // mode 3 (adjoint source, stage-2 recomputation): g = 2 (I - T) or dL/dI,
+  // R = g E written transposed as BF16 hi/lo rows (c, b), columns [Re a | Im a]
+  const float* T;       // [planes][nx][ny] (offset to the chunk) or null
+  const float* Gin;     // [planes][nx][ny] or null
+  float* loss_part;     // [planes * m_tiles * n_tiles * 4] or null
+  uint16_t* R_hi;
+  uint16_t* R_lo;
+  // mode 4 (adjoint stage 2): Gh stored as FP32 gWz[plane][c][re/im][p][q]
+  float* gWz;
 };
 
 // Tile index -> (plane, m-tile, n-tile).
@@ -271,6 +280,98 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
             }
           }
         }
+      } else if (p.mode == 3) {
+        // adjoint source: I from the three channels, g = 2 (I - T) or dL/dI,
+        // R_c = g E_c with E = out_scale (D_im - i D_re); the lane holding D_re
+        // writes Im R, the lane holding D_im writes Re R (no exchange needed)
+        float sq[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sq[j] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float v = __uint_as_float(r[j]);
+              sq[h * 32 + j] = fmaf(v, v, sq[h * 32 + j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], 1);
+        const float sc2 = p.out_scale * p.out_scale;
+        const int bb0 = nt * BOUT + part * 32;      // this lane's 32 outputs along b
+        const bool row_ok = mo < p.nx;
+        float g[32];
+        float lsum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int bb = bb0 + j;
+          float gv = 0.f;
+          if (row_ok && bb < p.ny) {
+            const float I = sc2 * (part ? sq[32 + j] : sq[j]);
+            const size_t pix = ((size_t)plane * p.nx + mo) * p.ny + bb;
+            if (p.T) {
+              const float d = I - p.T[pix];
+              lsum = fmaf(d, d, lsum);
+              gv = 2.f * d;
+            } else {
+              gv = p.Gin[pix];
+            }
+          }
+          g[j] = gv;
+        }
+        float go[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) go[j] = __shfl_xor_sync(0xffffffffu, g[j], 1);
+        const float sgn = part ? p.out_scale : -p.out_scale;
+        const size_t col = (size_t)(part ? 0 : p.nx) + mo;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+            if (!row_ok) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int bb = nt * BOUT + h * 32 + j;
+              if (bb >= p.ny) continue;
+              // outputs h * 32 + j: the lane's own g for h == part, else the partner's
+              const float gj = (h == part) ? g[j] : go[j];
+              uint16_t hh, ll;
+              split16(sgn * gj * __uint_as_float(r[j]), 1, hh, ll);
+              const size_t o = ((size_t)(plane * 3 + c) * p.ny + bb) * (size_t)(2 * p.nx) + col;
+              p.R_hi[o] = hh;
+              p.R_lo[o] = ll;
+            }
+          }
+        }
+        if (p.loss_part) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+          if (lane == 0) p.loss_part[(size_t)t * 4 + quad] = lsum;
+        }
+      } else if (p.mode == 4) {
+        // Gh: this lane holds Re (part 0) or Im (part 1) of Gh_c[p][q = mo] for
+        // 64 p; stored as FP32 Ghf[plane][c][part][p][q] (stores only: the
+        // pupil fields are folded in by a separate coalesced pass)
+        const bool q_ok = mo < p.m_out;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+            if (!q_ok) continue;
+            float* dst = p.gWz + (((size_t)(plane * 3 + c) * 2 + part) * p.n_rows) * p.m_out + mo;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int pp = nt * BOUT + h * 32 + j;
+              if (pp < p.n_rows) dst[(size_t)pp * p.m_out] = __uint_as_float(r[j]);
+            }
+          }
+        }
       } else if (p.mode == 0) {
         // stage 1: U[plane][c][b = mo][part * N + p] = split(out_scale * D)
         const bool row_ok = mo < p.m_out;
@@ -411,21 +512,103 @@ __global__ void k_twiddle_split(int N, int n_out, double alpha, float sA, int bf
   hi[im + pp] = h;  lo[im + pp] = l;           // (i, im): Im A
 }
 
+// Adjoint zoom-matrix blocks (BF16 hi + lo, unscaled): rows (q, re/im) over
+// the pupil index, columns [Re | Im] over the output index b,
+//   A'[q][b] = conj(A[b][q]) = exp(-2 pi i f u_q x_b),
+// the same exact integer angle as k_twiddle_split with the roles swapped.
+__global__ void k_twiddle_adj_split(int N, int n_out, double alpha, uint16_t* hi,
+                                    uint16_t* lo) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_out * N) return;
+  const int q = idx / n_out, bo = idx - (idx / n_out) * n_out;
+  const long long mn = (long long)(2 * q + 1 - N) * (long long)(2 * bo + 1 - n_out);
+  double cyc = -alpha * (double)mn;
+  cyc -= rint(cyc);
+  float sn, cs;
+  sincospif(2.0f * (float)cyc, &sn, &cs);
+  const size_t K = 2 * (size_t)n_out;
+  const size_t re = (size_t)(2 * q) * K, im = re + K;
+  uint16_t h, l;
+  split16(cs, 1, h, l);
+  hi[re + bo] = h;  lo[re + bo] = l;               // (q, re): Re A'
+  hi[im + n_out + bo] = h;  lo[im + n_out + bo] = l;   // (q, im): Re A'
+  split16(-sn, 1, h, l);
+  hi[re + n_out + bo] = h;  lo[re + n_out + bo] = l;   // (q, re): -Im A'
+  split16(sn, 1, h, l);
+  hi[im + bo] = h;  lo[im + bo] = l;               // (q, im): Im A'
+}
+
+// Phase gradient of a chunk: for node (p, q) and each flat plane of the chunk
+// (planes p0 .. p0 + planes over (pupil, z), nz_per per pupil)
+//   2 s Re(conj(Gh_c) P_c) summed over c = scale * (Gh_re P_re + Gh_im P_im),
+// with P = (hi + lo) / S_P from the split pupil planes, summed into gW[pupil]
+// in plane order (a pupil's first plane starts its sum).  One thread per
+// (pupil of the chunk, node).
+__global__ void k_gw_fold(const float* __restrict__ Ghf, const uint16_t* __restrict__ P_hi,
+                          const uint16_t* __restrict__ P_lo, int p_bf16, int N, int p0,
+                          int planes, int nz_per, float scale, float* gW) {
+  const int NN = N * N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NN) return;
+  const int pk = p0 / nz_per + (int)blockIdx.y;           // pupil of this thread
+  const int a = max(pk * nz_per - p0, 0), b = min((pk + 1) * nz_per - p0, planes);
+  if (a >= b) return;
+  const int ip = i / N, iq = i - (i / N) * N;
+  float* dst = gW + (size_t)pk * NN + i;
+  float v = (p0 + a - pk * nz_per == 0) ? 0.f : *dst;
+#pragma unroll 4
+  for (int pl = a; pl < b; ++pl) {
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t gb = ((size_t)(pl * 3 + c) * 2) * NN + i;
+      const size_t pb = ((size_t)(pl * 3 + c) * N + ip) * (size_t)(2 * N) + iq;
+      const float pr = unsplit16(P_hi[pb], P_lo[pb], p_bf16);
+      const float pi = unsplit16(P_hi[pb + N], P_lo[pb + N], p_bf16);
+      acc = fmaf(Ghf[gb], pr, acc);
+      acc = fmaf(Ghf[gb + NN], pi, acc);
+    }
+    v = fmaf(scale, acc, v);
+  }
+  *dst = v;
+}
+
+// loss[k] = sum of the partials of pupil k (n_per each), FP64, fixed order.
+__global__ void k_loss_group(const float* __restrict__ part, int n_per, float* loss) {
+  __shared__ double red[256];
+  const float* pp = part + (size_t)blockIdx.x * n_per;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n_per; i += blockDim.x) acc += pp[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[blockIdx.x] = (float)red[0];
+}
+
 // Pupil fields of a z-chunk as split operand rows: P[zc][c][p][q] -> row
 // (zc, c, p), columns [Re q | Im q], scaled by S_P.  Four consecutive nodes
 // (same p, N % 4 == 0) per thread and one plane per grid row, 8-byte stores.
+// Planes are numbered flat over (pupil, z) with nz_per planes per pupil; the
+// phase table of pupil k is t.wfr + k * wfr_stride (the amplitude and defocus
+// tables are shared).  A single pupil passes wfr_stride = 0.
 __global__ void k_pupil_z_split(NodeTable t, int N, const float2* __restrict__ zz,
-                                int z0, int nzc, float sP, int bf16,
+                                int z0, int nzc, int nz_per, long long wfr_stride,
+                                float sP, int bf16,
                                 uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
   const int NN = N * N;
   const int idx4 = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx4 * 4 >= NN) return;
   const int idx = idx4 * 4;
   const int ip = idx / N, iq = idx - (idx / N) * N;
+  const int flat = z0 + (int)blockIdx.y;
+  const int pk = flat / nz_per, zi = flat - pk * nz_per;
   float4 a4[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) a4[c] = *(const float4*)(t.amp + (size_t)c * NN + idx);
-  const float4 w4 = *(const float4*)(t.wfr + idx);
+  const float4 w4 = *(const float4*)(t.wfr + (size_t)pk * wfr_stride + idx);
   const float4 kh4 = *(const float4*)(t.kh + idx);
   const float4 kl4 = *(const float4*)(t.kl + idx);
   const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -441,7 +624,7 @@ __global__ void k_pupil_z_split(NodeTable t, int N, const float2* __restrict__ z
   }
   {
     const int zc = blockIdx.y;                 // one plane per grid row
-    const float2 z = zz[z0 + zc];
+    const float2 z = zz[zi];
     float2 e[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -662,7 +845,7 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     {
       TimingScope ts(kTimePupil, s);
       const dim3 pg(ceil_div(N * N / 4, 128), nzc);
-      k_pupil_z_split<<<pg, 128, 0, s>>>(nodes, N, zz, z0, nzc, sP, bf16, ops.P_hi,
+      k_pupil_z_split<<<pg, 128, 0, s>>>(nodes, N, zz, z0, nzc, nz, 0, sP, bf16, ops.P_hi,
                                          ops.P_lo);
     }
     Params p1;
@@ -705,6 +888,209 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     if (r) return r;
   }
   return PSF_OK;
+}
+
+// ==========================================================================
+// Fourier adjoint on the split-precision path
+// ==========================================================================
+const char* tc_fourier_bwd_supported(int N, int nx, int ny) {
+  if (const char* why = tc_fourier_supported(N, nx, ny)) return why;
+  if (nx % 8 != 0 || ny % 8 != 0)
+    return "the split-precision adjoint needs nx and ny multiples of 8";
+  return nullptr;
+}
+
+static double tc_bwd_plane_bytes(int N, int nx, int ny) {
+  // P, U (input precision) + R, V (BF16), hi + lo, and gWz, per plane
+  return 3.0 * 2.0 * 2.0 * 2.0 *
+             ((double)N * N + (double)ny * N + (double)ny * nx + (double)N * ny) +
+         24.0 * N * N;
+}
+
+int tc_fourier_bwd_zchunk(int N, int nx, int ny, int nz) {
+  // up to 128 planes (several pupils when a stack is shorter) and ~2 GB, so a
+  // launch holds several waves of tiles
+  int zc = (int)(2048.0 * 1048576.0 / tc_bwd_plane_bytes(N, nx, ny));
+  if (zc < 1) zc = 1;
+  if (zc > 128) zc = 128;
+  return zc;
+}
+
+int tc_fourier_bwd_group(int nz, int zc) { return nz <= zc ? zc / nz : 1; }
+
+void tc_fourier_bwd_carve(char* base, size_t* off, int N, int nx, int ny, int nz, int zc,
+                          TcBwdOperands* out) {
+  auto take = [&](size_t bytes) -> char* {
+    *off = align_up(*off, 1024);
+    char* p = base ? base + *off : nullptr;
+    *off += bytes;
+    return p;
+  };
+  const int gp = tc_fourier_bwd_group(nz, zc);
+  tc_fourier_carve(base, off, N, nx, ny, zc, &out->fwd);
+  const size_t K2 = 2 * (size_t)N, NN = (size_t)N * N;
+  out->AxH_hi = (uint16_t*)take(K2 * 2 * nx * 2);
+  out->AxH_lo = (uint16_t*)take(K2 * 2 * nx * 2);
+  out->AyH_hi = (uint16_t*)take(K2 * 2 * ny * 2);
+  out->AyH_lo = (uint16_t*)take(K2 * 2 * ny * 2);
+  out->R_hi = (uint16_t*)take((size_t)zc * 3 * ny * 2 * nx * 2);
+  out->R_lo = (uint16_t*)take((size_t)zc * 3 * ny * 2 * nx * 2);
+  out->V_hi = (uint16_t*)take((size_t)zc * 3 * N * 2 * ny * 2);
+  out->V_lo = (uint16_t*)take((size_t)zc * 3 * N * 2 * ny * 2);
+  out->gWz = (float*)take((size_t)zc * 6 * NN * 4);
+  out->wfr = (float*)take((size_t)gp * NN * 4);
+  out->gW = (float*)take((size_t)gp * NN * 4);
+  const size_t parts = (size_t)gp * nz * ceil_div(nx, tc::BOUT) * ceil_div(ny, tc::BOUT) * 4;
+  out->loss_part = (float*)take(parts * 4);
+  out->group = gp;
+}
+
+int tc_fourier_bwd_setup(const TcBwdOperands& ops, int N, int nx, int ny, double dx,
+                         double dy, double na_over_lambda, int precision, cudaStream_t s) {
+  using namespace tc;
+  const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
+  const float sA = pow2_scale(1.0, 16384.0);
+  k_twiddle_split<<<ceil_div(nx * N, 256), 256, 0, s>>>(
+      N, nx, na_over_lambda * dx / (2.0 * N), sA, bf16, ops.fwd.Ax_hi, ops.fwd.Ax_lo);
+  k_twiddle_split<<<ceil_div(ny * N, 256), 256, 0, s>>>(
+      N, ny, na_over_lambda * dy / (2.0 * N), sA, bf16, ops.fwd.Ay_hi, ops.fwd.Ay_lo);
+  k_twiddle_adj_split<<<ceil_div(nx * N, 256), 256, 0, s>>>(
+      N, nx, na_over_lambda * dx / (2.0 * N), ops.AxH_hi, ops.AxH_lo);
+  k_twiddle_adj_split<<<ceil_div(ny * N, 256), 256, 0, s>>>(
+      N, ny, na_over_lambda * dy / (2.0 * N), ops.AyH_hi, ops.AyH_lo);
+  return cudaPeekAtLastError() == cudaSuccess ? PSF_OK : PSF_ERR_CUDA;
+}
+
+struct TcBwdMaps {
+  CUtensorMap Ax_h, Ax_l, Ay_h, Ay_l, P_h, P_l, U_h, U_l;
+  CUtensorMap AxH_h, AxH_l, AyH_h, AyH_l, R_h, R_l, V_h, V_l;
+};
+
+int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2* zz,
+                        int N, int nx, int ny, int nz, int n_pupils, int zc, float scale,
+                        double amp_bound, int precision, const float* target,
+                        const float* grad_intensity, float* gW, float* loss, int* status,
+                        cudaStream_t s) {
+  using namespace tc;
+  const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
+  const int K = 2 * N;
+  const double tgt = 16384.0;
+  const float sA = pow2_scale(1.0, tgt);
+  const float sP = pow2_scale(amp_bound, tgt);
+  const float sU = pow2_scale(amp_bound * N, tgt);
+  const TcOperands& f = ops.fwd;
+  static thread_local TcBwdMaps m;      // encoded per call (host work only)
+  bool ok = make_map_2d(&m.Ax_h, f.Ax_hi, K, 2 * nx, BM) &&
+            make_map_2d(&m.Ax_l, f.Ax_lo, K, 2 * nx, BM) &&
+            make_map_2d(&m.Ay_h, f.Ay_hi, K, 2 * ny, BM) &&
+            make_map_2d(&m.Ay_l, f.Ay_lo, K, 2 * ny, BM) &&
+            make_map_3d(&m.P_h, f.P_hi, K, N, 3 * zc) &&
+            make_map_3d(&m.P_l, f.P_lo, K, N, 3 * zc) &&
+            make_map_3d(&m.U_h, f.U_hi, K, ny, 3 * zc) &&
+            make_map_3d(&m.U_l, f.U_lo, K, ny, 3 * zc) &&
+            make_map_2d(&m.AxH_h, ops.AxH_hi, 2 * nx, 2 * N, BM) &&
+            make_map_2d(&m.AxH_l, ops.AxH_lo, 2 * nx, 2 * N, BM) &&
+            make_map_2d(&m.AyH_h, ops.AyH_hi, 2 * ny, 2 * N, BM) &&
+            make_map_2d(&m.AyH_l, ops.AyH_lo, 2 * ny, 2 * N, BM) &&
+            make_map_3d(&m.R_h, ops.R_hi, 2 * nx, ny, 3 * zc) &&
+            make_map_3d(&m.R_l, ops.R_lo, 2 * nx, ny, 3 * zc) &&
+            make_map_3d(&m.V_h, ops.V_hi, 2 * ny, N, 3 * zc) &&
+            make_map_3d(&m.V_l, ops.V_lo, 2 * ny, N, 3 * zc);
+  if (!ok) return PSF_ERR_CUDA;
+  const uint32_t idesc = make_idesc(bf16), idesc_b = make_idesc(1);
+  const int tiles2 = ceil_div(nx, BOUT) * ceil_div(ny, BOUT);
+  const int total = n_pupils * nz;                 // flat planes of this group
+  NodeTable tn = nodes;
+  tn.wfr = ops.wfr;
+  int r;
+  for (int z0 = 0; z0 < total; z0 += zc) {
+    const int nzc = total - z0 < zc ? total - z0 : zc;
+    {
+      TimingScope ts(kTimePupil, s);
+      const dim3 pg(ceil_div(N * N / 4, 128), nzc);
+      k_pupil_z_split<<<pg, 128, 0, s>>>(tn, N, zz, z0, nzc, nz, (long long)N * N, sP,
+                                         bf16, f.P_hi, f.P_lo);
+    }
+    Params p1;
+    memset(&p1, 0, sizeof(p1));
+    p1.planes = nzc;
+    p1.m_tiles = ceil_div(ny, BOUT);
+    p1.n_tiles = ceil_div(N, BOUT);
+    p1.k_chunks = ceil_div(K, BK);
+    p1.m_out = ny;
+    p1.n_rows = N;
+    p1.N = N;
+    p1.idesc = idesc;
+    p1.mode = 0;
+    p1.bf16 = bf16;
+    p1.out_scale = sU / (sA * sP);
+    p1.U_hi = f.U_hi;
+    p1.U_lo = f.U_lo;
+    p1.nx = nx;
+    p1.ny = ny;
+    p1.status = status;
+    {
+      TimingScope ts(kTimeStage1, s);
+      if ((r = launch_gemm(m.Ay_h, m.Ay_l, m.P_h, m.P_l, p1, s))) return r;
+    }
+    // stage 2 recomputed: I, loss partials and R^T (BF16)
+    Params p3 = p1;
+    p3.m_tiles = ceil_div(nx, BOUT);
+    p3.n_tiles = ceil_div(ny, BOUT);
+    p3.m_out = nx;
+    p3.n_rows = ny;
+    p3.mode = 3;
+    p3.out_scale = scale / (sA * sU);
+    const size_t zoff = (size_t)z0 * nx * ny;
+    p3.T = target ? target + zoff : nullptr;
+    p3.Gin = target ? nullptr : grad_intensity + zoff;
+    p3.loss_part = target ? ops.loss_part + (size_t)z0 * tiles2 * 4 : nullptr;
+    p3.R_hi = ops.R_hi;
+    p3.R_lo = ops.R_lo;
+    {
+      TimingScope ts(kTimeAdjoint, s);
+      if ((r = launch_gemm(m.Ax_h, m.Ax_l, m.U_h, m.U_l, p3, s))) return r;
+    }
+    // V[c][p][b] = sum_a conj(Ax[a][p]) R_c[a][b]   (split BF16, stored like U)
+    Params pv = p1;
+    pv.m_tiles = ceil_div(N, BOUT);
+    pv.n_tiles = ceil_div(ny, BOUT);
+    pv.k_chunks = ceil_div(2 * nx, BK);
+    pv.m_out = N;
+    pv.n_rows = ny;
+    pv.N = ny;
+    pv.idesc = idesc_b;
+    pv.bf16 = 1;
+    pv.out_scale = 1.f;
+    pv.U_hi = ops.V_hi;
+    pv.U_lo = ops.V_lo;
+    {
+      TimingScope ts(kTimeAdjoint, s);
+      if ((r = launch_gemm(m.AxH_h, m.AxH_l, m.R_h, m.R_l, pv, s))) return r;
+    }
+    // Gh^T[q][p] = sum_b conj(Ay[b][q]) V[p][b] -> Ghf; then 2 s Re(conj(Gh) P)
+    Params p4 = p1;
+    p4.m_tiles = ceil_div(N, BOUT);
+    p4.n_tiles = ceil_div(N, BOUT);
+    p4.k_chunks = ceil_div(2 * ny, BK);
+    p4.m_out = N;
+    p4.n_rows = N;
+    p4.N = N;
+    p4.idesc = idesc_b;
+    p4.bf16 = 1;
+    p4.mode = 4;
+    p4.gWz = ops.gWz;
+    {
+      TimingScope ts(kTimeAdjoint, s);
+      if ((r = launch_gemm(m.AyH_h, m.AyH_l, m.V_h, m.V_l, p4, s))) return r;
+      const int pk0 = z0 / nz, pk1 = (z0 + nzc - 1) / nz;
+      k_gw_fold<<<dim3(ceil_div(N * N, 256), pk1 - pk0 + 1), 256, 0, s>>>(
+          ops.gWz, f.P_hi, f.P_lo, bf16, N, z0, nzc, nz, 2.f * scale / sP, gW);
+    }
+  }
+  if (target && loss)
+    k_loss_group<<<n_pupils, 256, 0, s>>>(ops.loss_part, nz * tiles2 * 4, loss);
+  return cudaPeekAtLastError() == cudaSuccess ? PSF_OK : PSF_ERR_CUDA;
 }
 
 // ==========================================================================

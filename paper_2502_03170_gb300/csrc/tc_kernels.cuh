@@ -80,4 +80,38 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
                        double amp_bound, int precision, float* intensity,
                        float2* fields, int* status, cudaStream_t s);
 
+// Split-precision Fourier adjoint (tensor cores).  Per z-chunk: pupil fields,
+// stage 1, stage 2 recomputed with the adjoint source R = g E written as BF16
+// operand rows, V = A_x^H R, Gh = V conj(A_y), then the phase gradient
+// 2 s Re(conj(Gh) P) (s = ds^2 / 2 pi), summed over planes in order.
+struct TcBwdOperands {
+  TcOperands fwd;            // Ax, Ay, P, U (input precision)
+  uint16_t *AxH_hi, *AxH_lo; // [2 N][2 nx] conj(Ax)^T blocks, BF16
+  uint16_t *AyH_hi, *AyH_lo; // [2 N][2 ny]
+  uint16_t *R_hi, *R_lo;     // [zc][3][ny][2 nx]
+  uint16_t *V_hi, *V_lo;     // [zc][3][N][2 ny]
+  float* gWz;                // [zc][3][re/im][N][N] Gh of a chunk (FP32)
+  float* wfr;                // [group][N][N] phase tables of a group of pupils
+  float* gW;                 // [group][N][N] dL/dW_0 of the group
+  float* loss_part;          // [group * nz * tiles * 4]
+  int group;                 // pupils per group (planes of a chunk span pupils)
+};
+const char* tc_fourier_bwd_supported(int N, int nx, int ny);
+int tc_fourier_bwd_zchunk(int N, int nx, int ny, int nz);
+int tc_fourier_bwd_group(int nz, int zc);
+void tc_fourier_bwd_carve(char* base, size_t* off, int N, int nx, int ny, int nz, int zc,
+                          TcBwdOperands* out);
+// zoom matrices and their adjoints (once per call)
+int tc_fourier_bwd_setup(const TcBwdOperands& ops, int N, int nx, int ny, double dx,
+                         double dy, double na_over_lambda, int precision, cudaStream_t s);
+// n_pupils (<= group) pupils whose phase tables are in ops.wfr: planes are
+// flat over (pupil, z); gW[k][N][N] = dL/dW_0 of pupil k (overwritten);
+// loss[k] (target only).  target / grad_intensity point at the group's first
+// plane.
+int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2* zz,
+                        int N, int nx, int ny, int nz, int n_pupils, int zc, float scale,
+                        double amp_bound, int precision, const float* target,
+                        const float* grad_intensity, float* gW, float* loss, int* status,
+                        cudaStream_t s);
+
 }  // namespace psf

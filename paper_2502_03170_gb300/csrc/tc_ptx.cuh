@@ -154,6 +154,14 @@ PSF_D void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // Splits x into hi + lo of the 16-bit type; returns the two 16-bit patterns.
+// hi + lo back to FP32.
+PSF_D float unsplit16(uint16_t hi, uint16_t lo, int bf16) {
+  if (bf16)
+    return __bfloat162float(__ushort_as_bfloat16(hi)) +
+           __bfloat162float(__ushort_as_bfloat16(lo));
+  return __half2float(__ushort_as_half(hi)) + __half2float(__ushort_as_half(lo));
+}
+
 PSF_D void split16(float x, int bf16, uint16_t& hi, uint16_t& lo) {
   if (bf16) {
     const __nv_bfloat16 h = __float2bfloat16_rn(x);

@@ -12,6 +12,8 @@ the device), then exits.  Cases:
   of output, above the 126 MB L2).
 * ``bessel_backward`` - the adjoint of the same 256 emitters with a seeded
   dL/dI (about 600 MB of input).
+* ``fourier_backward`` - the phase-retrieval adjoint (256^2 pupil, 128^2 px,
+  32 planes) for ``--batch`` pupils against a seeded target.
 """
 import argparse
 
@@ -24,7 +26,9 @@ from . import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward"])
+    ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward",
+                                     "fourier_backward"])
+    ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--nz", type=int, default=16)
     args = ap.parse_args()
@@ -39,6 +43,21 @@ def main():
                         precision=args.precision, out=out, workspace=ws)
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
+    elif args.case == "fourier_backward":
+        from . import autograd
+        c = W.adjoint(batch=args.batch)
+        g = c["grid"]
+        nz, nx, ny = len(g["z"]), g["nx"], g["ny"]
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        T = 1e-3 * torch.rand((args.batch, nz, nx, ny), device="cuda", generator=gen)
+        zern = np.zeros((args.batch, 21))
+        for _ in range(2):
+            loss, gW, gc = autograd._backward_call(
+                c["optics"], c["n_pupil"], g, zern, None, target=T,
+                precision=args.precision)
+        torch.cuda.synchronize()
+        assert torch.isfinite(gW).all()
     elif args.case == "bessel_backward":
         c = W.bessel(n_emitters=256)
         n_sl = int(c["z_offsets"][-1])

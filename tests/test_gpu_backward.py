@@ -1,5 +1,8 @@
 """Adjoint of the Fourier strategy on the GPU against the FP64 oracle adjoint
-(gradients within 1e-4 relative L2) and finite differences."""
+(gradients within 1e-4 relative L2; the oracle adjoint is pinned by finite
+differences on the CPU).  FP32 contractions and the tensor-core split path
+(forward recomputed in split FP16 / BF16, adjoint contractions in split
+BF16)."""
 import ctypes
 
 import numpy as np
@@ -17,13 +20,17 @@ pytestmark = pytest.mark.gpu
 TOL_G = 1e-4
 
 
-def gpu_backward(d, N, grid, zern, pm, target=None, grad_I=None):
+PREC = {"fp32": 0, "split_fp16": 1, "split_bf16": 2}
+
+
+def gpu_backward(d, N, grid, zern, pm, target=None, grad_I=None, prec="fp32"):
     lib = _lib.load()
     o = api.make_optics(d)
     g = api.Grid(grid)
     batch = zern.shape[0]
     need = lib.psf_fourier_backward_workspace_size(ctypes.byref(o), N,
-                                                   ctypes.byref(g.c), 0)
+                                                   ctypes.byref(g.c), PREC[prec])
+    assert need > 0, lib.psf_last_error()
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
     pm_d = dev(pm)
@@ -36,7 +43,7 @@ def gpu_backward(d, N, grid, zern, pm, target=None, grad_I=None):
     p = lambda t: ctypes.c_void_p(0 if t is None else t.data_ptr())
     _lib.check(lib, lib.psf_fourier_vectorial_backward(
         ctypes.byref(o), N, ctypes.byref(g.c), batch,
-        zh.ctypes.data_as(ctypes.c_void_p), zern.shape[1], p(pm_d), 0, p(T),
+        zh.ctypes.data_as(ctypes.c_void_p), zern.shape[1], p(pm_d), PREC[prec], p(T),
         p(G), p(loss) if T is not None else None, p(gW), p(gc), p(ws),
         ws.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
     torch.cuda.synchronize()
@@ -85,3 +92,74 @@ def test_backward_upstream_gradient(lib):
     _, gWr, gcr, _ = oa.loss_and_grad(opt, N, grid, zern[0], pm[0], I - gI[0] / 2)
     assert rel_l2(gW[0], gWr) <= TOL_G
     assert rel_l2(gc[0], gcr) <= TOL_G
+
+
+@pytest.mark.parametrize("prec", ["split_fp16", "split_bf16"])
+@pytest.mark.parametrize("N,nx,ny,nz", [(32, 16, 24, 5), (48, 72, 64, 3)])
+def test_split_backward_matches_oracle(lib, N, nx, ny, nz, prec):
+    """Tensor-core adjoint: several m/n tiles with a ragged tail (72 = 64 + 8)."""
+    rng = np.random.default_rng(7 + N)
+    d = W.optics_gibson_lanni(1.0)
+    grid = dict(nx=nx, ny=ny, dx=0.03, dy=0.035, z=np.linspace(-0.5, 0.6, nz))
+    batch = 2
+    zern = np.zeros((batch, 21))
+    zern[:, 3:15] = rng.normal(0, 0.2, (batch, 12))
+    pm = np.where(pupil_mask(N), rng.normal(0, 0.3, (batch, N, N)), 0.0)
+    opt = oracle_optics(d)
+    refs, targets = [], []
+    for b in range(batch):
+        T = rng.uniform(0, 2e-4, (nz, nx, ny))
+        targets.append(T)
+        refs.append(oa.loss_and_grad(opt, N, grid, zern[b], pm[b], T))
+    loss, gW, gc = gpu_backward(d, N, grid, zern, pm, target=np.stack(targets), prec=prec)
+    loss2, gW2, gc2 = gpu_backward(d, N, grid, zern, pm, target=np.stack(targets), prec=prec)
+    assert np.array_equal(gW, gW2) and np.array_equal(loss, loss2)   # fixed order
+    for b in range(batch):
+        L, gWr, gcr, _ = refs[b]
+        assert abs(loss[b] - L) <= 1e-4 * abs(L)
+        assert rel_l2(gW[b], gWr) <= TOL_G
+        assert rel_l2(gc[b], gcr) <= TOL_G
+
+
+def test_split_backward_upstream_gradient(lib):
+    rng = np.random.default_rng(15)
+    N, nx, ny, nz = 32, 16, 16, 2
+    d = W.optics_plain()
+    grid = dict(nx=nx, ny=ny, dx=0.04, dy=0.04, z=[-0.3, 0.2])
+    zern = np.zeros((1, 21))
+    zern[0, 4:9] = rng.normal(0, 0.2, 5)
+    pm = np.where(pupil_mask(N), rng.normal(0, 0.3, (1, N, N)), 0.0)
+    gI = rng.normal(0, 1.0, (1, nz, nx, ny))
+    _, gW, gc = gpu_backward(d, N, grid, zern, pm, grad_I=gI, prec="split_fp16")
+    opt = oracle_optics(d)
+    from oracle import fourier as of
+    I = of.psf_fourier(opt, N, grid, zern[0], pm[0])
+    _, gWr, gcr, _ = oa.loss_and_grad(opt, N, grid, zern[0], pm[0], I - gI[0] / 2)
+    assert rel_l2(gW[0], gWr) <= TOL_G
+    assert rel_l2(gc[0], gcr) <= TOL_G
+
+
+def test_split_backward_adjoint_config_sampled(lib):
+    """The phase-retrieval workload (batch 64, 256^2 pupil, 128^2 px, 32
+    planes) in one split-FP16 call; two batch elements recomputed by the
+    oracle.  The target is the oracle PSF of the true phases with 1 % noise."""
+    c = W.adjoint()
+    N, grid, B = c["n_pupil"], c["grid"], c["batch"]
+    d = c["optics"]
+    opt = oracle_optics(d)
+    from oracle import fourier as of
+    rng = np.random.default_rng(c["noise_seed"])
+    sample = (0, 37)
+    nz, nx, ny = len(grid["z"]), grid["nx"], grid["ny"]
+    T = np.zeros((B, nz, nx, ny), dtype=np.float32)
+    for b in sample:
+        I = of.psf_fourier(opt, N, grid, c["c_true"][b], c["w_true"][b])
+        T[b] = I + rng.normal(0, 0.01 * I.max(), I.shape)
+    zern = np.zeros((B, 21))
+    pm = np.zeros((B, N, N))
+    loss, gW, gc = gpu_backward(d, N, grid, zern, pm, target=T, prec="split_fp16")
+    for b in sample:
+        L, gWr, gcr, _ = oa.loss_and_grad(opt, N, grid, zern[b], pm[b], T[b].astype(np.float64))
+        assert abs(loss[b] - L) <= 1e-4 * abs(L)
+        assert rel_l2(gW[b], gWr) <= TOL_G
+        assert rel_l2(gc[b], gcr) <= TOL_G
