@@ -20,7 +20,8 @@ from numpy.polynomial.legendre import leggauss
 from scipy.special import jv
 
 from .fourier import grid_coords
-from .optics import amplitude, gibson_lanni_phase, noll_to_nm, zernike_phase
+from .optics import (amplitude, fresnel_coefficients, gibson_lanni_phase, noll_to_nm,
+                     zernike_phase)
 
 C_BESSEL = -0.5j                     # -i f k / 2 with f k = 1 (Eq. 10)
 
@@ -82,6 +83,26 @@ def pupil_function(opt, theta, zernike=None, project=False, w0=None):
     return amplitude(opt, cos_t, sin_t) * np.exp(1j * w)
 
 
+def angular_weights(opt, sin_t, cos_t):
+    """g_0, g_1, g_2 of Eq. 11 for the model: q_s = q_p = 1 (the printed
+    form); with Fresnel coefficients the phi integrals of Eq. 6 give
+    g_0 = sin (q_s + q_p cos), g_1 = q_p sin^2, g_2 = sin (q_p cos - q_s);
+    the scalar model (Eq. 5) is carried by g_0 = 2 sin (so that
+    E_x = -(i/2) I_0 is Eq. 5 with x polarisation), g_1 = g_2 = 0."""
+    if opt.scalar:
+        z = 0.0 * sin_t
+        return (2.0 * sin_t, z, z)
+    if opt.fresnel:
+        qs, qp = fresnel_coefficients(opt, sin_t)
+        return (sin_t * (qs + qp * cos_t), qp * sin_t * sin_t, sin_t * (qp * cos_t - qs))
+    return (sin_t * (1.0 + cos_t), sin_t * sin_t, sin_t * (cos_t - 1.0))
+
+
+def model_pol(opt):
+    """Jones vector the spherical form uses (x for the scalar model)."""
+    return (1.0 + 0j, 0j) if opt.scalar else opt.pol
+
+
 def profiles(opt, n_theta, r, zs, zernike=None, project=False, rule="gl",
              w0=None):
     """I_n(r_i, z) of Eq. 11 for n = 0, 1, 2 -> complex array [nz, 3, len(r)]."""
@@ -92,7 +113,7 @@ def profiles(opt, n_theta, r, zs, zernike=None, project=False, rule="gl",
     else:
         th, wt = riemann_rule(n_theta, opt.theta_max)
     sin_t, cos_t = np.sin(th), np.cos(th)
-    g = (sin_t * (1.0 + cos_t), sin_t * sin_t, sin_t * (cos_t - 1.0))
+    g = angular_weights(opt, sin_t, cos_t)
     f0 = pupil_function(opt, th, zernike, project, w0)
     arg = opt.k * np.outer(np.asarray(r, dtype=np.float64), sin_t)  # [nr, nth]
     zs = np.asarray(zs, dtype=np.float64)
@@ -151,7 +172,7 @@ def field_bessel(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike=None,
     E = np.empty((len(zs), 3, nx, ny), dtype=np.complex128)
     for iz in range(len(zs)):
         In = [interpolate(prof[iz, n], r_max, rho) for n in range(3)]
-        E[iz] = np.stack(field_from_profiles(*In, cos_p, sin_p, opt.pol))
+        E[iz] = np.stack(field_from_profiles(*In, cos_p, sin_p, model_pol(opt)))
     return E
 
 
@@ -163,7 +184,7 @@ def field_bessel_direct(opt, n_theta, nx, ny, dx, dy, zs, zernike=None,
     E = np.empty((len(zs), 3, nx, ny), dtype=np.complex128)
     for iz in range(len(zs)):
         In = [prof[iz, n].reshape(nx, ny) for n in range(3)]
-        E[iz] = np.stack(field_from_profiles(*In, cos_p, sin_p, opt.pol))
+        E[iz] = np.stack(field_from_profiles(*In, cos_p, sin_p, model_pol(opt)))
     return E
 
 

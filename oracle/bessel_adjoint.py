@@ -18,7 +18,7 @@ conj(a) g.  The adjoint runs the same steps backwards:
     g_E_c   = 2 (dL/dI) E_c
     g_v_n   = sum_c conj(C_B M_cn) g_E_c
     g_P_n   = transpose of the interpolation applied to g_v_n
-    g_F_s   = sum_n B_n^T g_P_n
+    g_F_s   = sum_n B_n^H g_P_n
     Q_j     = sum_s conj(g_F_s(theta_j)) F_s(theta_j)
     dL/dW_0(theta_j) = Re(i Q_j) = -Im Q_j
     dL/dc_q          = sum_j Z_q(sin theta_j / s_max) dL/dW_0(theta_j)     (Eq. 15)
@@ -35,8 +35,8 @@ import math
 import numpy as np
 from scipy.special import jv
 
-from .bessel import (C_BESSEL, gl_rule, interpolate, pixel_polar, pupil_function,
-                     radial_grid)
+from .bessel import (C_BESSEL, angular_weights, gl_rule, interpolate, model_pol,
+                     pixel_polar, pupil_function, radial_grid)
 from .optics import _layer_root, noll_to_nm
 from .optics import zernike as zernike_poly
 
@@ -67,12 +67,12 @@ def emitter_loss_and_grads(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike=None,
     (L, dL/dW_0 [n_theta], dL/dc [n_zern], dL/dt_s, I [nz, nx, ny])."""
     th, wt = gl_rule(n_theta, opt.theta_max)
     sin_t, cos_t = np.sin(th), np.cos(th)
-    g = (sin_t * (1.0 + cos_t), sin_t * sin_t, sin_t * (cos_t - 1.0))
+    g = angular_weights(opt, sin_t, cos_t)
     f0 = pupil_function(opt, th, zernike, project, w0)
     r, r_max = radial_grid(n_r, nx, ny, dx, dy)
     B = [jv(n, opt.k * np.outer(r, sin_t)) * (wt * g[n])[None, :] for n in range(3)]
     rho, cos_p, sin_p = pixel_polar(nx, ny, dx, dy)
-    M = field_matrix(cos_p, sin_p, opt.pol)
+    M = field_matrix(cos_p, sin_p, model_pol(opt))
     # interpolation cell and weight of every pixel (same rule as the forward)
     t = rho * ((n_r - 1) / r_max) if r_max > 0 else np.zeros_like(rho)
     c0 = np.clip(np.floor(t).astype(np.int64), 0, n_r - 2)
@@ -103,7 +103,7 @@ def emitter_loss_and_grads(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike=None,
             np.add.at(acc, c0.ravel(), ((1.0 - f) * gv).ravel())
             np.add.at(acc, c0.ravel() + 1, (f * gv).ravel())
             gP.append(acc)
-        gF = sum(B[n].T @ gP[n] for n in range(3))
+        gF = sum(np.conj(B[n]).T @ gP[n] for n in range(3))     # B^H (complex with Fresnel)
         Q += np.conj(gF) * F
     gW = -Q.imag
     D = depth_derivative(opt, sin_t)

@@ -15,7 +15,7 @@ import math
 import numpy as np
 
 from .bessel import gl_rule
-from .optics import amplitude, far_field, gibson_lanni_phase, zernike_phase
+from .optics import amplitude, far_field_model, gibson_lanni_phase, zernike_phase
 
 C_CONT = -1j / (2.0 * math.pi)
 
@@ -34,7 +34,7 @@ def field_points(opt, xs, ys, zs, zernike=None, n_theta=512, n_phi=256):
                               sin_t / opt.s_max, PH)
     base = (amplitude(opt, cos_t, sin_t) * np.exp(1j * w) * sin_t
             * (wt[:, None] * wph))
-    ef = far_field(cos_t, sin_t, cos_p, sin_p, opt.pol)
+    ef = far_field_model(opt, cos_t, sin_t, cos_p, sin_p)
     terms = [(base * e).ravel() for e in ef]              # 3 x [nodes]
     sx = (sin_t * cos_p).ravel()
     sy = (sin_t * sin_p).ravel()

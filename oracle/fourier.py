@@ -15,7 +15,7 @@ import math
 
 import numpy as np
 
-from .optics import (amplitude, far_field, gibson_lanni_phase, pupil_geometry,
+from .optics import (amplitude, far_field_model, gibson_lanni_phase, pupil_geometry,
                      pupil_mask, pupil_nodes, zernike_phase)
 
 C_FOURIER = -1j / (2.0 * math.pi)          # -i f k / (2 pi) with f k = 1
@@ -45,7 +45,7 @@ def pupil_field(opt, n_pupil, zernike=None, phase_map=None):
     mask = pupil_mask(n_pupil)
     amp = amplitude(opt, cos_t, sin_t)
     w = pupil_phase(opt, n_pupil, zernike, phase_map)
-    ef = far_field(cos_t, sin_t, cos_p, sin_p, opt.pol)
+    ef = far_field_model(opt, cos_t, sin_t, cos_p, sin_p)
     safe_cos = np.where(mask, cos_t, 1.0)
     P = np.stack([np.where(mask, amp * np.exp(1j * w) * e / safe_cos, 0.0)
                   for e in ef])

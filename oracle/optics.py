@@ -23,7 +23,8 @@ class Optics:
 
     def __init__(self, NA, lam, n_i, n_s=None, n_g=None, n_i_design=None,
                  n_g_design=None, t_g=170.0, t_g_design=None, t_i_design=150.0,
-                 depth=0.0, pol=(1.0, 0.0), apodize=True, s_env=0.0):
+                 depth=0.0, pol=(1.0, 0.0), apodize=True, s_env=0.0,
+                 scalar=False, fresnel=False):
         self.NA = float(NA)
         self.lam = float(lam)
         self.n_i = float(n_i)
@@ -38,12 +39,14 @@ class Optics:
         self.pol = (complex(pol[0]), complex(pol[1]))
         self.apodize = bool(apodize)
         self.s_env = float(s_env)
+        self.scalar = bool(scalar)        # Eq. 3 / Eq. 5: e_far = e_inc, one channel
+        self.fresnel = bool(fresnel)      # Eq. 6 with the q_s, q_p of Eq. 7
 
     @classmethod
     def from_dict(cls, d):
         keys = ("NA", "lam", "n_i", "n_s", "n_g", "n_i_design", "n_g_design",
                 "t_g", "t_g_design", "t_i_design", "depth", "pol", "apodize",
-                "s_env")
+                "s_env", "scalar", "fresnel")
         return cls(**{k: d[k] for k in keys if k in d})
 
     def with_depth(self, depth):
@@ -123,6 +126,36 @@ def far_field(cos_t, sin_t, cos_p, sin_p, pol, q_s=1.0, q_p=1.0):
           q_s * (1.0 + cos2) + q_p * (1.0 - cos2) * cos_t,
           -2.0 * q_p * sin_p * sin_t)
     return [0.5 * (cx[i] * px + cy[i] * py) for i in range(3)]
+
+
+def fresnel_coefficients(opt, sin_t):
+    """q_s, q_p of Eq. 7: products over the interfaces sample -> coverslip ->
+    immersion.  The angle in medium m follows from Snell's law,
+    n_m sin(theta_m) = n_i sin(theta), with cos(theta_m) the principal complex
+    root (Im >= 0) where medium m is evanescent."""
+    media = [opt.n_s, opt.n_g, opt.n_i]
+    nis = opt.n_i * np.asarray(sin_t, dtype=np.float64)
+    cos_m = [np.sqrt((1.0 - (nis / n) ** 2).astype(np.complex128) + 0j) for n in media]
+    qs = np.ones_like(cos_m[0])
+    qp = np.ones_like(cos_m[0])
+    for m in range(len(media) - 1):
+        n1, n2, c1, c2 = media[m], media[m + 1], cos_m[m], cos_m[m + 1]
+        qs = qs * (2.0 * n1 * c1 / (n1 * c1 + n2 * c2))
+        qp = qp * (2.0 * n1 * c1 / (n2 * c1 + n1 * c2))
+    return qs, qp
+
+
+def far_field_model(opt, cos_t, sin_t, cos_p, sin_p):
+    """The far field the model uses: scalar (Sec. 3.2: e_far = e_inc = 1 in
+    channel 0), vectorial with q_s = q_p = 1, or vectorial with the Fresnel
+    coefficients of Eq. 7."""
+    if opt.scalar:
+        one = np.ones(np.shape(cos_t), dtype=np.complex128)
+        return [one, 0.0 * one, 0.0 * one]
+    if opt.fresnel:
+        qs, qp = fresnel_coefficients(opt, sin_t)
+        return far_field(cos_t, sin_t, cos_p, sin_p, opt.pol, qs, qp)
+    return far_field(cos_t, sin_t, cos_p, sin_p, opt.pol)
 
 
 # ----------------------------------------------------------------------------
