@@ -42,16 +42,16 @@ FP32_LANES_PER_SM = 128
 # command and the figures).  A figure holds only for the source it was taken
 # on: when the kernel's sources hash differently, traffic is reported as null.
 PROFILED_TRAFFIC = {
-    # 13-plane z-chunk (256^2 pupil, 512^2 px): 43.05 MB read + 0.32 MB written
+    # 13-plane z-chunk (256^2 pupil, 512^2 px): 43.07 MB read + 0.29 MB written
     "stage2_contraction_intensity": dict(
-        bytes_per_unit=(43.046e6 + 0.316e6) / 13, unit="plane",
-        sources=("tc_kernels.cu", "tc_kernels.cuh", "tc_ptx.cuh"),
-        sha256_16="a8d98e5b0528b495", precision="split_fp16"),
-    # 9442 slices of 128^2 px: 58.33 MB read + 557.0 MB written
+        bytes_per_unit=(43.074e6 + 0.294e6) / 13, unit="plane",
+        sources=("tc_kernels.cu", "tc_ptx.cuh"),
+        sha256_16="240f39cafc7648f5", precision="split_fp16"),
+    # 9442 slices of 128^2 px: 58.27 MB read + 557.25 MB written
     "bessel_radial_to_cartesian": dict(
-        bytes_per_unit=(58.325e6 + 557.009e6) / 9442, unit="slice",
-        sources=("bessel_epilogue.cu", "bessel_kernels.cuh", "psf_common.cuh"),
-        sha256_16="4e7983811f09d1ff", precision=None),
+        bytes_per_unit=(58.272e6 + 557.250e6) / 9442, unit="slice",
+        sources=("bessel_epilogue.cu", "psf_common.cuh"),
+        sha256_16="454d25dd33e035fb", precision=None),
 }
 
 
