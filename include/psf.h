@@ -23,7 +23,8 @@
  *     float [nz][nx][ny]; fields are interleaved complex64 [nz][3][nx][ny].
  *   - Zernike coefficients: Noll index j = 1..n_zern stored at [j-1], radians,
  *     RMS-normalised on the unit pupil (Noll 1976); phi from +x towards +y.
- *   - Fresnel coefficients q_s = q_p = 1 (Eq. 7 not applied).
+ *   - Fresnel coefficients q_s = q_p = 1 (Eq. 7 not applied) unless the
+ *     PSF_FRESNEL flag is set; PSF_SCALAR selects the scalar model.
  *
  * Ownership and execution
  *   - Every device buffer is owned by the caller.  The library allocates no
@@ -78,6 +79,17 @@ extern "C" {
                                        instead of reporting an error (Sec. 3.4:
                                        the spherical form needs an
                                        axisymmetric pupil)                     */
+#define PSF_SCALAR               2  /* scalar model (Sec. 3.2): e_far = e_inc,
+                                       Eq. 3 (Cartesian) / Eq. 5 (spherical);
+                                       the field is channel 0 (x), the Jones
+                                       vector is not used; every path          */
+#define PSF_FRESNEL              4  /* vectorial model with the Fresnel
+                                       transmission coefficients q_s, q_p of
+                                       Eq. 7 in Eq. 6, over the interfaces
+                                       sample -> coverslip -> immersion (Snell
+                                       angles, principal root where evanescent).
+                                       Fourier: every path; Bessel: the FP32
+                                       forward only (complex J_n operand)       */
 
 /* Physical parameters (Eq. 1, Eq. 13-14, Eq. 16-17). */
 typedef struct {
@@ -96,7 +108,7 @@ typedef struct {
   double pol[4];      /* Jones vector (p_x.re, p_x.im, p_y.re, p_y.im)         */
   int    apodize;     /* 1: A = sqrt(cos theta) (Eq. 16); 0: A = 1            */
   double s_env;       /* > 0: Gaussian envelope exp(-sin^2/s_env^2) (Eq. 17)   */
-  int    flags;       /* PSF_PROJECT_AXISYMMETRIC                              */
+  int    flags;       /* PSF_PROJECT_AXISYMMETRIC | PSF_SCALAR | PSF_FRESNEL   */
 } psf_optics;
 
 /* Output grid of the Fourier strategy. */

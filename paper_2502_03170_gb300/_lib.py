@@ -22,6 +22,8 @@ PSF_PREC_SPLIT_FP16 = 1
 PSF_PREC_SPLIT_BF16 = 2
 
 PSF_PROJECT_AXISYMMETRIC = 1
+PSF_SCALAR = 2
+PSF_FRESNEL = 4
 
 ERROR_NAMES = {
     PSF_ERR_ARG: "PSF_ERR_ARG",

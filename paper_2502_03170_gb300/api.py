@@ -17,7 +17,8 @@ PRECISIONS = {"fp32": _lib.PSF_PREC_FP32, "split_fp16": _lib.PSF_PREC_SPLIT_FP16
 
 
 def make_optics(d, flags=0):
-    """psf_optics from a parameter dict (keys as in ``workloads``)."""
+    """psf_optics from a parameter dict (keys as in ``workloads``; optional
+    booleans ``scalar`` and ``fresnel`` select the model)."""
     o = PsfOptics()
     o.NA = d["NA"]
     o.lambda_ = d["lam"]
@@ -35,6 +36,10 @@ def make_optics(d, flags=0):
     o.pol[0], o.pol[1], o.pol[2], o.pol[3] = px.real, px.imag, py.real, py.imag
     o.apodize = 1 if d.get("apodize", True) else 0
     o.s_env = d.get("s_env", 0.0)
+    if d.get("scalar"):
+        flags |= _lib.PSF_SCALAR
+    if d.get("fresnel"):
+        flags |= _lib.PSF_FRESNEL
     o.flags = flags
     return o
 
@@ -135,7 +140,7 @@ class _BesselArgs:
         flags = _lib.PSF_PROJECT_AXISYMMETRIC if project else 0
         o = optics if isinstance(optics, PsfOptics) else make_optics(optics, flags)
         if isinstance(optics, PsfOptics):
-            o.flags = flags
+            o.flags = (o.flags & ~_lib.PSF_PROJECT_AXISYMMETRIC) | flags
         self.o = o
         self.dev = torch.device("cuda", torch.cuda.current_device())
 

@@ -17,21 +17,39 @@ __global__ void k_bessel_jmat(BesselParams p, ThetaTable t, float* Bt) {
   if (idx >= (long long)rows * p.n_theta) return;
   const int j = (int)(idx / rows), row = (int)(idx - (long long)j * rows);
   const int n = row / p.n_r, i = row - n * p.n_r;
-  const double st = t.sin_t[j], ct = t.cos_t[j];
+  const double st = t.sin_t[j];
   const double x = p.k * (i * p.dr) * st;
-  double jn_v, g;
+  double jn_v;
   if (n == 0) {
     jn_v = j0(x);
-    g = st * (1.0 + ct);
   } else if (n == 1) {
     jn_v = j1(x);
-    g = st * st;
   } else {
     // J_2(0) = 0 exactly (the library routine is not used at x = 0)
     jn_v = x > 0.0 ? jn(2, x) : 0.0;
-    g = st * (ct - 1.0);
   }
-  Bt[idx] = (float)(t.w[j] * g * jn_v);
+  Bt[idx] = (float)(t.w[j] * t.g[(2 * n) * p.n_theta + j] * jn_v);
+}
+
+// Complex form for weights with imaginary parts (Fresnel coefficients past a
+// critical angle).
+__global__ void k_bessel_jmat_complex(BesselParams p, ThetaTable t, float2* BtC) {
+  const int rows = 3 * p.n_r;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * p.n_theta) return;
+  const int j = (int)(idx / rows), row = (int)(idx - (long long)j * rows);
+  const int n = row / p.n_r, i = row - n * p.n_r;
+  const double x = p.k * (i * p.dr) * t.sin_t[j];
+  const double jn_v = n == 0 ? j0(x) : (n == 1 ? j1(x) : (x > 0.0 ? jn(2, x) : 0.0));
+  const double s = t.w[j] * jn_v;
+  BtC[idx] = make_float2((float)(s * t.g[(2 * n) * p.n_theta + j]),
+                         (float)(s * t.g[(2 * n + 1) * p.n_theta + j]));
+}
+
+void launch_bessel_jmat_complex(const BesselParams& p, ThetaTable t, float2* BtC,
+                                cudaStream_t s) {
+  const long long n = 3LL * p.n_r * p.n_theta;
+  k_bessel_jmat_complex<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, t, BtC);
 }
 
 void launch_bessel_jmat(const BesselParams& p, ThetaTable t, float* Bt,
@@ -166,8 +184,10 @@ void launch_pixel_table(const BesselParams& p, int* pix_i0, float* pix_f,
 // contracted against it.  Thread = one row x 8 slices.
 // ---------------------------------------------------------------------------
 constexpr int BP_SL = 32;
+template <bool CB>
 __global__ void __launch_bounds__(256)
 k_bessel_profiles_f32(BesselParams p, ThetaTable t, const float* __restrict__ Bt,
+                      const float2* __restrict__ BtC,
                       EmitterTable et, const int* __restrict__ slice_em,
                       const float2* __restrict__ zz, float2* __restrict__ prof) {
   extern __shared__ float2 F[];   // [n_theta][BP_SL]
@@ -198,12 +218,21 @@ k_bessel_profiles_f32(BesselParams p, ThetaTable t, const float* __restrict__ Bt
     for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
     if (row < rows) {
       for (int j = 0; j < p.n_theta; ++j) {
-        const float b = __ldg(&Bt[(size_t)j * rows + row]);
         const float2* Fj = &F[j * BP_SL + sg * 8];
+        if (CB) {
+          const float2 b = __ldg(&BtC[(size_t)j * rows + row]);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          acc[k].x = fmaf(b, Fj[k].x, acc[k].x);
-          acc[k].y = fmaf(b, Fj[k].y, acc[k].y);
+          for (int k = 0; k < 8; ++k) {
+            acc[k].x = fmaf(b.x, Fj[k].x, fmaf(-b.y, Fj[k].y, acc[k].x));
+            acc[k].y = fmaf(b.x, Fj[k].y, fmaf(b.y, Fj[k].x, acc[k].y));
+          }
+        } else {
+          const float b = __ldg(&Bt[(size_t)j * rows + row]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            acc[k].x = fmaf(b, Fj[k].x, acc[k].x);
+            acc[k].y = fmaf(b, Fj[k].y, acc[k].y);
+          }
         }
       }
 #pragma unroll
@@ -220,10 +249,21 @@ void launch_bessel_profiles_f32(const BesselParams& p, ThetaTable t,
                                 const int* slice_em, const float2* zz,
                                 float2* prof, cudaStream_t s) {
   const size_t smem = (size_t)p.n_theta * BP_SL * sizeof(float2);
-  cudaFuncSetAttribute(k_bessel_profiles_f32,
+  cudaFuncSetAttribute(k_bessel_profiles_f32<false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_bessel_profiles_f32<<<ceil_div(p.n_slices, BP_SL), 256, smem, s>>>(
-      p, t, Bt, e, slice_em, zz, prof);
+  k_bessel_profiles_f32<false><<<ceil_div(p.n_slices, BP_SL), 256, smem, s>>>(
+      p, t, Bt, nullptr, e, slice_em, zz, prof);
+}
+
+void launch_bessel_profiles_f32c(const BesselParams& p, ThetaTable t,
+                                 const float2* BtC, EmitterTable e,
+                                 const int* slice_em, const float2* zz,
+                                 float2* prof, cudaStream_t s) {
+  const size_t smem = (size_t)p.n_theta * BP_SL * sizeof(float2);
+  cudaFuncSetAttribute(k_bessel_profiles_f32<true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_bessel_profiles_f32<true><<<ceil_div(p.n_slices, BP_SL), 256, smem, s>>>(
+      p, t, nullptr, BtC, e, slice_em, zz, prof);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,10 @@ struct ThetaTable {
   const double* b_im;
   const double* amp0;    // A(theta): apodization x envelope (Eq. 16-17)
   const double* zm0;     // [kMaxM0][n_theta] Z_j(sin theta / s_max), m = 0 j
+  const double* g;       // [3][re, im][n_theta] angular weights g_n of the model:
+                         // sin(1+cos), sin^2, sin(cos-1) (Eq. 11); Fresnel:
+                         // sin(q_s + q_p cos), q_p sin^2, sin(q_p cos - q_s);
+                         // scalar (Eq. 5): 2 sin, 0, 0
   const float* kh;       // n_i cos(theta)/lambda as double-float
   const float* kl;
 };
@@ -38,6 +42,7 @@ struct BesselParams {
   unsigned long long nonaxis_mask[2];  // bit j-1 set: Noll j has m != 0
   int project;
   double pol[4];
+  int complex_g;         // the weights have imaginary parts (Fresnel)
 };
 
 // Per-emitter integrand table (float [n_em][n_theta]):
@@ -65,6 +70,13 @@ void launch_bessel_profiles_f32(const BesselParams& p, ThetaTable t,
                                 const float* Bt, EmitterTable e,
                                 const int* slice_em, const float2* zz,
                                 float2* prof, cudaStream_t s);
+// complex J_n operand (Fresnel weights): BtC [n_theta][3 N_r] complex
+void launch_bessel_jmat_complex(const BesselParams& p, ThetaTable t, float2* BtC,
+                                cudaStream_t s);
+void launch_bessel_profiles_f32c(const BesselParams& p, ThetaTable t,
+                                 const float2* BtC, EmitterTable e,
+                                 const int* slice_em, const float2* zz,
+                                 float2* prof, cudaStream_t s);
 void launch_bessel_intensity(const BesselParams& p, const float2* prof,
                              const int* slice_em, const int* valid,
                              const int* pix_i0, const float* pix_f,

@@ -2,6 +2,7 @@
 // matrices (FP64 twiddles), per-z pupil fields (double-float defocus), and
 // the plain-FP32 separable complex contractions with the |E|^2 epilogue.
 #include "fourier_kernels.cuh"
+#include "optics_models.cuh"
 
 namespace psf {
 
@@ -70,16 +71,29 @@ __global__ void k_node_table(NodeParams p, NodeTable t) {
   if (p.s_env > 0) a *= exp(-(sin_t * sin_t) / (p.s_env * p.s_env));
   if (decay_cyc != 0.0) a *= exp(-2.0 * kPi * decay_cyc);
 
-  // Eq. 6 with q_s = q_p = 1, columns for e_inc^x and e_inc^y (each / 2).
-  const double c2 = cp * cp - sp * sp, s2 = 2.0 * sp * cp;
-  const double xx = 0.5 * ((1.0 - c2) + (1.0 + c2) * cos_t);
-  const double xy = 0.5 * (cos_t - 1.0) * s2;
-  const double yy = 0.5 * ((1.0 + c2) + (1.0 - c2) * cos_t);
-  const double zx = -cp * sin_t, zy = -sp * sin_t;
-  const double pxr = p.pol[0], pxi = p.pol[1], pyr = p.pol[2], pyi = p.pol[3];
-  const double e[6] = {a * (xx * pxr + xy * pyr), a * (xx * pxi + xy * pyi),
-                       a * (xy * pxr + yy * pyr), a * (xy * pxi + yy * pyi),
-                       a * (zx * pxr + zy * pyr), a * (zx * pxi + zy * pyi)};
+  double e[6];
+  if (p.model == 1) {
+    // scalar model (Eq. 3): e_far = e_inc, carried in channel 0
+    e[0] = a;
+    e[1] = e[2] = e[3] = e[4] = e[5] = 0.0;
+  } else {
+    // Eq. 6, columns for e_inc^x and e_inc^y (each / 2); q_s = q_p = 1 unless
+    // the Fresnel coefficients of Eq. 7 are requested (complex past the
+    // critical angle of a layer)
+    dcplx qs{1.0, 0.0}, qp{1.0, 0.0};
+    if (p.model == 2) fresnel_q(p.n_s, p.n_g, p.n_i, sin_t, qs, qp);
+    const double c2 = cp * cp - sp * sp, s2 = 2.0 * sp * cp;
+    // xx = [qs (1 - c2) + qp (1 + c2) cos] / 2, xy = (qp cos - qs) s2 / 2,
+    // yy = [qs (1 + c2) + qp (1 - c2) cos] / 2, z = -qp (cos phi, sin phi) sin
+    const dcplx xx = 0.5 * ((1.0 - c2) * qs + ((1.0 + c2) * cos_t) * qp);
+    const dcplx xy = (0.5 * s2) * (cos_t * qp - qs);
+    const dcplx yy = 0.5 * ((1.0 + c2) * qs + ((1.0 - c2) * cos_t) * qp);
+    const dcplx zx = (-cp * sin_t) * qp, zy = (-sp * sin_t) * qp;
+    const dcplx px{p.pol[0], p.pol[1]}, py{p.pol[2], p.pol[3]};
+    const dcplx ex = a * (xx * px + xy * py), ey = a * (xy * px + yy * py),
+                ez = a * (zx * px + zy * py);
+    e[0] = ex.re; e[1] = ex.im; e[2] = ey.re; e[3] = ey.im; e[4] = ez.re; e[5] = ez.im;
+  }
 #pragma unroll
   for (int c = 0; c < 6; ++c) t.amp[c * NN + idx] = (float)e[c];
   t.wfr[idx] = (float)w_total;

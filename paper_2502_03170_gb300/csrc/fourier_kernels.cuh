@@ -37,6 +37,8 @@ struct NodeParams {
   double pol[4];
   ZernPoly zp;
   const float* phase_map;  // [N][N] radians or null
+  int model;               // 0 vectorial, 1 scalar (Eq. 3), 2 vectorial + Fresnel (Eq. 7)
+  double n_s, n_g;         // sample and coverslip indices (Fresnel interfaces)
 };
 
 // Per-node table written once per call (structure of arrays, float):

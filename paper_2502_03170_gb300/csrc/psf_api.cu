@@ -11,6 +11,7 @@
 #include "bessel_backward.cuh"
 #include "bessel_kernels.cuh"
 #include "fourier_kernels.cuh"
+#include "optics_models.cuh"
 #include "tc_kernels.cuh"
 #include "timing.cuh"
 
@@ -290,6 +291,9 @@ static NodeParams node_params(const psf_optics* opt, int N, const double* zern,
   for (int i = 0; i < 4; ++i) p.pol[i] = opt->pol[i];
   p.zp = zernike_poly(zern, n_zern);
   p.phase_map = phase_map;
+  p.model = (opt->flags & PSF_SCALAR) ? 1 : ((opt->flags & PSF_FRESNEL) ? 2 : 0);
+  p.n_s = opt->n_s;
+  p.n_g = opt->n_g;
   return p;
 }
 
@@ -604,9 +608,10 @@ extern "C" int psf_fourier_vectorial_backward(
 // Bessel strategy
 // ===========================================================================
 struct BesselLayout {
-  double* theta_tab;     // 10 x n_theta + kMaxM0 x n_theta doubles
+  double* theta_tab;     // (10 + kMaxM0 + 6) x n_theta doubles
   float* kappa;          // 2 x n_theta floats
   float* Bt;
+  float2* BtC;           // complex J_n operand (Fresnel weights), FP32 path
   EmitterTable et;
   int* slice_em;
   float2* zz;
@@ -625,10 +630,11 @@ static BesselLayout bessel_layout(void* ws, int n_em, int n_slices, int n_theta,
   BesselLayout L;
   memset(&L, 0, sizeof(L));
   Carver c(ws);
-  L.theta_tab = c.take<double>((size_t)(10 + kMaxM0) * n_theta);
+  L.theta_tab = c.take<double>((size_t)(10 + kMaxM0 + 6) * n_theta);
   L.kappa = c.take<float>(2 * (size_t)n_theta);
   if (precision == PSF_PREC_FP32 || fp32_bt)
     L.Bt = c.take<float>((size_t)3 * n_r * n_theta);
+  if (precision == PSF_PREC_FP32) L.BtC = c.take<float2>((size_t)3 * n_r * n_theta);
   if (precision != PSF_PREC_FP32)
     tc_bessel_carve(c.base, &c.off, n_theta, n_r, n_slices, &L.tc);
   L.et.amp = c.take<float>((size_t)n_em * n_theta);
@@ -691,7 +697,7 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
   const double th_max = asin(s_max);
   std::vector<double> gx, gw;
   gauss_legendre(n_theta, gx, gw);
-  std::vector<double> tab((size_t)(10 + kMaxM0) * n_theta, 0.0);
+  std::vector<double> tab((size_t)(10 + kMaxM0 + 6) * n_theta, 0.0);
   std::vector<float> kap(2 * (size_t)n_theta);
   double* T_th = tab.data();
   double* T_w = T_th + n_theta;
@@ -703,6 +709,9 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
   double* T_bim = T_bre + n_theta;
   double* T_amp = T_bim + n_theta;
   double* T_zm0 = T_amp + 2 * n_theta;   // slot 9 unused (alignment)
+  double* T_g = T_zm0 + (size_t)kMaxM0 * n_theta;   // [3][re, im][n_theta]
+  const bool scalar = (base->flags & PSF_SCALAR) != 0;
+  const bool fresnel = !scalar && (base->flags & PSF_FRESNEL) != 0;
   const GLLayers L0 = gl_layers(base, 0.0), L1 = gl_layers(base, 1.0);
   BesselParams& bp = R->bp;
   memset(&bp, 0, sizeof(bp));
@@ -758,6 +767,26 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
     const f2x kv = split_double(base->n_i * ct / base->lambda);
     kap[j] = kv.hi;
     kap[n_theta + j] = kv.lo;
+    // angular weights g_n of the model (Eq. 11; Eq. 6-7 with Fresnel; Eq. 5)
+    dcplx g[3];
+    if (scalar) {
+      g[0] = {2.0 * st, 0.0};
+      g[1] = g[2] = {0.0, 0.0};
+    } else if (fresnel) {
+      dcplx qs, qp;
+      fresnel_q(base->n_s, base->n_g, base->n_i, st, qs, qp);
+      g[0] = st * (qs + ct * qp);
+      g[1] = (st * st) * qp;
+      g[2] = st * (ct * qp - qs);
+    } else {
+      g[0] = {st * (1.0 + ct), 0.0};
+      g[1] = {st * st, 0.0};
+      g[2] = {st * (ct - 1.0), 0.0};
+    }
+    for (int n = 0; n < 3; ++n) {
+      T_g[(size_t)(2 * n) * n_theta + j] = g[n].re;
+      T_g[(size_t)(2 * n + 1) * n_theta + j] = g[n].im;
+    }
   }
   ThetaTable& tt = R->tt;
   tt.theta = L.theta_tab;
@@ -770,6 +799,7 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
   tt.b_im = tt.b_re + n_theta;
   tt.amp0 = tt.b_im + n_theta;
   tt.zm0 = tt.amp0 + 2 * n_theta;
+  tt.g = tt.zm0 + (size_t)kMaxM0 * n_theta;
   tt.kh = L.kappa;
   tt.kl = L.kappa + n_theta;
 
@@ -791,6 +821,11 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
   bp.nonaxis_mask[1] = mask[1];
   bp.project = (base->flags & PSF_PROJECT_AXISYMMETRIC) ? 1 : 0;
   for (int i = 0; i < 4; ++i) bp.pol[i] = base->pol[i];
+  if (scalar) {                 // Eq. 5 rides on channel x of Eq. 10
+    bp.pol[0] = 1.0;
+    bp.pol[1] = bp.pol[2] = bp.pol[3] = 0.0;
+  }
+  bp.complex_g = fresnel ? 1 : 0;
 
   cudaMemsetAsync(workspace, 0, sizeof(int), s);
   cudaMemcpyAsync(L.theta_tab, tab.data(), tab.size() * sizeof(double),
@@ -808,6 +843,8 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
     TimingScope ts(kTimeSetup, s);
     if (split)
       tc_bessel_jmat(bp, tt, max_w, precision, L.tc, s);
+    else if (bp.complex_g)
+      launch_bessel_jmat_complex(bp, tt, L.BtC, s);
     else
       launch_bessel_jmat(bp, tt, L.Bt, s);
   }
@@ -838,6 +875,10 @@ static int check_bessel_call(const psf_optics* base, int n_em, const double* dep
                              int ny, double dx, double dy, int precision) {
   int r = check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision);
   if (r) return r;
+  if ((base->flags & PSF_FRESNEL) && !(base->flags & PSF_SCALAR) &&
+      precision != PSF_PREC_FP32)
+    return fail(PSF_ERR_PRECISION,
+                "Fresnel weights on the Bessel path need PSF_PREC_FP32 (complex J_n operand)");
   if (!finite_pos(dx) || !finite_pos(dy)) return fail(PSF_ERR_ARG, "pixel pitch must be > 0");
   if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
   if (!depth || !z_offsets || (n_slices > 0 && !z) || (n_zern > 0 && !zernike))
@@ -877,6 +918,9 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
       r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, precision, L.tc,
                              L.prof, (int*)workspace, s);
       if (r) return fail(r, "split-precision Bessel contraction launch failed");
+    } else if (bp.complex_g) {
+      TimingScope ts(kTimeBesselRadial, s);
+      launch_bessel_profiles_f32c(bp, R.tt, L.BtC, L.et, L.slice_em, L.zz, L.prof, s);
     } else {
       TimingScope ts(kTimeBesselRadial, s);
       launch_bessel_profiles_f32(bp, R.tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
@@ -1031,6 +1075,8 @@ extern "C" int psf_bessel_vectorial_backward(
   if (r) return r;
   if (nx > 4096 || ny > 4096)
     return fail(PSF_ERR_ARG, "the Bessel adjoint takes nx, ny <= 4096");
+  if ((base->flags & PSF_FRESNEL) && !(base->flags & PSF_SCALAR))
+    return fail(PSF_ERR_ARG, "the Bessel adjoint does not take Fresnel weights");
   if (n_slices > 0 && !target && !grad_intensity)
     return fail(PSF_ERR_ARG, "target and grad_intensity are both NULL");
   if (loss && !target) return fail(PSF_ERR_ARG, "loss needs a target");

@@ -798,7 +798,8 @@ double tc_pupil_amplitude_bound(const NodeParams& np) {
     a *= exp(-2.0 * kPi * dec);
     if (a > best) best = a;
   }
-  return 1.05 * best * (pol > 0 ? pol : 1.0);
+  // Fresnel coefficients scale the unitary Eq. 6 by at most max|q| <= 2
+  return 1.05 * best * (pol > 0 ? pol : 1.0) * (np.model == 2 ? 2.0 : 1.0);
 }
 
 static float pow2_scale(double bound, double target) {
@@ -1121,20 +1122,17 @@ __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
   double v = 0.0;
   if (j < p.n_theta) {
     const int n = row / p.n_r, i = row - n * p.n_r;
-    const double st = t.sin_t[j], ct = t.cos_t[j];
+    const double st = t.sin_t[j];
     const double x = p.k * (i * p.dr) * st;
-    double jn_v, g;
+    double jn_v;
     if (n == 0) {
       jn_v = j0(x);
-      g = st * (1.0 + ct);
     } else if (n == 1) {
       jn_v = j1(x);
-      g = st * st;
     } else {
       jn_v = x > 0.0 ? jn(2, x) : 0.0;   // J_2(0) = 0
-      g = st * (ct - 1.0);
     }
-    v = sB * t.w[j] * g * jn_v;
+    v = sB * t.w[j] * t.g[(2 * n) * p.n_theta + j] * jn_v;   // real weights only
   }
   uint16_t h, l;
   split16d(v, bf16, h, l);
