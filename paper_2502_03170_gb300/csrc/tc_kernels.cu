@@ -808,6 +808,30 @@ static float pow2_scale(double bound, double target) {
   return (float)exp2(floor(log2(target / bound)));
 }
 
+// Per-thread, per-device side stream and fork/join events (created once).
+struct SideStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t consumed = nullptr, ready = nullptr;
+};
+
+static SideStream* side_stream() {
+  static thread_local SideStream ss[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  SideStream& x = ss[dev];
+  if (x.dev != dev) {
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.consumed, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.ready, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    x.dev = dev;
+  }
+  return &x;
+}
+
 int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
                        int N, int nx, int ny, double dx, double dy, int nz,
                        int zc, double na_over_lambda, float scale,
@@ -841,14 +865,22 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
             make_map_3d(&mU_l, ops.U_lo, K, ny, 3 * zc);
   if (!ok) return PSF_ERR_CUDA;
   const uint32_t idesc = make_idesc(bf16);
+  // The pupil planes of chunk i + 1 are built on a side stream while stage 2
+  // of chunk i runs (stage 2 does not read them); the side stream forks after
+  // stage 1 of chunk i has consumed the buffer and joins before stage 1 of
+  // chunk i + 1, so the caller's stream order is kept.
+  SideStream* side = side_stream();
+  auto pupil = [&](int zc0, cudaStream_t st) {
+    const int n = nz - zc0 < zc ? nz - zc0 : zc;
+    TimingScope ts(kTimePupil, st);
+    const dim3 pg(ceil_div(N * N / 4, 128), n);
+    k_pupil_z_split<<<pg, 128, 0, st>>>(nodes, N, zz, zc0, n, nz, 0, sP, bf16, ops.P_hi,
+                                        ops.P_lo);
+  };
+  pupil(0, s);
   for (int z0 = 0; z0 < nz; z0 += zc) {
     const int nzc = nz - z0 < zc ? nz - z0 : zc;
-    {
-      TimingScope ts(kTimePupil, s);
-      const dim3 pg(ceil_div(N * N / 4, 128), nzc);
-      k_pupil_z_split<<<pg, 128, 0, s>>>(nodes, N, zz, z0, nzc, nz, 0, sP, bf16, ops.P_hi,
-                                         ops.P_lo);
-    }
+    const bool more = z0 + zc < nz;
     Params p1;
     memset(&p1, 0, sizeof(p1));
     p1.planes = nzc;
@@ -873,6 +905,14 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
       r = launch_gemm(mAy_h, mAy_l, mP_h, mP_l, p1, s);
     }
     if (r) return r;
+    if (more) {
+      if (side) {
+        cudaEventRecord(side->consumed, s);
+        cudaStreamWaitEvent(side->s, side->consumed, 0);
+        pupil(z0 + zc, side->s);
+        cudaEventRecord(side->ready, side->s);
+      }
+    }
     Params p2 = p1;
     p2.m_tiles = ceil_div(nx, BOUT);
     p2.n_tiles = ceil_div(ny, BOUT);
@@ -887,6 +927,12 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
       r = launch_gemm(mAx_h, mAx_l, mU_h, mU_l, p2, s);
     }
     if (r) return r;
+    if (more) {
+      if (side)
+        cudaStreamWaitEvent(s, side->ready, 0);
+      else
+        pupil(z0 + zc, s);
+    }
   }
   return PSF_OK;
 }

@@ -8,10 +8,10 @@ the device), then exits.  Cases:
 
 * ``fourier``  - 256^2 pupil, 512^2 px at 10 nm, 16 planes, Gibson-Lanni +
   Zernike (one z-chunk of the benchmark stack).
-* ``bessel``   - 256 emitters of the batched Bessel workload (about 600 MB
-  of output, above the 126 MB L2).
-* ``bessel_backward`` - the adjoint of the same 256 emitters with a seeded
-  dL/dI (about 600 MB of input).
+* ``bessel``   - ``--emitters`` (default 256) emitters of the batched Bessel
+  workload (about 600 MB of output for 256, above the 126 MB L2).
+* ``bessel_backward`` - the adjoint of the same emitters with a seeded dL/dI
+  (about 600 MB of input for 256 emitters).
 * ``fourier_backward`` - the phase-retrieval adjoint (256^2 pupil, 128^2 px,
   32 planes) for ``--batch`` pupils against a seeded target.
 """
@@ -29,6 +29,7 @@ def main():
     ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward",
                                      "fourier_backward"])
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--emitters", type=int, default=256)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--nz", type=int, default=16)
     args = ap.parse_args()
@@ -59,7 +60,7 @@ def main():
         torch.cuda.synchronize()
         assert torch.isfinite(gW).all()
     elif args.case == "bessel_backward":
-        c = W.bessel(n_emitters=256)
+        c = W.bessel(n_emitters=args.emitters)
         n_sl = int(c["z_offsets"][-1])
         gen = torch.Generator(device="cuda")
         gen.manual_seed(7)
@@ -73,7 +74,7 @@ def main():
         torch.cuda.synchronize()
         assert torch.isfinite(r["grad_phase_theta"]).all()
     else:
-        c = W.bessel(n_emitters=256)
+        c = W.bessel(n_emitters=args.emitters)
         for _ in range(2):
             I = api.bessel(c["optics"], c["depth"], c["zernike"], c["z_offsets"],
                            c["z"], c["n_theta"], c["n_r"], c["nx"], c["ny"],
