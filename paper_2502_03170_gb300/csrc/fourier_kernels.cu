@@ -463,26 +463,31 @@ void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s)
 }
 
 // dL/dc_j = sum_{p,q} Z_j[p][q] dL/dW_0[p][q] for `nb` pupils at once: CTA
-// (j, k, part) sums its contiguous 1/kZgParts of the nodes in FP64 (fixed
-// order), then one thread per (k, j) adds the parts in order.
-constexpr int kZgParts = 16;
+// (j, part) takes its contiguous 1/kZgParts of the nodes, reads that slice of
+// Z_j once and reduces it against every pupil's gradient (FP64, fixed order);
+// one thread per (k, j) then adds the parts in order.
+constexpr int kZgParts = 64;
+constexpr int kZgMaxPupils = 128;
 
-__global__ void k_zernike_grad_part(const float* __restrict__ Zt, int NN,
+__global__ void k_zernike_grad_part(const float* __restrict__ Zt, int NN, int nb,
                                     const float* __restrict__ gW, double* part) {
   __shared__ double red[256];
-  const int j = blockIdx.x, k = blockIdx.y, sp = blockIdx.z;
+  const int j = blockIdx.x, sp = blockIdx.y;
   const int i0 = (int)((long long)NN * sp / kZgParts), i1 = (int)((long long)NN * (sp + 1) / kZgParts);
   const float* z = Zt + (size_t)j * NN;
-  const float* g = gW + (size_t)k * NN;
-  double acc = 0.0;
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += (double)z[i] * (double)g[i];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+  for (int k = 0; k < nb; ++k) {
+    const float* g = gW + (size_t)k * NN;
+    double acc = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += (double)z[i] * (double)g[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[((size_t)k * gridDim.x + j) * kZgParts + sp] = red[0];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[((size_t)k * gridDim.x + j) * kZgParts + sp] = red[0];
 }
 
 __global__ void k_zernike_grad_fin(const double* __restrict__ part, int n_zern, int nb,
@@ -501,7 +506,7 @@ size_t zernike_grad_part_bytes(int n_zern, int nb) {
 void launch_zernike_grad(const ZernBasis& zb, int N, const float* Zt, const float* gW,
                          int nb, double* part, float* grad_c, cudaStream_t s) {
   if (zb.n_zern <= 0 || nb <= 0) return;
-  k_zernike_grad_part<<<dim3(zb.n_zern, nb, kZgParts), 256, 0, s>>>(Zt, N * N, gW, part);
+  k_zernike_grad_part<<<dim3(zb.n_zern, kZgParts), 256, 0, s>>>(Zt, N * N, nb, gW, part);
   k_zernike_grad_fin<<<ceil_div(zb.n_zern * nb, 128), 128, 0, s>>>(part, zb.n_zern, nb,
                                                                    grad_c);
 }

@@ -531,22 +531,27 @@ extern "C" int psf_fourier_vectorial_backward(
       TimingScope ts(kTimeSetup, s);
       if ((r = tc_fourier_bwd_setup(L.tc, N, nx, ny, grid->dx, grid->dy, f, precision, s)))
         return fail(r, "split-precision adjoint setup failed");
-      if (grad_zernike) launch_zernike_table(zb, N, L.Zt, s);
     }
-    // groups of pupils share one pass over their planes (flat over (pupil, z))
+    // groups of pupils share one pass over their planes (flat over (pupil, z));
+    // the node table (amplitudes, defocus factors, Gibson-Lanni phase) is
+    // common to all pupils, their phases differ by sum_j c_j Z_j + W_0
     const int gp = L.tc.group;
-    double amp_bound = 0.0;
+    const NodeParams np0 = node_params(opt, N, nullptr, 0, nullptr);
+    const double amp_bound = tc_pupil_amplitude_bound(np0);   // phase-independent
+    {
+      TimingScope ts(kTimeSetup, s);
+      launch_node_table(np0, L.nodes, s);        // L.nodes.wfr = Gibson-Lanni phase
+      if (n_zern > 0) launch_zernike_table(zb, N, L.Zt, s);
+    }
     for (int b0 = 0; b0 < batch; b0 += gp) {
       const int nb = batch - b0 < gp ? batch - b0 : gp;
-      for (int k = 0; k < nb; ++k) {
-        const int b = b0 + k;
-        NodeParams np = node_params(opt, N, zernike ? zernike + (size_t)b * n_zern : nullptr,
-                                    n_zern, phase_map ? phase_map + (size_t)b * NN : nullptr);
-        if (b == 0) amp_bound = tc_pupil_amplitude_bound(np);   // phase-independent
-        NodeTable t = L.nodes;
-        t.wfr = L.tc.wfr + (size_t)k * NN;
+      if (n_zern > 0)
+        cudaMemcpyAsync(L.tc.coef, zernike + (size_t)b0 * n_zern,
+                        (size_t)nb * n_zern * sizeof(double), cudaMemcpyHostToDevice, s);
+      {
         TimingScope ts(kTimeSetup, s);
-        launch_node_table(np, t, s);
+        tc_group_phase(L.tc, L.nodes.wfr, L.Zt, L.tc.coef, n_zern,
+                       phase_map ? phase_map + (size_t)b0 * NN : nullptr, N, nb, s);
       }
       const float* Tb = target ? target + (size_t)b0 * vox : nullptr;
       const float* Gb = grad_intensity ? grad_intensity + (size_t)b0 * vox : nullptr;

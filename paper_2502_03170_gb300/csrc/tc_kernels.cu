@@ -540,37 +540,61 @@ __global__ void k_twiddle_adj_split(int N, int n_out, double alpha, uint16_t* hi
 
 // Phase gradient of a chunk: for node (p, q) and each flat plane of the chunk
 // (planes p0 .. p0 + planes over (pupil, z), nz_per per pupil)
-//   2 s Re(conj(Gh_c) P_c) summed over c = scale * (Gh_re P_re + Gh_im P_im),
-// with P = (hi + lo) / S_P from the split pupil planes, summed into gW[pupil]
-// in plane order (a pupil's first plane starts its sum).  One thread per
-// (pupil of the chunk, node).
-__global__ void k_gw_fold(const float* __restrict__ Ghf, const uint16_t* __restrict__ P_hi,
-                          const uint16_t* __restrict__ P_lo, int p_bf16, int N, int p0,
-                          int planes, int nz_per, float scale, float* gW) {
+//   2 s Re(conj(Gh_c) P_c) summed over c = scale * sum_c (Gh_re P_re + Gh_im P_im),
+// with the pupil field P_c = amp_c e^{2 pi i (wfr_k + n_i z cos / lambda)}
+// rebuilt from the node table exactly as the pupil planes were built, summed
+// into gW[pupil] in plane order (a pupil's first plane starts its sum).  One
+// thread per (pupil of the chunk, node).
+__global__ void k_gw_fold(const float* __restrict__ Ghf, NodeTable t,
+                          const float2* __restrict__ zz, int N, int p0, int planes,
+                          int nz_per, float scale, float* gW) {
   const int NN = N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN) return;
   const int pk = p0 / nz_per + (int)blockIdx.y;           // pupil of this thread
   const int a = max(pk * nz_per - p0, 0), b = min((pk + 1) * nz_per - p0, planes);
   if (a >= b) return;
-  const int ip = i / N, iq = i - (i / N) * N;
+  float amp[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) amp[c] = t.amp[(size_t)c * NN + i];
+  const float w = t.wfr[(size_t)pk * NN + i];
+  const f2x kap{t.kh[i], t.kl[i]};
   float* dst = gW + (size_t)pk * NN + i;
   float v = (p0 + a - pk * nz_per == 0) ? 0.f : *dst;
 #pragma unroll 4
   for (int pl = a; pl < b; ++pl) {
+    const float2 z = zz[p0 + pl - pk * nz_per];
+    const float2 e = cis_cycles(frac_mul_add(kap, f2x{z.x, z.y}, w));
     float acc = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t gb = ((size_t)(pl * 3 + c) * 2) * NN + i;
-      const size_t pb = ((size_t)(pl * 3 + c) * N + ip) * (size_t)(2 * N) + iq;
-      const float pr = unsplit16(P_hi[pb], P_lo[pb], p_bf16);
-      const float pi = unsplit16(P_hi[pb + N], P_lo[pb + N], p_bf16);
+      const float pr = amp[2 * c] * e.x - amp[2 * c + 1] * e.y;
+      const float pi = amp[2 * c] * e.y + amp[2 * c + 1] * e.x;
       acc = fmaf(Ghf[gb], pr, acc);
       acc = fmaf(Ghf[gb + NN], pi, acc);
     }
     v = fmaf(scale, acc, v);
   }
   *dst = v;
+}
+
+// Phases of a group of pupils from the shared Gibson-Lanni phase:
+//   wfr[k][i] = frac(wfr_gl[i] + (sum_j c[k][j] Z_j[i] + W_0[k][i]) / 2 pi)
+// (Zernike basis table Zt [n_zern][N N]; the Zernike and free phases are
+// O(1) rad, so FP32 terms keep ~1e-7 rad).
+__global__ void k_group_phase(const float* __restrict__ wfr_gl, const float* __restrict__ Zt,
+                              const double* __restrict__ coef, int n_zern,
+                              const float* __restrict__ phase_map, int NN, float* wfr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NN) return;
+  const int k = blockIdx.y;
+  double w = 0.0;
+  for (int j = 0; j < n_zern; ++j) w += coef[(size_t)k * n_zern + j] * (double)Zt[(size_t)j * NN + i];
+  if (phase_map) w += (double)phase_map[(size_t)k * NN + i];
+  double cyc = (double)wfr_gl[i] + w * (0.5 / kPi);
+  cyc -= rint(cyc);
+  wfr[(size_t)k * NN + i] = (float)cyc;
 }
 
 // loss[k] = sum of the partials of pupil k (n_per each), FP64, fixed order.
@@ -986,6 +1010,7 @@ void tc_fourier_bwd_carve(char* base, size_t* off, int N, int nx, int ny, int nz
   out->V_lo = (uint16_t*)take((size_t)zc * 3 * N * 2 * ny * 2);
   out->gWz = (float*)take((size_t)zc * 6 * NN * 4);
   out->wfr = (float*)take((size_t)gp * NN * 4);
+  out->coef = (double*)take((size_t)gp * 66 * 8);
   out->gW = (float*)take((size_t)gp * NN * 4);
   const size_t parts = (size_t)gp * nz * ceil_div(nx, tc::BOUT) * ceil_div(ny, tc::BOUT) * 4;
   out->loss_part = (float*)take(parts * 4);
@@ -1012,6 +1037,13 @@ struct TcBwdMaps {
   CUtensorMap Ax_h, Ax_l, Ay_h, Ay_l, P_h, P_l, U_h, U_l;
   CUtensorMap AxH_h, AxH_l, AyH_h, AyH_l, R_h, R_l, V_h, V_l;
 };
+
+void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* Zt,
+                    const double* coef, int n_zern, const float* phase_map, int N, int nb,
+                    cudaStream_t s) {
+  tc::k_group_phase<<<dim3(ceil_div(N * N, 256), nb), 256, 0, s>>>(wfr_gl, Zt, coef, n_zern,
+                                                               phase_map, N * N, ops.wfr);
+}
 
 int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2* zz,
                         int N, int nx, int ny, int nz, int n_pupils, int zc, float scale,
@@ -1132,7 +1164,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
       if ((r = launch_gemm(m.AyH_h, m.AyH_l, m.V_h, m.V_l, p4, s))) return r;
       const int pk0 = z0 / nz, pk1 = (z0 + nzc - 1) / nz;
       k_gw_fold<<<dim3(ceil_div(N * N, 256), pk1 - pk0 + 1), 256, 0, s>>>(
-          ops.gWz, f.P_hi, f.P_lo, bf16, N, z0, nzc, nz, 2.f * scale / sP, gW);
+          ops.gWz, tn, zz, N, z0, nzc, nz, 2.f * scale, gW);
     }
   }
   if (target && loss)

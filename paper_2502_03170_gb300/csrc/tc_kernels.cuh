@@ -92,6 +92,7 @@ struct TcBwdOperands {
   uint16_t *V_hi, *V_lo;     // [zc][3][N][2 ny]
   float* gWz;                // [zc][3][re/im][N][N] Gh of a chunk (FP32)
   float* wfr;                // [group][N][N] phase tables of a group of pupils
+  double* coef;              // [group][<= 66] Zernike coefficients of the group
   float* gW;                 // [group][N][N] dL/dW_0 of the group
   float* loss_part;          // [group * nz * tiles * 4]
   int group;                 // pupils per group (planes of a chunk span pupils)
@@ -104,6 +105,12 @@ void tc_fourier_bwd_carve(char* base, size_t* off, int N, int nx, int ny, int nz
 // zoom matrices and their adjoints (once per call)
 int tc_fourier_bwd_setup(const TcBwdOperands& ops, int N, int nx, int ny, double dx,
                          double dy, double na_over_lambda, int precision, cudaStream_t s);
+// Phase tables of nb pupils into ops.wfr from the shared Gibson-Lanni phase
+// wfr_gl, the Zernike basis Zt and the coefficients coef [nb][n_zern] (device)
+// plus the free phase maps [nb][N][N] (device, or null).
+void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* Zt,
+                    const double* coef, int n_zern, const float* phase_map, int N, int nb,
+                    cudaStream_t s);
 // n_pupils (<= group) pupils whose phase tables are in ops.wfr: planes are
 // flat over (pupil, z); gW[k][N][N] = dL/dW_0 of pupil k (overwritten);
 // loss[k] (target only).  target / grad_intensity point at the group's first
