@@ -20,9 +20,11 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "tc_kernels.cuh"
+#include "tc_pair_ptx.cuh"
 #include "tc_ptx.cuh"
 #include "timing.cuh"
 
@@ -762,6 +764,392 @@ static int launch_gemm(const CUtensorMap& Ah, const CUtensorMap& Al,
   return cudaPeekAtLastError() == cudaSuccess ? PSF_OK : PSF_ERR_CUDA;
 }
 
+
+// --------------------------------------------------------------------------
+// CTA-pair form (cta_group::2) of the forward stages (modes 0 and 1).
+// A cluster of two CTAs owns a 256-row tile (two m-tiles): each CTA loads its
+// own 128 rows of the zoom-matrix operand and half (96 of 192 rows) of the
+// data operand, so a CTA receives 56 KB per K chunk instead of 80 KB; the
+// leader (rank 0) issues M = 256 MMAs that read both CTAs' shared memory and
+// write both CTAs' TMEM, and multicasts its commits to both CTAs' barriers.
+// Each CTA's epilogue reads its own 128 TMEM lanes exactly as in the single
+// CTA kernel and returns the accumulator to the leader (remote arrival).
+// Every wait is bounded as in k_split_cgemm.
+// --------------------------------------------------------------------------
+constexpr int PS_STAGES = 3;
+constexpr int PS_ACCS = 2;                            // accumulators in TMEM
+constexpr int PS_TMEM_COLS = 512;                     // two 192-column accumulators
+constexpr int PB_ROWS = BN / 2;                       // 96 data rows per CTA
+constexpr int PB_BYTES = PB_ROWS * BK * 2;            // 12 KB
+constexpr int PSTAGE_BYTES = 2 * A_BYTES + 2 * PB_BYTES;
+constexpr int PSMEM_BYTES = PS_STAGES * PSTAGE_BYTES + 1024 + 1024;
+
+PSF_D uint4 shfl_xor4(uint4 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  v.z = __shfl_xor_sync(0xffffffffu, v.z, m);
+  v.w = __shfl_xor_sync(0xffffffffu, v.w, m);
+  return v;
+}
+
+// Stores the 64-byte row pieces w[16] of the 32 lanes (row offset `off` in
+// 16-bit elements, valid rows only) after a 4 x 4 transpose of 16-byte units
+// within each group of four lanes (jj = lane & 3, k4 = lane & ~3).
+PSF_D void store_rows_t4(uint16_t* base, const uint32_t (&w)[16], int jj, int k4, int lane,
+                         bool row_ok, size_t off) {
+  uint4 u0 = make_uint4(w[0], w[1], w[2], w[3]), u1 = make_uint4(w[4], w[5], w[6], w[7]);
+  uint4 u2 = make_uint4(w[8], w[9], w[10], w[11]), u3 = make_uint4(w[12], w[13], w[14], w[15]);
+  const bool b1 = (jj & 2) != 0, b0 = (jj & 1) != 0;
+  // swap the off-diagonal 2 x 2 blocks (partner lane ^ 2)
+  uint4 s0 = b1 ? u0 : u2, s1 = b1 ? u1 : u3;
+  uint4 r0 = shfl_xor4(s0, 2), r1 = shfl_xor4(s1, 2);
+  if (b1) { u0 = r0; u1 = r1; } else { u2 = r0; u3 = r1; }
+  // then the off-diagonal units inside each 2 x 2 block (partner lane ^ 1)
+  s0 = b0 ? u0 : u1;
+  s1 = b0 ? u2 : u3;
+  r0 = shfl_xor4(s0, 1);
+  r1 = shfl_xor4(s1, 1);
+  if (b0) { u0 = r0; u2 = r1; } else { u1 = r0; u3 = r1; }
+  // u_i = unit jj of row k4 + i; row offsets and validity come from that lane
+  const uint4 us[4] = {u0, u1, u2, u3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const unsigned long long ro = __shfl_sync(0xffffffffu, (unsigned long long)off, k4 + i);
+    const int ok = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, k4 + i);
+    if (ok) *(uint4*)(base + ro + (size_t)jj * 8) = us[i];
+  }
+  (void)lane;
+}
+
+PSF_D void decode_pair(const Params& p, int t, int& plane, int& mp, int& nt) {
+  const int m_pairs = (p.m_tiles + 1) / 2;
+  const int tpp = m_pairs * p.n_tiles;
+  plane = t / tpp;
+  const int rem = t - plane * tpp;
+  nt = rem / m_pairs;
+  mp = rem - nt * m_pairs;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+k_split_cgemm_pair(const __grid_constant__ CUtensorMap mapA_hi,
+                   const __grid_constant__ CUtensorMap mapA_lo,
+                   const __grid_constant__ CUtensorMap mapB_hi,
+                   const __grid_constant__ CUtensorMap mapB_lo, const Params p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + PS_STAGES * PSTAGE_BYTES);
+  // bars: full[S], empty[S], tfull[2], tempty[2], drain
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * PS_STAGES + 5);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const bool leader = rank == 0;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (PS_STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * PS_STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * PS_STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * PS_STAGES + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PS_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 2 * EPI_THREADS);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc_pair(smem_u32(tmem_slot), PS_TMEM_COLS);
+  tmem_fence_before();
+  __syncthreads();
+  cluster_sync_all();          // both CTAs' barriers exist before any remote use
+  tmem_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int m_pairs = (p.m_tiles + 1) / 2;
+  const int total = p.planes * m_pairs * p.n_tiles;
+  const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    int issued = 0;
+    for (int t = cluster; t < total && ok; t += n_clusters) {
+      int plane, mp, nt;
+      decode_pair(p, t, plane, mp, nt);
+      const int mt = 2 * mp + (int)rank;
+      for (int kc = 0; kc < p.k_chunks; ++kc) {
+        if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const uint32_t base = smem_u32(smem + stage * PSTAGE_BYTES);
+        const uint32_t fb = mapa_shared(full_bar(stage), 0);   // the leader's barrier
+        if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * PSTAGE_BYTES);
+        tma_load_2d_pair(base, &mapA_hi, kc * BK, mt * BM, fb);
+        tma_load_2d_pair(base + A_BYTES, &mapA_lo, kc * BK, mt * BM, fb);
+        // this CTA's 96 rows of the 192 (3 channels x 64) data rows, 32 at a time
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const int r = (int)rank * PB_ROWS + i * 32;
+          const int ch = r >> 6, ro = r & 63;
+          tma_load_3d_pair(base + 2 * A_BYTES + i * 4096, &mapB_hi, kc * BK, nt * BOUT + ro,
+                           plane * 3 + ch, fb);
+          tma_load_3d_pair(base + 2 * A_BYTES + PB_BYTES + i * 4096, &mapB_lo, kc * BK,
+                           nt * BOUT + ro, plane * 3 + ch, fb);
+        }
+        ++issued;
+        if (++stage == PS_STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (!ok && leader) {
+      // drain: wait (bounded) for the copies still in flight before exiting
+      for (int k = 0; k < PS_STAGES && k < issued; ++k) {
+        if (--stage < 0) {
+          stage = PS_STAGES - 1;
+          phase ^= 1u;
+        }
+        mbar_drain_wait(full_bar(stage), phase);
+      }
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ------------------------------ MMA issuer (leader) -----------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int t = cluster; t < total && ok; t += n_clusters) {
+      if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.status)) {
+        ok = false;
+        break;
+      }
+      tmem_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ACC_COL);
+      for (int kc = 0; kc < p.k_chunks; ++kc) {
+        if (!mbar_wait(full_bar(stage), phase, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        tmem_fence_after();
+        const uint32_t base = smem_u32(smem + stage * PSTAGE_BYTES);
+        const uint64_t dAh = smem_desc<SWZ>(base), dAl = smem_desc<SWZ>(base + A_BYTES);
+        const uint64_t dBh = smem_desc<SWZ>(base + 2 * A_BYTES);
+        const uint64_t dBl = smem_desc<SWZ>(base + 2 * A_BYTES + PB_BYTES);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t adv = (uint64_t)((k * 32) >> 4);   // 16 elements = 32 bytes
+          const uint32_t first = (kc == 0 && k == 0) ? 0u : 1u;
+          mma_f16_pair(d_tmem, dAh + adv, dBh + adv, p.idesc, first);
+          mma_f16_pair(d_tmem, dAl + adv, dBh + adv, p.idesc, 1u);
+          mma_f16_pair(d_tmem, dAh + adv, dBl + adv, p.idesc, 1u);
+        }
+        mma_commit_pair(empty_bar(stage), 3);   // frees the stage in both CTAs
+        if (++stage == PS_STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (!ok) break;
+      mma_commit_pair(tfull_bar(acc), 3);       // accumulator ready in both CTAs
+      if (++acc == PS_ACCS) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+    mma_commit_pair(drain_bar, 1);
+    mbar_drain_wait(drain_bar, 0);
+  } else if (warp >= 2) {
+    // ------------------------------ epilogue ----------------------------------
+    const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
+    const int row = quad * 32 + lane;          // accumulator row = A row
+    const int oi = row >> 1, part = row & 1;   // output index within tile, re/im
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = cluster; t < total; t += n_clusters) {
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, p.status) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
+      tmem_fence_after();
+      int plane, mp, nt;
+      decode_pair(p, t, plane, mp, nt);
+      const int mt = 2 * mp + (int)rank;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * ACC_COL);
+      const int mo = mt * BOUT + oi;           // output index along m
+      if (p.mode == 0) {
+        // stage 1: U[plane][c][b = mo][part * N + p] = split(out_scale * D)
+        const bool row_ok = mo < p.m_out;
+        for (int c = 0; c < 3; ++c) {
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+            const int p0 = nt * BOUT + h * 32;
+            if (p0 >= p.n_rows) continue;                 // uniform over the warp
+            const size_t off = ((size_t)(plane * 3 + c) * p.m_out + mo) * (size_t)(2 * p.N) +
+                               (size_t)part * p.N + p0;
+            uint32_t hw[16], lw[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              uint16_t h0, l0, h1, l1;
+              split16(p.out_scale * __uint_as_float(r[j]), p.bf16, h0, l0);
+              split16(p.out_scale * __uint_as_float(r[j + 1]), p.bf16, h1, l1);
+              hw[j / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              lw[j / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+            if (p0 + 32 <= p.n_rows) {
+              // Each lane holds 64 bytes (four 16-byte units) of its own row.
+              // A 4 x 4 transpose of units inside every group of four lanes
+              // gives lane 4k + j the unit j of rows 4k .. 4k + 3, so every
+              // store instruction writes eight contiguous 64-byte row pieces.
+              const int jj = lane & 3, k4 = lane & ~3;
+              store_rows_t4(p.U_hi, hw, jj, k4, lane, row_ok, off);
+              store_rows_t4(p.U_lo, lw, jj, k4, lane, row_ok, off);
+            } else if (row_ok) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                if (p0 + j < p.n_rows) {
+                  p.U_hi[off + j] = (uint16_t)(hw[j / 2] >> (16 * (j & 1)));
+                  p.U_lo[off + j] = (uint16_t)(lw[j / 2] >> (16 * (j & 1)));
+                }
+              }
+            }
+          }
+        }
+      } else {
+        // stage 2: I[plane][a = mo][b] = (out_scale)^2 sum_c (Re^2 + Im^2)
+        float s[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) s[j] = 0.f;
+        const bool want_f = p.F != nullptr;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float v = __uint_as_float(r[j]);
+              s[h * 32 + j] = fmaf(v, v, s[h * 32 + j]);
+            }
+            if (want_f) {
+              // E = (-i) * out_scale * (Re + i Im): pair Re (even row) with Im
+              const int b0 = nt * BOUT + h * 32;
+              for (int j = 0; j < 32; ++j) {
+                const float v = p.out_scale * __uint_as_float(r[j]);
+                const float o = __shfl_xor_sync(0xffffffffu, v, 1);
+                const float re = part ? o : v, im = part ? v : o;
+                // even lane writes j < 16, odd lane j >= 16
+                if ((j < 16) == (part == 0) && mo < p.nx && b0 + j < p.ny)
+                  p.F[((size_t)(plane * 3 + c) * p.nx + mo) * p.ny + b0 + j] =
+                      make_float2(im, -re);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 64; ++j) s[j] += __shfl_xor_sync(0xffffffffu, s[j], 1);
+        const float sc = p.out_scale * p.out_scale;
+        const int b0 = nt * BOUT + part * 32;
+        // even lane (part 0) stores b0 + [0, 32), odd lane b0 + [32, 64):
+        // select with compile-time indices so s[] stays in registers
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] = sc * (part ? s[32 + j] : s[j]);
+        if (mo < p.nx && b0 < p.ny) {
+          float* dst = p.I + ((size_t)plane * p.nx + mo) * p.ny + b0;
+          if (b0 + 32 <= p.ny && (p.ny & 3) == 0) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+              ((float4*)dst)[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (b0 + j < p.ny) dst[j] = o[j];
+          }
+        }
+      }
+      tmem_fence_before();
+      mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));   // the leader's barrier
+      if (++acc == PS_ACCS) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+  }
+  tmem_fence_before();
+  __syncthreads();
+  cluster_sync_all();          // every MMA done and every TMEM read done in both CTAs
+  tmem_fence_after();
+  if (warp == 1) tmem_dealloc_pair(tmem_base, PS_TMEM_COLS);
+}
+
+// 3D map with 32-row boxes (one channel) for the pair kernel's data operand
+static bool make_map_3d_rows32(CUtensorMap* m, const uint16_t* base, int K, int rows,
+                               int planes) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)K * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)BK, 32, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, (void*)base, dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            SWZ == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static uint32_t make_idesc_pair(int bf16) {
+  const uint32_t fmt = bf16 ? 1u : 0u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)((2 * BM) >> 4) << 24);
+}
+
+// Pair launch of a forward stage (modes 0 and 1): Bh, Bl must be 32-row maps.
+static int launch_gemm_pair(const CUtensorMap& Ah, const CUtensorMap& Al,
+                            const CUtensorMap& Bh, const CUtensorMap& Bl, Params p,
+                            cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_split_cgemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PSMEM_BYTES) != cudaSuccess)
+      return PSF_ERR_CUDA;
+    attr = true;
+  }
+  p.idesc = make_idesc_pair(p.bf16);
+  const int total = p.planes * ((p.m_tiles + 1) / 2) * p.n_tiles;
+  int clusters = num_sms() / 2;
+  if (total < clusters) clusters = total;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(2 * clusters);
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = PSMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_split_cgemm_pair, Ah, Al, Bh, Bl, p) != cudaSuccess)
+    return PSF_ERR_CUDA;
+  return cudaPeekAtLastError() == cudaSuccess ? PSF_OK : PSF_ERR_CUDA;
+}
 }  // namespace tc
 
 // ==========================================================================
@@ -888,6 +1276,16 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
             make_map_3d(&mU_h, ops.U_hi, K, ny, 3 * zc) &&
             make_map_3d(&mU_l, ops.U_lo, K, ny, 3 * zc);
   if (!ok) return PSF_ERR_CUDA;
+  // CTA-pair contraction by default; PSF_TC_PAIR=0 in the environment selects
+  // the single-CTA kernel (same arithmetic, bitwise identical results)
+  const char* pe = getenv("PSF_TC_PAIR");
+  bool pair = !(pe && pe[0] == '0');
+  CUtensorMap mP2_h, mP2_l, mU2_h, mU2_l;
+  if (pair)
+    pair = make_map_3d_rows32(&mP2_h, ops.P_hi, K, N, 3 * zc) &&
+           make_map_3d_rows32(&mP2_l, ops.P_lo, K, N, 3 * zc) &&
+           make_map_3d_rows32(&mU2_h, ops.U_hi, K, ny, 3 * zc) &&
+           make_map_3d_rows32(&mU2_l, ops.U_lo, K, ny, 3 * zc);
   const uint32_t idesc = make_idesc(bf16);
   // The pupil planes of chunk i + 1 are built on a side stream while stage 2
   // of chunk i runs (stage 2 does not read them); the side stream forks after
@@ -926,7 +1324,12 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     int r;
     {
       TimingScope ts(kTimeStage1, s);
-      r = launch_gemm(mAy_h, mAy_l, mP_h, mP_l, p1, s);
+      r = pair ? launch_gemm_pair(mAy_h, mAy_l, mP2_h, mP2_l, p1, s) : PSF_ERR_CUDA;
+      if (r) {                   // no cluster launch: the single-CTA kernel
+        cudaGetLastError();
+        pair = false;
+        r = launch_gemm(mAy_h, mAy_l, mP_h, mP_l, p1, s);
+      }
     }
     if (r) return r;
     if (more) {
@@ -948,7 +1351,8 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     p2.F = fields ? fields + (size_t)z0 * 3 * nx * ny : nullptr;
     {
       TimingScope ts(kTimeStage2, s);
-      r = launch_gemm(mAx_h, mAx_l, mU_h, mU_l, p2, s);
+      r = pair ? launch_gemm_pair(mAx_h, mAx_l, mU2_h, mU2_l, p2, s)
+               : launch_gemm(mAx_h, mAx_l, mU_h, mU_l, p2, s);
     }
     if (r) return r;
     if (more) {

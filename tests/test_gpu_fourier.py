@@ -99,3 +99,21 @@ def test_rejects_bad_arguments(lib):
     d = dict(c["optics"], NA=1.6)
     with pytest.raises(Exception):
         api.fourier(d, 64, c["grid"])
+
+
+@pytest.mark.parametrize("nx,ny,N", [(150, 72, 48), (512, 512, 256)])
+def test_cta_pair_kernel_matches_single_cta(lib, nx, ny, N, monkeypatch):
+    """The CTA-pair contraction (default) and the single-CTA kernel compute
+    the same products in the same order: bitwise equal stacks, also with an
+    odd number of 64-row output tiles (the peer of the last pair has none)."""
+    c = W.fourier(n_pupil=N, nx=nx, nz=6)
+    grid = dict(c["grid"], ny=ny)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("PSF_TC_PAIR", mode)
+        out[mode] = api.fourier(c["optics"], N, grid, zernike=c["zernike"],
+                                precision="split_fp16").cpu().numpy()
+    assert np.array_equal(out["1"], out["0"])
+    Ir = of.psf_fourier(oracle_optics(c["optics"]), N, dict(grid, z=grid["z"][2:3]),
+                        zernike=c["zernike"])
+    assert max_rel(out["1"][2:3], Ir) <= 1e-5
