@@ -42,11 +42,11 @@ FP32_LANES_PER_SM = 128
 # command and the figures).  A figure holds only for the source it was taken
 # on: when the kernel's sources hash differently, traffic is reported as null.
 PROFILED_TRAFFIC = {
-    # 13-plane z-chunk (256^2 pupil, 512^2 px): 43.07 MB read + 0.29 MB written
+    # 13-plane z-chunk (256^2 pupil, 512^2 px), CTA-pair kernel: 43.06 MB read + 0.23 MB written
     "stage2_contraction_intensity": dict(
-        bytes_per_unit=(43.074e6 + 0.294e6) / 13, unit="plane",
-        sources=("tc_kernels.cu:k_split_cgemm", "tc_ptx.cuh"),
-        sha256_16="c7884e45e10d892c", precision="split_fp16"),
+        bytes_per_unit=(43.060e6 + 0.230e6) / 13, unit="plane",
+        sources=("tc_kernels.cu:k_split_cgemm_pair", "tc_ptx.cuh", "tc_pair_ptx.cuh"),
+        sha256_16="82c97c213905c89e", precision="split_fp16"),
     # 9442 slices of 128^2 px: 58.27 MB read + 557.25 MB written
     "bessel_radial_to_cartesian": dict(
         bytes_per_unit=(58.272e6 + 557.250e6) / 9442, unit="slice",
@@ -383,6 +383,20 @@ def run_gpu(args, rank, world, local_rank):
     if bound == "alu":
         roof["peak_source"] = ("FP32 CUDA cores: 152 SMs x 128 lanes x 2 FLOP x "
                                "%.0f MHz (max SM clock)" % float(peaks.get("sm_max_mhz", 2070.0)))
+    if bound == "tensor":
+        # the split forms compute FP32-accurate complex contractions from
+        # three 16-bit tensor products (hi.hi + lo.hi + hi.lo), so the peak of
+        # this dtype is the measured 16-bit tensor peak / 3; the executed
+        # tensor-pipe fraction is the same number
+        bf16 = peak
+        roof["peak"] = bf16 / 3.0
+        roof["frac"] = (achieved / roof["peak"]) if achieved else None
+        roof["peak_source"] = ("%s BF16 %.1f TFLOP/s (MEASURED_PEAKS.json) x 1/3: three "
+                               "16-bit tensor products per FP32-accurate MAC of the split "
+                               "form" % ("measured" if peaks_src == "measured" else "fallback",
+                                         bf16))
+        roof["tensor_pipe_executed_tflops"] = 3.0 * achieved if achieved else None
+        roof["tensor_pipe_frac_of_bf16_peak"] = (3.0 * achieved / bf16) if achieved else None
 
     result = {
         "metric": METRIC,
