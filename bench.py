@@ -246,6 +246,13 @@ def run_gpu(args, rank, world, local_rank):
         h2d = nz * 8 + 21 * 8            # z list (double-float) + Zernike row
         dom_class = 2                   # stage-2 contraction + |E|^2
         dom_work = 8.0 * 3 * nz * nx * ny * N      # algorithmic FLOP per step
+        if args.precision == "chirpz_fp32":
+            # two length-L FFTs (5 L log2 L real FLOP each) per x-line, 3 ny
+            # x-lines per plane
+            Lx = 256
+            while Lx < N + nx - 1:
+                Lx *= 2
+            dom_work = 3.0 * nz * ny * 2 * 5.0 * Lx * math.log2(Lx)
         cfg = {"workload": "fourier_vectorial_zstack", "n_pupil": N,
                "nx": nx, "ny": ny, "nz": nz, "dx_um": 0.010,
                "z_range_um": [-2.0, 2.0], "gibson_lanni": True,
@@ -354,7 +361,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_value = world * voxels / (ms_e2e / args.steps * 1e-3)
 
     n_dom, t_dom = counts[dom_class]
-    if args.workload == "fourier" and args.precision != "fp32":
+    if args.workload == "fourier" and args.precision not in ("fp32", "chirpz_fp32"):
         bound, unit = "tensor", "TFLOP/s"
         peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
         achieved = dom_work * args.steps / (t_dom * 1e-3) / 1e12 if t_dom else None
@@ -368,6 +375,8 @@ def run_gpu(args, rank, world, local_rank):
         peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
         achieved = dom_work * args.steps / (t_dom * 1e-3) / 1e9 if t_dom else None
     kname = {2: "stage2_contraction_intensity", 4: "bessel_radial_to_cartesian"}[dom_class]
+    if args.precision == "chirpz_fp32" and dom_class == 2:
+        kname = "chirpz_stage2_fft_zoom_x_intensity"
     per_step = max(n_dom // max(args.steps, 1), 1)
     units = (cfg["nz"] if dom_class == 2 else cfg["n_slices"]) / per_step
     traffic = profiled_traffic(kname, units, args.precision)
@@ -431,6 +440,7 @@ def run_gpu(args, rank, world, local_rank):
     if world == 1 and args.workload == "fourier":
         result["accuracy"] = fourier_accuracy(I_host, c)
         result["variants"] = fourier_variants(args, c, g, opt, N, ws, flush, stream)
+        result["pupil_scaling"] = pupil_scaling(c, ws, flush, stream)
     return result, rank
 
 
@@ -571,16 +581,53 @@ def fourier_accuracy(I, c, planes=(0, 64, 127)):
     return {"max_rel_err_vs_fp64_oracle": worst, "planes_checked": list(planes)}
 
 
+def pupil_scaling(c, ws, flush, stream, pupils=(512, 1024), steps=3):
+    """The zoom by chirp-Z FFTs against the dense split-FP16 contraction as
+    the pupil grows (same 512^2 x 128-plane stack): ms per stack and the
+    error on one plane against the FP64 oracle."""
+    import torch
+
+    from oracle import fourier as of
+    from oracle.optics import Optics
+    from paper_2502_03170_gb300 import api
+    opt = Optics.from_dict(c["optics"])
+    g = api.Grid(c["grid"])
+    o = torch.empty((g.c.nz, g.c.nx, g.c.ny), dtype=torch.float32, device=flush.device)
+    out = {}
+    for Np in pupils:
+        Ir = of.psf_fourier(opt, Np, dict(c["grid"], z=[c["grid"]["z"][64]]),
+                            zernike=c["zernike"])[0]
+        row = {}
+        for prec in ("chirpz_fp32", "split_fp16"):
+            for _ in range(2):
+                api.fourier(c["optics"], Np, g, zernike=c["zernike"], precision=prec,
+                            out=o, workspace=ws)
+            ms = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                api.fourier(c["optics"], Np, g, zernike=c["zernike"], precision=prec,
+                            out=o, workspace=ws)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+            err = float(np.max(np.abs(o[64].cpu().numpy() - Ir)) / np.max(Ir))
+            row[prec] = {"ms_per_stack": ms / steps, "max_rel_err": err}
+        out["n_pupil_%d" % Np] = row
+    return out
+
+
 def fourier_variants(args, c, g, opt, N, ws, flush, stream, steps=5):
-    """Every contraction precision on the same stack, and the scalar (Eq. 3)
-    and Fresnel (Eq. 6-7) models at split FP16: voxels/s and error against
-    the FP64 oracle of the same model."""
+    """Every contraction precision on the same stack (the chirp-Z FFT zoom
+    among them), and the scalar (Eq. 3) and Fresnel (Eq. 6-7) models at split
+    FP16: voxels/s and error against the FP64 oracle of the same model."""
     import torch
 
     from paper_2502_03170_gb300 import api
     out = {}
     runs = [("fp32", "fp32", {}), ("split_fp16", "split_fp16", {}),
-            ("split_bf16", "split_bf16", {}),
+            ("split_bf16", "split_bf16", {}), ("chirpz_fp32", "chirpz_fp32", {}),
             ("scalar_split_fp16", "split_fp16", {"scalar": True}),
             ("fresnel_split_fp16", "split_fp16", {"fresnel": True})]
     for name, prec, kw in runs:
@@ -616,7 +663,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier", choices=["fourier", "bessel"])
     ap.add_argument("--precision", default="split_fp16",
-                    choices=["fp32", "split_fp16", "split_bf16"])
+                    choices=["fp32", "split_fp16", "split_bf16", "chirpz_fp32"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
 

@@ -73,6 +73,13 @@ extern "C" {
                                    fp16 (power-of-two scaled), 3 products,
                                    FP32 accumulation in TMEM                  */
 #define PSF_PREC_SPLIT_BF16  2  /* same with bf16 hi+lo operands              */
+#define PSF_PREC_FP32_CHIRPZ 3  /* Fourier forward only: the zoom DFTs of
+                                   Eq. 8 by Bluestein's chirp-Z transform
+                                   (Sec. 4: FFT-based zoom for arbitrary pixel
+                                   size), FP32 shared-memory FFTs of length
+                                   L = 2^k >= max(256, n_pupil + n_out - 1),
+                                   L <= 4096 per direction; same discrete sum
+                                   as PSF_PREC_FP32, O(L log L) per line      */
 
 /* ---- flags ---------------------------------------------------------------- */
 #define PSF_PROJECT_AXISYMMETRIC 1  /* Bessel path: drop m != 0 Zernike terms

@@ -13,7 +13,8 @@ from . import _lib
 from ._lib import PsfGrid, PsfOptics, check
 
 PRECISIONS = {"fp32": _lib.PSF_PREC_FP32, "split_fp16": _lib.PSF_PREC_SPLIT_FP16,
-              "split_bf16": _lib.PSF_PREC_SPLIT_BF16}
+              "split_bf16": _lib.PSF_PREC_SPLIT_BF16,
+              "chirpz_fp32": _lib.PSF_PREC_FP32_CHIRPZ}
 
 
 def make_optics(d, flags=0):

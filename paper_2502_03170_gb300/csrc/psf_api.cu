@@ -10,6 +10,7 @@
 
 #include "bessel_backward.cuh"
 #include "bessel_kernels.cuh"
+#include "czt_kernels.cuh"
 #include "fourier_kernels.cuh"
 #include "optics_models.cuh"
 #include "tc_kernels.cuh"
@@ -224,9 +225,22 @@ struct FourierLayout {
   float2 *Ax, *Ay;
   float2 *P, *U;       // FP32 path
   TcOperands tc;       // split-precision path
+  float2* czt_words;   // chirp-Z path: x tables | y tables
+  size_t czt_wx, czt_wy;
+  float2* T;           // chirp-Z stage-1 output [zc][3][ny][N]
   int zc;
   size_t bytes;
 };
+
+static int czt_zchunk(int N, int ny, int nz) {
+  // stage-1 output of a chunk near 48 MB, so that stage 2 reads it from L2
+  const double per_z = 3.0 * 8.0 * (double)ny * N;
+  int zc = (int)(48.0 * 1048576.0 / per_z);
+  if (zc < 1) zc = 1;
+  if (zc > 64) zc = 64;
+  if (zc > nz) zc = nz;
+  return zc;
+}
 
 static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
                                     int precision) {
@@ -240,7 +254,13 @@ static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
   L.nodes.kl = c.take<float>(NN);
   L.zz = c.take<float2>(g->nz);
   L.zc = fourier_zchunk(N, g->nx, g->ny, g->nz);
-  if (precision == PSF_PREC_FP32) {
+  if (precision == PSF_PREC_FP32_CHIRPZ) {
+    L.czt_wx = czt_dir_words(N, g->nx);
+    L.czt_wy = czt_dir_words(N, g->ny);
+    L.czt_words = c.take<float2>(L.czt_wx + L.czt_wy);
+    L.zc = czt_zchunk(N, g->ny, g->nz);
+    L.T = c.take<float2>((size_t)L.zc * 3 * g->ny * N);
+  } else if (precision == PSF_PREC_FP32) {
     L.Ax = c.take<float2>((size_t)g->nx * N);
     L.Ay = c.take<float2>((size_t)g->ny * N);
     L.P = c.take<float2>((size_t)L.zc * 3 * NN);
@@ -268,9 +288,13 @@ static int check_fourier_args(const psf_optics* opt, int N, const psf_grid* g,
     if (!isfinite(g->z[i]) || fabs(g->z[i]) > 1e4)
       return fail(PSF_ERR_ARG, "z[%d] not finite or beyond 1e4 um", i);
   if (precision != PSF_PREC_FP32 && precision != PSF_PREC_SPLIT_FP16 &&
-      precision != PSF_PREC_SPLIT_BF16)
+      precision != PSF_PREC_SPLIT_BF16 && precision != PSF_PREC_FP32_CHIRPZ)
     return fail(PSF_ERR_PRECISION, "unknown precision mode %d", precision);
-  if (precision != PSF_PREC_FP32) {
+  if (precision == PSF_PREC_FP32_CHIRPZ) {
+    if (!czt_length(N, g->nx) || !czt_length(N, g->ny))
+      return fail(PSF_ERR_PRECISION, "chirp-Z: n_pupil + n_out - 1 = %d exceeds %d",
+                  N + (g->nx > g->ny ? g->nx : g->ny) - 1, kCztMaxL);
+  } else if (precision != PSF_PREC_FP32) {
     const char* why = tc_fourier_supported(N, g->nx, g->ny);
     if (why) return fail(PSF_ERR_PRECISION, "split precision: %s", why);
   }
@@ -361,7 +385,31 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
   const double f = opt->NA / opt->lambda;   // k s_max / (2 pi)
   const double ds = 2.0 * (opt->NA / opt->n_i) / N;
   const float scale = (float)(ds * ds / (2.0 * kPi));
-  if (precision == PSF_PREC_FP32) {
+  if (precision == PSF_PREC_FP32_CHIRPZ) {
+    // tables of both directions; the Eq. 8 prefactor C ds^2 = -i ds^2 / (2 pi)
+    // rides on the x post-chirp (stage 2 zooms along x)
+    std::vector<float2> words(L.czt_wx + L.czt_wy);
+    czt_build_dir(N, grid->nx, f, grid->dx, 0.0, -ds * ds / (2.0 * kPi), words.data());
+    czt_build_dir(N, grid->ny, f, grid->dy, 1.0, 0.0, words.data() + L.czt_wx);
+    cudaMemcpyAsync(L.czt_words, words.data(), words.size() * sizeof(float2),
+                    cudaMemcpyHostToDevice, s);
+    if ((r = cuda_check("chirp-Z tables"))) return r;
+    const CztDir cx = czt_dir_view(L.czt_words, N, grid->nx);
+    const CztDir cy = czt_dir_view(L.czt_words + L.czt_wx, N, grid->ny);
+    for (int z0 = 0; z0 < grid->nz; z0 += L.zc) {
+      const int nzc = grid->nz - z0 < L.zc ? grid->nz - z0 : L.zc;
+      {
+        TimingScope ts(kTimeStage1, s);
+        launch_czt_stage1(L.nodes, N, L.zz, z0, nzc, cx, cy, grid->ny, L.T, s);
+      }
+      float2* fz = fields ? (float2*)fields + (size_t)z0 * 3 * grid->nx * grid->ny : nullptr;
+      {
+        TimingScope ts(kTimeStage2, s);
+        launch_czt_stage2(L.T, N, grid->nx, grid->ny, nzc, cx,
+                          intensity + (size_t)z0 * grid->nx * grid->ny, fz, s);
+      }
+    }
+  } else if (precision == PSF_PREC_FP32) {
     {
       TimingScope ts(kTimeSetup, s);
       launch_twiddle(N, grid->nx, grid->dx, f, L.Ax, s);
@@ -476,6 +524,7 @@ extern "C" size_t psf_fourier_backward_workspace_size(const psf_optics* opt,
                                                        const psf_grid* grid,
                                                        int precision) {
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
+  if (precision == PSF_PREC_FP32_CHIRPZ) return 0;
   if (precision != PSF_PREC_FP32 && tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
     return 0;
   return backward_layout(nullptr, n_pupil, grid, precision).bytes;
@@ -490,6 +539,8 @@ extern "C" int psf_fourier_vectorial_backward(
   g_err[0] = 0;
   int r = check_fourier_args(opt, n_pupil, grid, precision);
   if (r) return r;
+  if (precision == PSF_PREC_FP32_CHIRPZ)
+    return fail(PSF_ERR_PRECISION, "the chirp-Z mode is forward only");
   if (precision != PSF_PREC_FP32) {
     if (const char* why = tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
       return fail(PSF_ERR_ARG, "%s", why);

@@ -6,8 +6,8 @@ Each case runs one warm-up call and one measured call of the library on
 cuda:0 with sizes small enough for a full ncu capture (well under a few GB on
 the device), then exits.  Cases:
 
-* ``fourier``  - 256^2 pupil, 512^2 px at 10 nm, 16 planes, Gibson-Lanni +
-  Zernike (one z-chunk of the benchmark stack).
+* ``fourier``  - 256^2 pupil (``--pupil`` to change it), 512^2 px at 10 nm,
+  16 planes, Gibson-Lanni + Zernike (one z-chunk of the benchmark stack).
 * ``bessel``   - ``--emitters`` (default 256) emitters of the batched Bessel
   workload (about 600 MB of output for 256, above the 126 MB L2).
 * ``bessel_backward`` - the adjoint of the same emitters with a seeded dL/dI
@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--emitters", type=int, default=256)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--nz", type=int, default=16)
+    ap.add_argument("--pupil", type=int, default=0, help="pupil size (0: the workload's)")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     if args.case == "fourier":
@@ -39,8 +40,9 @@ def main():
         g = api.Grid(c["grid"])
         ws = api.Workspace()
         out = torch.empty((g.c.nz, g.c.nx, g.c.ny), device="cuda")
+        n_pupil = args.pupil or c["n_pupil"]
         for _ in range(2):
-            api.fourier(c["optics"], c["n_pupil"], g, zernike=c["zernike"],
+            api.fourier(c["optics"], n_pupil, g, zernike=c["zernike"],
                         precision=args.precision, out=out, workspace=ws)
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()

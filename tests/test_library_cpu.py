@@ -111,3 +111,31 @@ def test_host_validation(cpu_lib):
         None, None, ctypes.c_void_p(16), None, ctypes.c_void_p(256), 1 << 30,
         None)
     assert r == _lib.PSF_ERR_ARG
+
+
+def test_chirpz_mode_validation(cpu_lib):
+    """The chirp-Z mode: forward only, FFT length per direction <= 4096."""
+    o = api.make_optics(W.optics_plain())
+    C = _lib.PSF_PREC_FP32_CHIRPZ
+    g = api.Grid(dict(nx=512, ny=512, dx=0.01, dy=0.01, z=[0.0, 0.1]))
+    size = cpu_lib.psf_fourier_workspace_size(ctypes.byref(o), 256, ctypes.byref(g.c), C)
+    # tables (2 x (2 L + N + n) + N/2 words) and the stage-1 chunk, two planes
+    assert size >= 2 * 3 * 512 * 256 * 8
+    assert cpu_lib.psf_fourier_backward_workspace_size(ctypes.byref(o), 256,
+                                                       ctypes.byref(g.c), C) == 0
+    r = cpu_lib.psf_fourier_vectorial_backward(
+        ctypes.byref(o), 256, ctypes.byref(g.c), 1, None, 0, None, C,
+        ctypes.c_void_p(16), None, None, ctypes.c_void_p(16), None,
+        ctypes.c_void_p(256), 1 << 30, None)
+    assert r == _lib.PSF_ERR_PRECISION
+    assert b"forward only" in cpu_lib.psf_last_error()
+    # N + n - 1 = 4096 fits, 4097 does not
+    ok = api.Grid(dict(nx=2049, ny=8, dx=0.01, dy=0.01, z=[0.0]))
+    assert cpu_lib.psf_fourier_workspace_size(ctypes.byref(o), 2048, ctypes.byref(ok.c), C) > 0
+    big = api.Grid(dict(nx=2050, ny=8, dx=0.01, dy=0.01, z=[0.0]))
+    assert cpu_lib.psf_fourier_workspace_size(ctypes.byref(o), 2048, ctypes.byref(big.c), C) == 0
+    r = cpu_lib.psf_fourier_vectorial(ctypes.byref(o), 2048, ctypes.byref(big.c), None, 0,
+                                      None, C, ctypes.c_void_p(16), None,
+                                      ctypes.c_void_p(256), 1 << 40, None)
+    assert r == _lib.PSF_ERR_PRECISION
+    assert b"chirp-Z" in cpu_lib.psf_last_error()
