@@ -245,6 +245,49 @@ int psf_bessel_vectorial(const psf_optics* base, int n_emitters,
                          float* intensity, void* profiles, void* workspace,
                          size_t ws_bytes, void* stream);
 
+/* ========================================================================== */
+/* Spherical strategy without axial symmetry: azimuthal harmonics.            */
+/* ========================================================================== */
+
+/* The spherical form (Sec. 3.4, Eq. 10-11) needs an axisymmetric pupil.  For
+ * any W(theta, phi) the pupil is expanded in azimuthal harmonics,
+ *   A e^{i W(theta, phi)} = sum_{|m| <= M} P_m(theta) e^{i m phi},
+ * P_m by a DFT over N_phi = 4 * (smallest power of two >= M + 1) azimuths;
+ * the far field of Eq. 6 has harmonics n = -2 .. 2, and the phi integral of
+ * Eq. 9 is exact by the Jacobi-Anger expansion:
+ *   E_c(rho, phi, z) = -i sum_{|l| <= M+2} i^l e^{i l phi} I_{c,l}(rho, z),
+ *   I_{c,l} = int sum_kinds coef_c g_n(theta) P_{l-n'}(theta)
+ *             J_l(k rho sin theta) e^{i k z cos theta} dtheta
+ * (g_n of Eq. 11 and its Fresnel / scalar forms; Gauss-Legendre in theta;
+ * I_{c,l} on the radial grid r_i = i r_max / (N_r - 1), linearly
+ * interpolated).  With m = 0 terms only this is Eq. 10-11.  Cost grows with
+ * the 2M + 5 orders; FP32 arithmetic.                                      */
+
+/* Truncation order: the largest over the emitters of the smallest M = K d
+ * with alpha^{K+1} / (K+1)! e^alpha <= tol, alpha = sum |c_j| N_j and d =
+ * max |m| over the emitter's m != 0 Noll terms (the l1 tail of the
+ * harmonics of e^{i W} beyond M).  zernike: HOST [n_em][n_zern].  Returns
+ * M >= 0, or a negative PSF_ERR_* code. */
+int psf_bessel_harmonic_order(const double* zernike, int n_em, int n_zern, double tol);
+
+/* Workspace for psf_bessel_vectorial_harmonic() (0 on invalid arguments). */
+size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_emitters,
+                                          int n_slices, int n_theta, int n_r,
+                                          int nx, int ny, int m_max);
+
+/* Batched PSFs with every Zernike term (any m) by the azimuthal harmonics
+ * |m| <= m_max (0 <= m_max <= 64).  Arguments as psf_bessel_vectorial()
+ * (device arrays depth [n_em], zernike [n_em][n_zern], z_offsets [n_em+1],
+ * z [n_slices]; intensity device [n_slices][nx][ny]); no free radial phase,
+ * no profiles output; the flags PSF_SCALAR / PSF_FRESNEL select the model
+ * (PSF_PROJECT_AXISYMMETRIC is ignored: no term is dropped). */
+int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_emitters,
+                                  const double* depth, const double* zernike,
+                                  int n_zern, const int* z_offsets, const double* z,
+                                  int n_slices, int n_theta, int n_r, int nx, int ny,
+                                  double dx, double dy, int m_max, float* intensity,
+                                  void* workspace, size_t ws_bytes, void* stream);
+
 /* Workspace for psf_bessel_vectorial_backward() (0 if the arguments are
  * invalid; the backward takes nx, ny <= 4096). */
 size_t psf_bessel_backward_workspace_size(const psf_optics* base, int n_emitters,

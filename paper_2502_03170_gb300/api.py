@@ -134,6 +134,48 @@ def fourier(optics, n_pupil, grid, zernike=None, phase_map=None,
     return (I, F) if fields else I
 
 
+def harmonic_order(zernike, tol=1e-7):
+    """Azimuthal truncation order M for the harmonic Bessel path: the largest
+    over the emitters of the tail bound (host computation in the library).
+    zernike: [n_em, n_zern] (host array or tensor)."""
+    lib = _lib.load()
+    zh = np.ascontiguousarray(
+        (zernike.detach().cpu().numpy() if torch.is_tensor(zernike) else np.asarray(zernike)),
+        dtype=np.float64)
+    if zh.ndim == 1:
+        zh = zh[None, :]
+    m = lib.psf_bessel_harmonic_order(zh.ctypes.data_as(ctypes.c_void_p), zh.shape[0],
+                                      zh.shape[1], float(tol))
+    if m < 0:
+        raise _lib.PsfError(m, lib.psf_last_error().decode())
+    return m
+
+
+def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
+                    m_max=None, tol=1e-7, workspace=None, stream=None):
+    """Batched vectorial PSFs by the spherical strategy for pupils without
+    axial symmetry (azimuthal harmonics |m| <= m_max of the pupil; m != 0
+    Zernike terms enter exactly).  m_max defaults to harmonic_order(zernike,
+    tol).  Same array conventions as bessel(); returns [n_slices, nx, ny]."""
+    lib = _lib.load()
+    if m_max is None:
+        m_max = 0 if zernike is None else harmonic_order(zernike, tol)
+    a = _BesselArgs(optics, depth, zernike, z_offsets, z, False, None)
+    o, dev = a.o, a.dev
+    ws = workspace or Workspace(dev)
+    need = lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), a.n_em, a.n_slices,
+                                                  n_theta, n_r, nx, ny, int(m_max))
+    if need == 0:
+        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+    buf = ws.get(need)
+    I = torch.empty((a.n_slices, nx, ny), dtype=torch.float32, device=dev)
+    check(lib, lib.psf_bessel_vectorial_harmonic(
+        ctypes.byref(o), a.n_em, _ptr(a.depth), _ptr(a.zern), a.n_zern, _ptr(a.offs),
+        _ptr(a.z), a.n_slices, n_theta, n_r, nx, ny, float(dx), float(dy), int(m_max),
+        _ptr(I), _ptr(buf), buf.numel(), _stream(stream)))
+    return I
+
+
 class _BesselArgs:
     """Device copies of the per-emitter inputs of a Bessel call."""
 

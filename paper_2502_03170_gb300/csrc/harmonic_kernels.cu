@@ -1,0 +1,301 @@
+// Azimuthal-harmonic (non-axisymmetric) Bessel strategy: pupil harmonics,
+// J_n table, batched radial contraction per order and the Cartesian
+// epilogue (FP32 arithmetic, FP64 tables).
+#include "harmonic_kernels.cuh"
+
+namespace psf {
+
+namespace {
+
+// kinds: P index = l + shift, weight g_n
+PSF_D int kind_shift(int kind) {
+  return kind == 1 ? -2 : kind == 2 ? 2 : kind == 3 ? -1 : kind == 4 ? 1 : 0;
+}
+PSF_D int kind_g(int kind) { return kind == 0 ? 0 : (kind <= 2 ? 2 : 1); }
+
+// ---------------------------------------------------------------------------
+// One CTA per (theta node, emitter): e^{i W_na(theta, phi_k)} on the N_phi
+// azimuths, its DFT (harmonics |m| <= M) times the axisymmetric integrand,
+// then the channel/order mixtures Bh.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restrict__ zern,
+             const float* __restrict__ Zr, const float2* __restrict__ cs,
+             float2* __restrict__ Bh) {
+  extern __shared__ float2 sh[];
+  float2* Ek = sh;                 // [n_phi]
+  float2* Pm = sh + p.n_phi;       // [2 M + 1]
+  const int j = blockIdx.x, e = blockIdx.y;
+  const int nP = 2 * p.m_max + 1, mask = p.n_phi - 1;
+  const size_t ej = (size_t)e * p.n_theta + j;
+  for (int k = threadIdx.x; k < p.n_phi; k += blockDim.x) {
+    float w = 0.f;
+    for (int q = 0; q < p.n_na; ++q) {
+      const float c = (float)zern[(size_t)e * p.n_zern + p.na_j[q] - 1];
+      if (c == 0.f) continue;
+      const float2 a = cs[(p.na_m[q] * k) & mask];   // e^{i m phi_k}
+      w = fmaf(c * Zr[q * p.n_theta + j], p.na_cos[q] ? a.x : a.y, w);
+    }
+    float sn, cn;
+    sincosf(w, &sn, &cn);
+    Ek[k] = make_float2(cn, sn);
+  }
+  __syncthreads();
+  const float amp = et.amp[ej];
+  const float2 base = cis_cycles(et.wfr[ej]);
+  const float scale = amp / (float)p.n_phi;
+  for (int mi = threadIdx.x; mi < nP; mi += blockDim.x) {
+    const int m = mi - p.m_max;
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < p.n_phi; ++k) {
+      const float2 a = cs[(m * k) & mask];   // e^{i m phi_k}; times conj
+      const float2 x = Ek[k];
+      re = fmaf(x.x, a.x, fmaf(x.y, a.y, re));
+      im = fmaf(x.y, a.x, fmaf(-x.x, a.y, im));
+    }
+    const float2 h = cmul(base, make_float2(re, im));
+    Pm[mi] = make_float2(scale * h.x, scale * h.y);
+  }
+  __syncthreads();
+  const bool ok = et.valid[e] != 0;
+  const int L = p.m_max + 2;
+  for (int o = threadIdx.x; o < 3 * p.n_ord; o += blockDim.x) {
+    const int c = o / p.n_ord, li = o - c * p.n_ord, l = li - L;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int kind = 0; kind < 5; ++kind) {
+      const int m = l + kind_shift(kind);
+      if (m < -p.m_max || m > p.m_max) continue;
+      const double cr = p.coef[c][kind][0], ci = p.coef[c][kind][1];
+      if (cr == 0.0 && ci == 0.0) continue;
+      const int gk = kind_g(kind);
+      const float2 g = make_float2((float)t.g[(size_t)(2 * gk) * p.n_theta + j],
+                                   (float)t.g[(size_t)(2 * gk + 1) * p.n_theta + j]);
+      const float2 v = cmul(cmul(make_float2((float)cr, (float)ci), g), Pm[m + p.m_max]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    if (l < 0 && ((-l) & 1)) acc = make_float2(-acc.x, -acc.y);   // J_{-n} = (-1)^n J_n
+    Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j] =
+        ok ? acc : make_float2(0.f, 0.f);
+  }
+}
+
+__global__ void k_harm_jtab(HarmParams p, ThetaTable t, float* __restrict__ Jt) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)(p.m_max + 3) * p.n_r * p.n_theta;
+  if (idx >= total) return;
+  const int j = (int)(idx % p.n_theta);
+  const long long rest = idx / p.n_theta;
+  const int i = (int)(rest % p.n_r), n = (int)(rest / p.n_r);
+  const double x = p.k * (i * p.dr) * t.sin_t[j];
+  Jt[idx] = (float)(t.w[j] * jn(n, x));
+}
+
+// D[s][j] = e^{i k z_s cos theta_j} for the slices of a chunk
+__global__ void k_harm_defocus(int n_theta, ThetaTable t, const float2* __restrict__ zz,
+                               int s0, int ns, float2* __restrict__ D) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)ns * n_theta) return;
+  const int sl = (int)(idx / n_theta), j = (int)(idx - (long long)sl * n_theta);
+  const float2 z = zz[s0 + sl];
+  D[idx] = cis_cycles(frac_mul_add(f2x{t.kh[j], t.kl[j]}, f2x{z.x, z.y}, 0.f));
+}
+
+// ---------------------------------------------------------------------------
+// Radial contraction, one order per grid z: C[i][(s, c)] = sum_j Jt[|l|][i][j]
+// D[s][j] Bh[e(s)][c][l'][j].  Tile 64 radii x 32 columns, K step 16, 256
+// threads with 4 x 2 complex accumulators.
+// ---------------------------------------------------------------------------
+constexpr int HP_BM = 64, HP_BN = 32, HP_BK = 16;
+
+__global__ void __launch_bounds__(256)
+k_harm_profiles(HarmParams p, const float* __restrict__ Jt, const float2* __restrict__ Bh,
+                const int* __restrict__ slice_em, const int* __restrict__ valid,
+                const float2* __restrict__ D, int s0, int ns, float2* __restrict__ prof) {
+  __shared__ float As[HP_BK][HP_BM + 1];
+  __shared__ float2 Bs[HP_BK][HP_BN + 1];
+  const int li = blockIdx.z, L = p.m_max + 2;
+  const int n = li >= L ? li - L : L - li;
+  const int i0 = blockIdx.y * HP_BM, c0 = blockIdx.x * HP_BN;
+  const int ncol = 3 * ns;
+  const float* A = Jt + (size_t)n * p.n_r * p.n_theta;
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  float2 acc[4][2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < p.n_theta; k0 += HP_BK) {
+    for (int x = tid; x < HP_BM * HP_BK; x += 256) {
+      const int r = x / HP_BK, kk = x - r * HP_BK;
+      const int gi = i0 + r, gk = k0 + kk;
+      As[kk][r] = (gi < p.n_r && gk < p.n_theta) ? A[(size_t)gi * p.n_theta + gk] : 0.f;
+    }
+    for (int x = tid; x < HP_BN * HP_BK; x += 256) {
+      const int col = x / HP_BK, kk = x - col * HP_BK;
+      const int gc = c0 + col, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gc < ncol && gk < p.n_theta) {
+        const int sl = gc / 3, c = gc - 3 * sl;
+        const int e = slice_em[s0 + sl];
+        if (e >= 0 && valid[e])
+          v = cmul(D[(size_t)sl * p.n_theta + gk],
+                   Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + gk]);
+      }
+      Bs[kk][col] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < HP_BK; ++kk) {
+      float a[4];
+      float2 b[2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = As[kk][tr + 16 * q];
+      b[0] = Bs[kk][tc];
+      b[1] = Bs[kk][tc + 16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          acc[q][u].x = fmaf(a[q], b[u].x, acc[q][u].x);
+          acc[q][u].y = fmaf(a[q], b[u].y, acc[q][u].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int gc = c0 + tc + 16 * u;
+    if (gc >= ncol) continue;
+    const int sl = gc / 3, c = gc - 3 * sl;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = i0 + tr + 16 * q;
+      if (gi < p.n_r)
+        prof[(((size_t)sl * 3 + c) * p.n_ord + li) * p.n_r + gi] = acc[q][u];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue: one thread per quarter pixel (a < ceil(nx/2), b < ceil(ny/2)) of
+// one slice and its mirrors (+-x, +-y), which share the radius and so the
+// interpolated I_{c,l}.  With T_l = (i e^{i phi})^l at (x, y):
+//   (x, y): sum T_l v_l          (-x, -y): sum (-1)^l T_l v_l
+//   (-x, y): sum conj(T_l) v_l   (x, -y): sum (-1)^l conj(T_l) v_l,
+// kept as even and odd partial sums.  T_l by forward and backward
+// recurrences from l = 0 (the large low orders carry the least rounding);
+// |E_c|^2 = |sum|^2 (the -i prefactor has modulus 1).
+// ---------------------------------------------------------------------------
+struct MirrorAcc {
+  float2 te, to, ce, co;   // sums of T v and conj(T) v over even / odd l
+};
+
+PSF_D void harm_add(MirrorAcc& m, float2 t, float2 v, bool odd) {
+  const float2 a = cmul(t, v);
+  const float2 b = cmul(make_float2(t.x, -t.y), v);
+  if (odd) {
+    m.to.x += a.x; m.to.y += a.y; m.co.x += b.x; m.co.y += b.y;
+  } else {
+    m.te.x += a.x; m.te.y += a.y; m.ce.x += b.x; m.ce.y += b.y;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
+                 const int* __restrict__ slice_em, const int* __restrict__ valid, int s0,
+                 float* __restrict__ I) {
+  const int sl = blockIdx.y, s = s0 + sl;
+  const int e = slice_em[s];
+  if (e < 0 || !valid[e]) return;
+  const int ha = (p.nx + 1) / 2, hb = (p.ny + 1) / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ha * hb) return;
+  const int a = idx / hb, b = idx - a * hb;
+  const double x = (a - 0.5 * (p.nx - 1)) * p.dx, y = (b - 0.5 * (p.ny - 1)) * p.dy;
+  const double rho = sqrt(x * x + y * y);
+  const double tt = p.dr > 0 ? rho / p.dr : 0.0;   // r_max = 0: all r_i = 0
+  int i0 = (int)floor(tt);
+  i0 = i0 < 0 ? 0 : (i0 > p.n_r - 2 ? p.n_r - 2 : i0);
+  const float f = (float)(tt - i0);
+  const float cp = rho > 0 ? (float)(x / rho) : 1.f, sp = rho > 0 ? (float)(y / rho) : 0.f;
+  const float2 w = make_float2(-sp, cp);    // i e^{i phi}
+  const float2 wc = make_float2(-sp, -cp);  // its inverse
+  const int L = p.m_max + 2;
+  const float2* base = prof + (size_t)sl * 3 * p.n_ord * p.n_r + i0;
+  MirrorAcc acc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = MirrorAcc{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  float2 tf = make_float2(1.f, 0.f);
+  for (int l = 0; l <= L; ++l) {
+    const bool odd = l & 1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2* q = base + ((size_t)c * p.n_ord + (l + L)) * p.n_r;
+      const float2 u = q[0], v = q[1];
+      harm_add(acc[c], tf, make_float2(fmaf(f, v.x - u.x, u.x), fmaf(f, v.y - u.y, u.y)), odd);
+    }
+    tf = cmul(tf, w);
+  }
+  tf = wc;
+  for (int l = -1; l >= -L; --l) {
+    const bool odd = (-l) & 1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2* q = base + ((size_t)c * p.n_ord + (l + L)) * p.n_r;
+      const float2 u = q[0], v = q[1];
+      harm_add(acc[c], tf, make_float2(fmaf(f, v.x - u.x, u.x), fmaf(f, v.y - u.y, u.y)), odd);
+    }
+    tf = cmul(tf, wc);
+  }
+  float i_pp = 0.f, i_mm = 0.f, i_mp = 0.f, i_pm = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const MirrorAcc& m = acc[c];
+    const float2 pp = make_float2(m.te.x + m.to.x, m.te.y + m.to.y);
+    const float2 mm = make_float2(m.te.x - m.to.x, m.te.y - m.to.y);
+    const float2 mp = make_float2(m.ce.x + m.co.x, m.ce.y + m.co.y);
+    const float2 pm = make_float2(m.ce.x - m.co.x, m.ce.y - m.co.y);
+    i_pp = fmaf(pp.x, pp.x, fmaf(pp.y, pp.y, i_pp));
+    i_mm = fmaf(mm.x, mm.x, fmaf(mm.y, mm.y, i_mm));
+    i_mp = fmaf(mp.x, mp.x, fmaf(mp.y, mp.y, i_mp));
+    i_pm = fmaf(pm.x, pm.x, fmaf(pm.y, pm.y, i_pm));
+  }
+  float* out = I + (size_t)s * p.nx * p.ny;
+  const int am = p.nx - 1 - a, bm = p.ny - 1 - b;
+  out[(size_t)a * p.ny + b] = i_pp;
+  out[(size_t)am * p.ny + bm] = i_mm;
+  out[(size_t)am * p.ny + b] = i_mp;
+  out[(size_t)a * p.ny + bm] = i_pm;
+}
+
+}  // namespace
+
+void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const double* zern,
+                       const float* Zr, const float2* cs, float2* Bh, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * ((size_t)p.n_phi + 2 * p.m_max + 1);
+  k_harm_pupil<<<dim3(p.n_theta, p.n_em), 128, smem, s>>>(p, t, e, zern, Zr, cs, Bh);
+}
+
+void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t s) {
+  const long long total = (long long)(p.m_max + 3) * p.n_r * p.n_theta;
+  k_harm_jtab<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, t, Jt);
+}
+
+void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,
+                          const float2* Bh, const int* slice_em, const int* valid,
+                          const float2* zz, int s0, int ns, float2* D, float2* prof,
+                          cudaStream_t s) {
+  const long long nd = (long long)ns * p.n_theta;
+  k_harm_defocus<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(p.n_theta, t, zz, s0, ns, D);
+  const dim3 grid(ceil_div(3 * ns, HP_BN), ceil_div(p.n_r, HP_BM), p.n_ord);
+  k_harm_profiles<<<grid, 256, 0, s>>>(p, Jt, Bh, slice_em, valid, D, s0, ns, prof);
+}
+
+void launch_harm_intensity(const HarmParams& p, const float2* prof, const int* slice_em,
+                           const int* valid, int s0, int ns, float* I, cudaStream_t s) {
+  const int quarter = ((p.nx + 1) / 2) * ((p.ny + 1) / 2);
+  const dim3 grid(ceil_div(quarter, 256), ns);
+  k_harm_intensity<<<grid, 256, 0, s>>>(p, prof, slice_em, valid, s0, I);
+}
+
+}  // namespace psf

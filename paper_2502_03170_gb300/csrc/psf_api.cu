@@ -11,6 +11,7 @@
 #include "bessel_backward.cuh"
 #include "bessel_kernels.cuh"
 #include "czt_kernels.cuh"
+#include "harmonic_kernels.cuh"
 #include "fourier_kernels.cuh"
 #include "optics_models.cuh"
 #include "tc_kernels.cuh"
@@ -1226,4 +1227,211 @@ extern "C" int psf_bessel_vectorial_backward(
                              grad_phase_theta, grad_zernike, grad_depth, s);
   }
   return cuda_check("psf_bessel_vectorial_backward launch");
+}
+
+// ===========================================================================
+// Spherical strategy without axial symmetry: azimuthal harmonics of the
+// pupil (Eq. 9 with the Jacobi-Anger expansion; the harmonics of Eq. 6).
+// ===========================================================================
+static int harm_n_phi(int m_max) {
+  int p = 1;
+  while (p < m_max + 1) p *= 2;
+  return 4 * p;
+}
+
+struct HarmLayout {
+  BesselLayout b;
+  float2* cs;      // [n_phi] e^{2 pi i k / n_phi}
+  float* Zr;       // [kHarmMaxNA][n_theta] N_j R_n^{|m|}(sin theta / s_max)
+  float2* Bh;      // [n_em][3][n_ord][n_theta]
+  float* Jt;       // [m_max + 3][n_r][n_theta]
+  float2* D;       // [chunk][n_theta]
+  float2* prof;    // [chunk][3][n_ord][n_r]
+  int chunk;
+  size_t bytes;
+};
+
+static HarmLayout harm_layout(void* ws, int n_em, int n_slices, int n_theta, int n_r,
+                              int nx, int ny, int m_max) {
+  HarmLayout H;
+  memset(&H, 0, sizeof(H));
+  H.b = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, false, PSF_PREC_FP32);
+  Carver c(ws);
+  c.off = H.b.bytes;
+  const int n_ord = 2 * m_max + 5;
+  H.cs = c.take<float2>(harm_n_phi(m_max));
+  H.Zr = c.take<float>((size_t)kHarmMaxNA * n_theta);
+  H.Bh = c.take<float2>((size_t)n_em * 3 * n_ord * n_theta);
+  H.Jt = c.take<float>((size_t)(m_max + 3) * n_r * n_theta);
+  // profiles of a slice chunk near 256 MB
+  const double per_slice = 8.0 * (3.0 * n_ord * n_r + n_theta);
+  long long chunk = (long long)(256.0 * 1048576.0 / per_slice);
+  if (chunk > n_slices) chunk = n_slices;
+  if (chunk > 65535) chunk = 65535;
+  if (chunk < 1) chunk = 1;
+  H.chunk = (int)chunk;
+  H.D = c.take<float2>((size_t)chunk * n_theta);
+  H.prof = c.take<float2>((size_t)chunk * 3 * n_ord * n_r);
+  H.bytes = align_up(c.off, 256);
+  return H;
+}
+
+extern "C" int psf_bessel_harmonic_order(const double* zernike, int n_em, int n_zern,
+                                         double tol) {
+  g_err[0] = 0;
+  if (n_em < 0 || n_zern < 0 || n_zern > 66 || (n_em > 0 && n_zern > 0 && !zernike) ||
+      !(tol > 0.0) || !(tol < 1.0))
+    return fail(PSF_ERR_ARG, "psf_bessel_harmonic_order: bad arguments");
+  int best = 0;
+  for (int e = 0; e < n_em; ++e) {
+    double alpha = 0.0;
+    int d = 0;
+    for (int j = 1; j <= n_zern; ++j) {
+      const double c = zernike[(size_t)e * n_zern + j - 1];
+      int n, m;
+      noll_nm(j, &n, &m);
+      if (m == 0 || c == 0.0) continue;
+      if (!isfinite(c)) return fail(PSF_ERR_ARG, "zernike not finite");
+      alpha += fabs(c) * sqrt(2.0 * (n + 1.0));
+      d = abs(m) > d ? abs(m) : d;
+    }
+    if (d == 0) continue;
+    // tail of e^{i W}: sum_{k > K} alpha^k / k! <= alpha^{K+1} / (K+1)! e^alpha
+    int K = 0;
+    double term = alpha;
+    while (term * exp(alpha) > tol && K < 1000) {
+      ++K;
+      term *= alpha / (K + 1);
+    }
+    const int M = (K > 1 ? K : 1) * d;
+    best = M > best ? M : best;
+  }
+  return best;
+}
+
+static int check_harm_args(int m_max) {
+  if (m_max < 0 || m_max > kHarmMaxM)
+    return fail(PSF_ERR_ARG, "m_max %d outside [0, %d]", m_max, kHarmMaxM);
+  return PSF_OK;
+}
+
+extern "C" size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_em,
+                                                     int n_slices, int n_theta, int n_r,
+                                                     int nx, int ny, int m_max) {
+  if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, PSF_PREC_FP32)) return 0;
+  if (check_harm_args(m_max)) return 0;
+  return harm_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, m_max).bytes;
+}
+
+extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
+                                             const double* depth, const double* zernike,
+                                             int n_zern, const int* z_offsets, const double* z,
+                                             int n_slices, int n_theta, int n_r, int nx,
+                                             int ny, double dx, double dy, int m_max,
+                                             float* intensity, void* workspace,
+                                             size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
+                            n_theta, n_r, nx, ny, dx, dy, PSF_PREC_FP32);
+  if (r) return r;
+  if ((r = check_harm_args(m_max))) return r;
+  if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");
+  if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
+  HarmLayout H = harm_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny, m_max);
+  if (ws_bytes < H.bytes)
+    return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, H.bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the emitter table carries the axisymmetric part (m != 0 terms dropped
+  // there; they enter through the harmonics)
+  psf_optics b2 = *base;
+  b2.flags |= PSF_PROJECT_AXISYMMETRIC;
+  BesselRun R;
+  r = bessel_prepare(&b2, n_em, depth, zernike, n_zern, nullptr, z_offsets, z, n_slices,
+                     n_theta, n_r, nx, ny, dx, dy, PSF_PREC_FP32, false, H.b, workspace, &R, s);
+  if (r) return r;
+  const BesselParams& bp = R.bp;
+  HarmParams hp;
+  memset(&hp, 0, sizeof(hp));
+  hp.n_theta = n_theta;
+  hp.n_r = n_r;
+  hp.nx = nx;
+  hp.ny = ny;
+  hp.n_em = n_em;
+  hp.n_zern = n_zern;
+  hp.m_max = m_max;
+  hp.n_phi = harm_n_phi(m_max);
+  hp.n_ord = 2 * m_max + 5;
+  hp.k = bp.k;
+  hp.dr = bp.dr;
+  hp.r_max = bp.r_max;
+  hp.dx = dx;
+  hp.dy = dy;
+  // host tables: m != 0 Zernike radial values at the nodes, azimuth phasors
+  const double s_max = base->NA / base->n_i;
+  std::vector<double> gx, gw;
+  gauss_legendre(n_theta, gx, gw);
+  const double th_max = asin(s_max);
+  std::vector<float> zr((size_t)kHarmMaxNA * n_theta, 0.f);
+  for (int j = 1; j <= n_zern; ++j) {
+    int n, m;
+    noll_nm(j, &n, &m);
+    if (m == 0) continue;
+    const int q = hp.n_na++;
+    hp.na_j[q] = j;
+    hp.na_m[q] = abs(m);
+    hp.na_cos[q] = m > 0 ? 1 : 0;
+    double rc[kZernMaxOrder + 1];
+    zernike_radial_coeffs(n, abs(m), rc);
+    for (int t = 0; t < n_theta; ++t) {
+      const double rho = sin(0.5 * th_max * (gx[t] + 1.0)) / s_max;
+      double v = 0;
+      for (int k = kZernMaxOrder; k >= 0; --k) v = v * rho + rc[k];
+      zr[(size_t)q * n_theta + t] = (float)v;
+    }
+  }
+  std::vector<float2> cs(hp.n_phi);
+  for (int k = 0; k < hp.n_phi; ++k)
+    cs[k] = make_float2((float)cos(2.0 * kPi * k / hp.n_phi), (float)sin(2.0 * kPi * k / hp.n_phi));
+  // channel x kind coefficients for the model's Jones vector (p_x, p_y)
+  const double pxr = bp.pol[0], pxi = bp.pol[1], pyr = bp.pol[2], pyi = bp.pol[3];
+  auto set = [&](int c, int kind, double re, double im) {
+    hp.coef[c][kind][0] = re;
+    hp.coef[c][kind][1] = im;
+  };
+  // (p_x - i p_y) and (p_x + i p_y)
+  const double am_r = pxr + pyi, am_i = pxi - pyr;
+  const double ap_r = pxr - pyi, ap_i = pxi + pyr;
+  set(0, 0, 0.5 * pxr, 0.5 * pxi);
+  set(0, 1, 0.25 * am_r, 0.25 * am_i);
+  set(0, 2, 0.25 * ap_r, 0.25 * ap_i);
+  set(1, 0, 0.5 * pyr, 0.5 * pyi);
+  // (-i p_x - p_y) / 4 and (i p_x - p_y) / 4
+  set(1, 1, 0.25 * (pxi - pyr), 0.25 * (-pxr - pyi));
+  set(1, 2, 0.25 * (-pxi - pyr), 0.25 * (pxr - pyi));
+  set(2, 3, -0.5 * am_r, -0.5 * am_i);
+  set(2, 4, -0.5 * ap_r, -0.5 * ap_i);
+  cudaMemcpyAsync(H.Zr, zr.data(), zr.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(H.cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice, s);
+  if ((r = cuda_check("harmonic tables"))) return r;
+  {
+    TimingScope ts(kTimeSetup, s);
+    launch_harm_pupil(hp, R.tt, H.b.et, n_zern > 0 ? zernike : nullptr, H.Zr, H.cs, H.Bh, s);
+  }
+  {
+    TimingScope ts(kTimeSetup, s);
+    launch_harm_jtab(hp, R.tt, H.Jt, s);
+  }
+  for (int s0 = 0; s0 < n_slices; s0 += H.chunk) {
+    const int ns = n_slices - s0 < H.chunk ? n_slices - s0 : H.chunk;
+    {
+      TimingScope ts(kTimeBesselRadial, s);
+      launch_harm_profiles(hp, R.tt, H.Jt, H.Bh, H.b.slice_em, H.b.et.valid, H.b.zz, s0,
+                           ns, H.D, H.prof, s);
+    }
+    {
+      TimingScope ts(kTimeBesselEpilogue, s);
+      launch_harm_intensity(hp, H.prof, H.b.slice_em, H.b.et.valid, s0, ns, intensity, s);
+    }
+  }
+  return cuda_check("psf_bessel_vectorial_harmonic launch");
 }

@@ -139,3 +139,28 @@ def test_chirpz_mode_validation(cpu_lib):
                                       ctypes.c_void_p(256), 1 << 40, None)
     assert r == _lib.PSF_ERR_PRECISION
     assert b"chirp-Z" in cpu_lib.psf_last_error()
+
+
+def test_harmonic_order_and_validation(cpu_lib):
+    """The truncation order of the library's host helper is the tail bound
+    the oracle states; argument checks run before any launch."""
+    from oracle import bessel_harmonic as bh
+    c = W.bessel(n_emitters=40)
+    zs = np.ascontiguousarray(c["zernike"], dtype=np.float64)
+    for tol in (1e-5, 1e-7, 1e-9):
+        m = cpu_lib.psf_bessel_harmonic_order(zs.ctypes.data_as(ctypes.c_void_p),
+                                              zs.shape[0], zs.shape[1], tol)
+        assert m == max(bh.harmonic_order(z, tol) for z in zs)
+    assert cpu_lib.psf_bessel_harmonic_order(None, 0, 0, 1e-7) == 0
+    assert cpu_lib.psf_bessel_harmonic_order(zs.ctypes.data_as(ctypes.c_void_p), 4,
+                                             zs.shape[1], 0.0) == _lib.PSF_ERR_ARG
+    o = api.make_optics(W.optics_plain())
+    assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
+                                                      8, 8, 12) > 0
+    assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
+                                                      8, 8, 65) == 0
+    d = ctypes.c_void_p(16)
+    r = cpu_lib.psf_bessel_vectorial_harmonic(ctypes.byref(o), 4, d, d, 21, d, d, 16, 64,
+                                              64, 8, 8, 0.02, 0.02, -1, d,
+                                              ctypes.c_void_p(256), 1 << 30, None)
+    assert r == _lib.PSF_ERR_ARG
