@@ -441,6 +441,7 @@ def run_gpu(args, rank, world, local_rank):
         result["accuracy"] = fourier_accuracy(I_host, c)
         result["variants"] = fourier_variants(args, c, g, opt, N, ws, flush, stream)
         result["pupil_scaling"] = pupil_scaling(c, ws, flush, stream)
+        result["bessel_harmonic"] = bessel_harmonic_variant(flush, stream)
     return result, rank
 
 
@@ -579,6 +580,53 @@ def fourier_accuracy(I, c, planes=(0, 64, 127)):
                             zernike=c["zernike"])[0]
         worst = max(worst, float(np.max(np.abs(I[iz] - Ir)) / np.max(Ir)))
     return {"max_rel_err_vs_fp64_oracle": worst, "planes_checked": list(planes)}
+
+
+def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
+    """The spherical strategy with every Zernike term (azimuthal harmonics,
+    no axisymmetric projection) on emitters of the batched workload: voxels/s
+    at the tail-bound order for 1e-7 and at M = 8, error of one emitter
+    against the FP64 harmonic oracle at the same order."""
+    import torch
+
+    from oracle import bessel_harmonic as bh
+    from oracle.optics import Optics
+    from paper_2502_03170_gb300 import api
+    from paper_2502_03170_gb300 import workloads as W
+    c = W.bessel(n_emitters=n_em)
+    geo = (c["n_theta"], c["n_r"], c["nx"], c["ny"], c["dx"], c["dy"])
+    ws = api.Workspace()
+    out = {"n_emitters": n_em, "n_slices": int(c["z_offsets"][-1]),
+           "tail_bound_tol": 1e-7}
+    m_bound = api.harmonic_order(c["zernike"], 1e-7)
+    for name, m in (("m_bound", m_bound), ("m_8", 8)):
+        run = lambda: api.bessel_harmonic(c["optics"], c["depth"], c["zernike"],
+                                          c["z_offsets"], c["z"], *geo, m_max=m,
+                                          workspace=ws, stream=stream)
+        I = run()
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            I = run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        e0, e1 = int(c["z_offsets"][0]), int(c["z_offsets"][1])
+        Iref = bh.psf_harmonic_batch(Optics.from_dict(c["optics"]), c["depth"], c["zernike"],
+                                     c["z_offsets"], c["z"], *geo, m, emitters=[0])
+        Ie = I[e0:e1].cpu().numpy()
+        out[name] = {"m_max": m, "ms": ms / steps,
+                     "voxels_per_s": I.numel() / (ms / steps * 1e-3),
+                     "max_rel_err_vs_oracle_emitter0":
+                         float(np.max(np.abs(Ie - Iref)) / np.max(Iref))}
+        if name == "m_bound":
+            I_bound = I[e0:e1].cpu().numpy()
+        else:
+            out[name]["truncation_vs_m_bound_emitter0"] = float(
+                np.max(np.abs(Ie - I_bound)) / np.max(I_bound))
+    return out
 
 
 def pupil_scaling(c, ws, flush, stream, pupils=(512, 1024), steps=3):

@@ -81,15 +81,50 @@ k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restri
   }
 }
 
+// J_0 .. J_nmax at one argument x >= 0 by Miller's backward recurrence
+// J_{n-1} = (2n / x) J_n - J_{n+1}, started far above max(nmax, x) where the
+// minimal solution dominates, normalised by J_0 + 2 sum_k J_{2k} = 1
+// (FP64; values rescaled before they can overflow).
+constexpr int kJMax = kHarmMaxM + 3;
+
+PSF_D void bessel_j_all(double x, int nmax, double* out) {
+  for (int n = 0; n <= nmax; ++n) out[n] = 0.0;
+  if (x <= 0.0) {
+    out[0] = 1.0;
+    return;
+  }
+  const int start = 2 * ((max(nmax, (int)x) + 40 + (int)sqrt(40.0 * (max(nmax, (int)x) + 1))) / 2);
+  const double two_x = 2.0 / x;
+  double jp = 0.0, jc = 1.0, sum = 0.0;   // J_{n+1}, J_n (unnormalised)
+  for (int n = start; n >= 1; --n) {
+    const double jm = n * two_x * jc - jp;   // J_{n-1}
+    jp = jc;
+    jc = jm;
+    const int m = n - 1;
+    if (m <= nmax) out[m] = jc;
+    if (m > 0 && (m & 1) == 0) sum += 2.0 * jc;
+    if (fabs(jc) > 1e250) {
+      jc *= 1e-250;
+      jp *= 1e-250;
+      sum *= 1e-250;
+      for (int k = m; k <= nmax; ++k) out[k] *= 1e-250;
+    }
+  }
+  const double norm = 1.0 / (sum + jc);
+  for (int n = 0; n <= nmax; ++n) out[n] *= norm;
+}
+
+// one thread per (r_i, theta_j): every order at once
 __global__ void k_harm_jtab(HarmParams p, ThetaTable t, float* __restrict__ Jt) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)(p.m_max + 3) * p.n_r * p.n_theta;
-  if (idx >= total) return;
-  const int j = (int)(idx % p.n_theta);
-  const long long rest = idx / p.n_theta;
-  const int i = (int)(rest % p.n_r), n = (int)(rest / p.n_r);
-  const double x = p.k * (i * p.dr) * t.sin_t[j];
-  Jt[idx] = (float)(t.w[j] * jn(n, x));
+  if (idx >= (long long)p.n_r * p.n_theta) return;
+  const int i = (int)(idx / p.n_theta), j = (int)(idx - (long long)i * p.n_theta);
+  const int nmax = p.m_max + 2;
+  double J[kJMax];
+  bessel_j_all(p.k * (i * p.dr) * t.sin_t[j], nmax, J);
+  const double w = t.w[j];
+  const size_t plane = (size_t)p.n_r * p.n_theta;
+  for (int n = 0; n <= nmax; ++n) Jt[n * plane + idx] = (float)(w * J[n]);
 }
 
 // D[s][j] = e^{i k z_s cos theta_j} for the slices of a chunk
@@ -277,8 +312,8 @@ void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const 
 }
 
 void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t s) {
-  const long long total = (long long)(p.m_max + 3) * p.n_r * p.n_theta;
-  k_harm_jtab<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, t, Jt);
+  const long long total = (long long)p.n_r * p.n_theta;
+  k_harm_jtab<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(p, t, Jt);
 }
 
 void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,

@@ -40,8 +40,9 @@ void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e,
                        const double* zern, const float* Zr, const float2* cs,
                        float2* Bh, cudaStream_t s);
 
-// Jt[n][i][j] = w_j J_n(k r_i sin theta_j), n = 0 .. m_max + 2 (FP64 Bessel
-// functions, stored FP32).
+// Jt[n][i][j] = w_j J_n(k r_i sin theta_j), n = 0 .. m_max + 2 (FP64 by
+// Miller's backward recurrence, all orders of one argument at once; stored
+// FP32).
 void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t s);
 
 // Profiles of the slices [s0, s0 + ns) (D: scratch [ns][n_theta] for the

@@ -14,6 +14,9 @@ the device), then exits.  Cases:
   (about 600 MB of input for 256 emitters).
 * ``fourier_backward`` - the phase-retrieval adjoint (256^2 pupil, 128^2 px,
   32 planes) for ``--batch`` pupils against a seeded target.
+* ``bessel_harmonic`` - ``--emitters`` emitters of the batched workload with
+  every Zernike term, by azimuthal harmonics at the tail-bound order
+  (``--mmax`` to set it).
 """
 import argparse
 
@@ -27,7 +30,8 @@ from . import workloads as W
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward",
-                                     "fourier_backward"])
+                                     "fourier_backward", "bessel_harmonic"])
+    ap.add_argument("--mmax", type=int, default=-1)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--emitters", type=int, default=256)
     ap.add_argument("--precision", default="fp32")
@@ -61,6 +65,15 @@ def main():
                 precision=args.precision)
         torch.cuda.synchronize()
         assert torch.isfinite(gW).all()
+    elif args.case == "bessel_harmonic":
+        c = W.bessel(n_emitters=args.emitters)
+        m = args.mmax if args.mmax >= 0 else api.harmonic_order(c["zernike"], 1e-7)
+        for _ in range(2):
+            I = api.bessel_harmonic(c["optics"], c["depth"], c["zernike"], c["z_offsets"],
+                                    c["z"], c["n_theta"], c["n_r"], c["nx"], c["ny"],
+                                    c["dx"], c["dy"], m_max=m)
+        torch.cuda.synchronize()
+        assert torch.isfinite(I).all()
     elif args.case == "bessel_backward":
         c = W.bessel(n_emitters=args.emitters)
         n_sl = int(c["z_offsets"][-1])
