@@ -469,23 +469,44 @@ void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s)
 constexpr int kZgParts = 64;
 constexpr int kZgMaxPupils = 128;
 
-__global__ void k_zernike_grad_part(const float* __restrict__ Zt, int NN, int nb,
-                                    const float* __restrict__ gW, double* part) {
-  __shared__ double red[256];
+// One CTA per (Zernike term j, node part): every pupil of the group at once.
+// Each thread reads Z_j at its nodes once and keeps one FP32 partial per
+// pupil (a few nodes each); the CTA reduces all of them in one pass (warp
+// shuffles in FP64, then the warps in a fixed order).
+constexpr int kZgMaxNb = 8;
+
+__global__ void __launch_bounds__(256)
+k_zernike_grad_part(const float* __restrict__ Zt, int NN, int nb,
+                    const float* __restrict__ gW, double* part) {
+  __shared__ double red[8][kZgMaxNb];
   const int j = blockIdx.x, sp = blockIdx.y;
   const int i0 = (int)((long long)NN * sp / kZgParts), i1 = (int)((long long)NN * (sp + 1) / kZgParts);
   const float* z = Zt + (size_t)j * NN;
-  for (int k = 0; k < nb; ++k) {
-    const float* g = gW + (size_t)k * NN;
-    double acc = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += (double)z[i] * (double)g[i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-      __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k0 = 0; k0 < nb; k0 += kZgMaxNb) {
+    const int kn = min(kZgMaxNb, nb - k0);
+    float acc[kZgMaxNb];
+#pragma unroll
+    for (int k = 0; k < kZgMaxNb; ++k) acc[k] = 0.f;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const float zi = z[i];
+#pragma unroll
+      for (int k = 0; k < kZgMaxNb; ++k)
+        if (k < kn) acc[k] = fmaf(zi, gW[(size_t)(k0 + k) * NN + i], acc[k]);
     }
-    if (threadIdx.x == 0) part[((size_t)k * gridDim.x + j) * kZgParts + sp] = red[0];
+#pragma unroll
+    for (int k = 0; k < kZgMaxNb; ++k) {
+      double v = (double)acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kn) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+      part[((size_t)(k0 + threadIdx.x) * gridDim.x + j) * kZgParts + sp] = v;
+    }
     __syncthreads();
   }
 }

@@ -591,12 +591,13 @@ __global__ void k_group_phase(const float* __restrict__ wfr_gl, const float* __r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN) return;
   const int k = blockIdx.y;
-  double w = 0.0;
-  for (int j = 0; j < n_zern; ++j) w += coef[(size_t)k * n_zern + j] * (double)Zt[(size_t)j * NN + i];
-  if (phase_map) w += (double)phase_map[(size_t)k * NN + i];
-  double cyc = (double)wfr_gl[i] + w * (0.5 / kPi);
-  cyc -= rint(cyc);
-  wfr[(size_t)k * NN + i] = (float)cyc;
+  float w = 0.f;
+  for (int j = 0; j < n_zern; ++j)
+    w = fmaf((float)coef[(size_t)k * n_zern + j], Zt[(size_t)j * NN + i], w);
+  if (phase_map) w += phase_map[(size_t)k * NN + i];
+  float cyc = wfr_gl[i] + w * (float)(0.5 / kPi);
+  cyc -= rintf(cyc);
+  wfr[(size_t)k * NN + i] = cyc;
 }
 
 // loss[k] = sum of the partials of pupil k (n_per each), FP64, fixed order.
@@ -1440,6 +1441,7 @@ int tc_fourier_bwd_setup(const TcBwdOperands& ops, int N, int nx, int ny, double
 struct TcBwdMaps {
   CUtensorMap Ax_h, Ax_l, Ay_h, Ay_l, P_h, P_l, U_h, U_l;
   CUtensorMap AxH_h, AxH_l, AyH_h, AyH_l, R_h, R_l, V_h, V_l;
+  CUtensorMap P2_h, P2_l, R2_h, R2_l;   // 32-row maps of the CTA-pair kernel
 };
 
 void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* Zt,
@@ -1480,6 +1482,25 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
             make_map_3d(&m.V_h, ops.V_hi, 2 * ny, N, 3 * zc) &&
             make_map_3d(&m.V_l, ops.V_lo, 2 * ny, N, 3 * zc);
   if (!ok) return PSF_ERR_CUDA;
+  // the two mode-0 contractions (stage 1 and V = A_x^H R) run on the CTA-pair
+  // kernel unless PSF_TC_PAIR=0 or the cluster launch is refused
+  const char* pe = getenv("PSF_TC_PAIR");
+  bool pair = !(pe && pe[0] == '0');
+  if (pair)
+    pair = make_map_3d_rows32(&m.P2_h, f.P_hi, K, N, 3 * zc) &&
+           make_map_3d_rows32(&m.P2_l, f.P_lo, K, N, 3 * zc) &&
+           make_map_3d_rows32(&m.R2_h, ops.R_hi, 2 * nx, ny, 3 * zc) &&
+           make_map_3d_rows32(&m.R2_l, ops.R_lo, 2 * nx, ny, 3 * zc);
+  auto gemm0 = [&](const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
+                   const CUtensorMap& Bl, const CUtensorMap& Bh2, const CUtensorMap& Bl2,
+                   const Params& p) {
+    if (pair) {
+      if (launch_gemm_pair(Ah, Al, Bh2, Bl2, p, s) == PSF_OK) return PSF_OK;
+      cudaGetLastError();
+      pair = false;
+    }
+    return launch_gemm(Ah, Al, Bh, Bl, p, s);
+  };
   const uint32_t idesc = make_idesc(bf16), idesc_b = make_idesc(1);
   const int tiles2 = ceil_div(nx, BOUT) * ceil_div(ny, BOUT);
   const int total = n_pupils * nz;                 // flat planes of this group
@@ -1514,7 +1535,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
     p1.status = status;
     {
       TimingScope ts(kTimeStage1, s);
-      if ((r = launch_gemm(m.Ay_h, m.Ay_l, m.P_h, m.P_l, p1, s))) return r;
+      if ((r = gemm0(m.Ay_h, m.Ay_l, m.P_h, m.P_l, m.P2_h, m.P2_l, p1))) return r;
     }
     // stage 2 recomputed: I, loss partials and R^T (BF16)
     Params p3 = p1;
@@ -1549,7 +1570,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
     pv.U_lo = ops.V_lo;
     {
       TimingScope ts(kTimeAdjoint, s);
-      if ((r = launch_gemm(m.AxH_h, m.AxH_l, m.R_h, m.R_l, pv, s))) return r;
+      if ((r = gemm0(m.AxH_h, m.AxH_l, m.R_h, m.R_l, m.R2_h, m.R2_l, pv))) return r;
     }
     // Gh^T[q][p] = sum_b conj(Ay[b][q]) V[p][b] -> Ghf; then 2 s Re(conj(Gh) P)
     Params p4 = p1;
