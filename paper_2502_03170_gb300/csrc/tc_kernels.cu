@@ -103,6 +103,262 @@ PSF_D void decode_tile(const Params& p, int t, int& plane, int& mt, int& nt) {
   }
 }
 
+PSF_D uint4 shfl_xor4(uint4 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  v.z = __shfl_xor_sync(0xffffffffu, v.z, m);
+  v.w = __shfl_xor_sync(0xffffffffu, v.w, m);
+  return v;
+}
+
+// Stores the 64-byte row pieces w[16] of the 32 lanes (row offset `off` in
+// 16-bit elements, valid rows only) after a 4 x 4 transpose of 16-byte units
+// within each group of four lanes (jj = lane & 3, k4 = lane & ~3).
+PSF_D void store_rows_t4(uint16_t* base, const uint32_t (&w)[16], int jj, int k4, int lane,
+                         bool row_ok, size_t off) {
+  uint4 u0 = make_uint4(w[0], w[1], w[2], w[3]), u1 = make_uint4(w[4], w[5], w[6], w[7]);
+  uint4 u2 = make_uint4(w[8], w[9], w[10], w[11]), u3 = make_uint4(w[12], w[13], w[14], w[15]);
+  const bool b1 = (jj & 2) != 0, b0 = (jj & 1) != 0;
+  // swap the off-diagonal 2 x 2 blocks (partner lane ^ 2)
+  uint4 s0 = b1 ? u0 : u2, s1 = b1 ? u1 : u3;
+  uint4 r0 = shfl_xor4(s0, 2), r1 = shfl_xor4(s1, 2);
+  if (b1) { u0 = r0; u1 = r1; } else { u2 = r0; u3 = r1; }
+  // then the off-diagonal units inside each 2 x 2 block (partner lane ^ 1)
+  s0 = b0 ? u0 : u1;
+  s1 = b0 ? u2 : u3;
+  r0 = shfl_xor4(s0, 1);
+  r1 = shfl_xor4(s1, 1);
+  if (b0) { u0 = r0; u2 = r1; } else { u1 = r0; u3 = r1; }
+  // u_i = unit jj of row k4 + i; row offsets and validity come from that lane
+  const uint4 us[4] = {u0, u1, u2, u3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const unsigned long long ro = __shfl_sync(0xffffffffu, (unsigned long long)off, k4 + i);
+    const int ok = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, k4 + i);
+    if (ok) *(uint4*)(base + ro + (size_t)jj * 8) = us[i];
+  }
+  (void)lane;
+}
+
+// --------------------------------------------------------------------------
+// Epilogue of one accumulator tile (tile plane / mt / nt; this warp's TMEM
+// lane quarter `quad`), shared by the single-CTA and the CTA-pair kernels:
+//   mode 0  stage 1 / V: split hi+lo store of out_scale * D (rows transposed
+//           4 x 4 between lanes so each store writes 64-byte row pieces)
+//   mode 1  stage 2: I = out_scale^2 sum_c |E_c|^2 (and the fields)
+//   mode 2  Bessel radial profiles
+//   mode 3  adjoint source R = g E with the loss partials
+//   mode 4  Gh stored in FP32
+// --------------------------------------------------------------------------
+PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int nt,
+                         int quad, int lane) {
+  const int row = quad * 32 + lane;          // accumulator row = A row
+  const int oi = row >> 1, part = row & 1;   // output index within tile, re/im
+  const int mo = mt * BOUT + oi;             // output index along m
+      if (p.mode == 2) {
+        // Bessel: prof[s][row] = scale * (D[row][2k], D[row][2k+1]), s = nt*96 + k
+        const int grow = mt * BM + row;
+        const float sc = *p.scale_ptr;
+        for (int h = 0; h < BN / 32; ++h) {
+          uint32_t r[32];
+          tmem_ld32(tbase + (uint32_t)(h * 32), r);
+          if (grow < p.rows_total) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int s = nt * (BN / 2) + h * 16 + k;
+              if (s < p.n_slices)
+                p.prof[(size_t)s * p.rows_total + grow] =
+                    make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
+            }
+          }
+        }
+      } else if (p.mode == 3) {
+        // adjoint source: I from the three channels, g = 2 (I - T) or dL/dI,
+        // R_c = g E_c with E = out_scale (D_im - i D_re); the lane holding D_re
+        // writes Im R, the lane holding D_im writes Re R (no exchange needed)
+        float sq[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sq[j] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float v = __uint_as_float(r[j]);
+              sq[h * 32 + j] = fmaf(v, v, sq[h * 32 + j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], 1);
+        const float sc2 = p.out_scale * p.out_scale;
+        const int bb0 = nt * BOUT + part * 32;      // this lane's 32 outputs along b
+        const bool row_ok = mo < p.nx;
+        float g[32];
+        float lsum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int bb = bb0 + j;
+          float gv = 0.f;
+          if (row_ok && bb < p.ny) {
+            const float I = sc2 * (part ? sq[32 + j] : sq[j]);
+            const size_t pix = ((size_t)plane * p.nx + mo) * p.ny + bb;
+            if (p.T) {
+              const float d = I - p.T[pix];
+              lsum = fmaf(d, d, lsum);
+              gv = 2.f * d;
+            } else {
+              gv = p.Gin[pix];
+            }
+          }
+          g[j] = gv;
+        }
+        float go[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) go[j] = __shfl_xor_sync(0xffffffffu, g[j], 1);
+        const float sgn = part ? p.out_scale : -p.out_scale;
+        const size_t col = (size_t)(part ? 0 : p.nx) + mo;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+            if (!row_ok) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int bb = nt * BOUT + h * 32 + j;
+              if (bb >= p.ny) continue;
+              // outputs h * 32 + j: the lane's own g for h == part, else the partner's
+              const float gj = (h == part) ? g[j] : go[j];
+              uint16_t hh, ll;
+              split16(sgn * gj * __uint_as_float(r[j]), 1, hh, ll);
+              const size_t o = ((size_t)(plane * 3 + c) * p.ny + bb) * (size_t)(2 * p.nx) + col;
+              p.R_hi[o] = hh;
+              p.R_lo[o] = ll;
+            }
+          }
+        }
+        if (p.loss_part) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+          if (lane == 0 && mt < p.m_tiles)
+            p.loss_part[(((size_t)plane * p.m_tiles + mt) * p.n_tiles + nt) * 4 + quad] = lsum;
+        }
+      } else if (p.mode == 4) {
+        // Gh: this lane holds Re (part 0) or Im (part 1) of Gh_c[p][q = mo] for
+        // 64 p; stored as FP32 Ghf[plane][c][part][p][q] (stores only: the
+        // pupil fields are folded in by a separate coalesced pass)
+        const bool q_ok = mo < p.m_out;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+            if (!q_ok) continue;
+            float* dst = p.gWz + (((size_t)(plane * 3 + c) * 2 + part) * p.n_rows) * p.m_out + mo;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int pp = nt * BOUT + h * 32 + j;
+              if (pp < p.n_rows) dst[(size_t)pp * p.m_out] = __uint_as_float(r[j]);
+            }
+          }
+        }
+      } else if (p.mode == 0) {
+        // stage 1: U[plane][c][b = mo][part * N + p] = split(out_scale * D)
+        const bool row_ok = mo < p.m_out;
+        for (int c = 0; c < 3; ++c) {
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+            const int p0 = nt * BOUT + h * 32;
+            if (p0 >= p.n_rows) continue;                 // uniform over the warp
+            const size_t off = ((size_t)(plane * 3 + c) * p.m_out + mo) * (size_t)(2 * p.N) +
+                               (size_t)part * p.N + p0;
+            uint32_t hw[16], lw[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              uint16_t h0, l0, h1, l1;
+              split16(p.out_scale * __uint_as_float(r[j]), p.bf16, h0, l0);
+              split16(p.out_scale * __uint_as_float(r[j + 1]), p.bf16, h1, l1);
+              hw[j / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              lw[j / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+            if (p0 + 32 <= p.n_rows) {
+              // Each lane holds 64 bytes (four 16-byte units) of its own row.
+              // A 4 x 4 transpose of units inside every group of four lanes
+              // gives lane 4k + j the unit j of rows 4k .. 4k + 3, so every
+              // store instruction writes eight contiguous 64-byte row pieces.
+              const int jj = lane & 3, k4 = lane & ~3;
+              store_rows_t4(p.U_hi, hw, jj, k4, lane, row_ok, off);
+              store_rows_t4(p.U_lo, lw, jj, k4, lane, row_ok, off);
+            } else if (row_ok) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                if (p0 + j < p.n_rows) {
+                  p.U_hi[off + j] = (uint16_t)(hw[j / 2] >> (16 * (j & 1)));
+                  p.U_lo[off + j] = (uint16_t)(lw[j / 2] >> (16 * (j & 1)));
+                }
+              }
+            }
+          }
+        }
+      } else {
+        // stage 2: I[plane][a = mo][b] = (out_scale)^2 sum_c (Re^2 + Im^2)
+        float s[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) s[j] = 0.f;
+        const bool want_f = p.F != nullptr;
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float v = __uint_as_float(r[j]);
+              s[h * 32 + j] = fmaf(v, v, s[h * 32 + j]);
+            }
+            if (want_f) {
+              // E = (-i) * out_scale * (Re + i Im): pair Re (even row) with Im
+              const int b0 = nt * BOUT + h * 32;
+              for (int j = 0; j < 32; ++j) {
+                const float v = p.out_scale * __uint_as_float(r[j]);
+                const float o = __shfl_xor_sync(0xffffffffu, v, 1);
+                const float re = part ? o : v, im = part ? v : o;
+                // even lane writes j < 16, odd lane j >= 16
+                if ((j < 16) == (part == 0) && mo < p.nx && b0 + j < p.ny)
+                  p.F[((size_t)(plane * 3 + c) * p.nx + mo) * p.ny + b0 + j] =
+                      make_float2(im, -re);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 64; ++j) s[j] += __shfl_xor_sync(0xffffffffu, s[j], 1);
+        const float sc = p.out_scale * p.out_scale;
+        const int b0 = nt * BOUT + part * 32;
+        // even lane (part 0) stores b0 + [0, 32), odd lane b0 + [32, 64):
+        // select with compile-time indices so s[] stays in registers
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] = sc * (part ? s[32 + j] : s[j]);
+        if (mo < p.nx && b0 < p.ny) {
+          float* dst = p.I + ((size_t)plane * p.nx + mo) * p.ny + b0;
+          if (b0 + 32 <= p.ny && (p.ny & 3) == 0) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+              ((float4*)dst)[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (b0 + j < p.ny) dst[j] = o[j];
+          }
+        }
+      }
+}
+
 // --------------------------------------------------------------------------
 // The persistent GEMM kernel
 // --------------------------------------------------------------------------
@@ -251,8 +507,6 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
   } else if (warp >= 2) {
     // ------------------------------ epilogue ----------------------------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
-    const int row = quad * 32 + lane;          // accumulator row = A row
-    const int oi = row >> 1, part = row & 1;   // output index within tile, re/im
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -264,208 +518,7 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
       int plane, mt, nt;
       decode_tile(p, t, plane, mt, nt);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * ACC_COL);
-      const int mo = mt * BOUT + oi;           // output index along m
-      if (p.mode == 2) {
-        // Bessel: prof[s][row] = scale * (D[row][2k], D[row][2k+1]), s = nt*96 + k
-        const int grow = mt * BM + row;
-        const float sc = *p.scale_ptr;
-        for (int h = 0; h < BN / 32; ++h) {
-          uint32_t r[32];
-          tmem_ld32(tbase + (uint32_t)(h * 32), r);
-          if (grow < p.rows_total) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int s = nt * (BN / 2) + h * 16 + k;
-              if (s < p.n_slices)
-                p.prof[(size_t)s * p.rows_total + grow] =
-                    make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
-            }
-          }
-        }
-      } else if (p.mode == 3) {
-        // adjoint source: I from the three channels, g = 2 (I - T) or dL/dI,
-        // R_c = g E_c with E = out_scale (D_im - i D_re); the lane holding D_re
-        // writes Im R, the lane holding D_im writes Re R (no exchange needed)
-        float sq[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) sq[j] = 0.f;
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float v = __uint_as_float(r[j]);
-              sq[h * 32 + j] = fmaf(v, v, sq[h * 32 + j]);
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 64; ++j) sq[j] += __shfl_xor_sync(0xffffffffu, sq[j], 1);
-        const float sc2 = p.out_scale * p.out_scale;
-        const int bb0 = nt * BOUT + part * 32;      // this lane's 32 outputs along b
-        const bool row_ok = mo < p.nx;
-        float g[32];
-        float lsum = 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int bb = bb0 + j;
-          float gv = 0.f;
-          if (row_ok && bb < p.ny) {
-            const float I = sc2 * (part ? sq[32 + j] : sq[j]);
-            const size_t pix = ((size_t)plane * p.nx + mo) * p.ny + bb;
-            if (p.T) {
-              const float d = I - p.T[pix];
-              lsum = fmaf(d, d, lsum);
-              gv = 2.f * d;
-            } else {
-              gv = p.Gin[pix];
-            }
-          }
-          g[j] = gv;
-        }
-        float go[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) go[j] = __shfl_xor_sync(0xffffffffu, g[j], 1);
-        const float sgn = part ? p.out_scale : -p.out_scale;
-        const size_t col = (size_t)(part ? 0 : p.nx) + mo;
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-            if (!row_ok) continue;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int bb = nt * BOUT + h * 32 + j;
-              if (bb >= p.ny) continue;
-              // outputs h * 32 + j: the lane's own g for h == part, else the partner's
-              const float gj = (h == part) ? g[j] : go[j];
-              uint16_t hh, ll;
-              split16(sgn * gj * __uint_as_float(r[j]), 1, hh, ll);
-              const size_t o = ((size_t)(plane * 3 + c) * p.ny + bb) * (size_t)(2 * p.nx) + col;
-              p.R_hi[o] = hh;
-              p.R_lo[o] = ll;
-            }
-          }
-        }
-        if (p.loss_part) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
-          if (lane == 0) p.loss_part[(size_t)t * 4 + quad] = lsum;
-        }
-      } else if (p.mode == 4) {
-        // Gh: this lane holds Re (part 0) or Im (part 1) of Gh_c[p][q = mo] for
-        // 64 p; stored as FP32 Ghf[plane][c][part][p][q] (stores only: the
-        // pupil fields are folded in by a separate coalesced pass)
-        const bool q_ok = mo < p.m_out;
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-            if (!q_ok) continue;
-            float* dst = p.gWz + (((size_t)(plane * 3 + c) * 2 + part) * p.n_rows) * p.m_out + mo;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int pp = nt * BOUT + h * 32 + j;
-              if (pp < p.n_rows) dst[(size_t)pp * p.m_out] = __uint_as_float(r[j]);
-            }
-          }
-        }
-      } else if (p.mode == 0) {
-        // stage 1: U[plane][c][b = mo][part * N + p] = split(out_scale * D)
-        const bool row_ok = mo < p.m_out;
-        for (int c = 0; c < 3; ++c) {
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-            const int p0 = nt * BOUT + h * 32;
-            if (!row_ok || p0 >= p.n_rows) continue;
-            const size_t off = ((size_t)(plane * 3 + c) * p.m_out + mo) * (size_t)(2 * p.N) +
-                               (size_t)part * p.N + p0;
-            uint32_t hw[16], lw[16];
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint16_t h0, l0, h1, l1;
-              split16(p.out_scale * __uint_as_float(r[j]), p.bf16, h0, l0);
-              split16(p.out_scale * __uint_as_float(r[j + 1]), p.bf16, h1, l1);
-              hw[j / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-              lw[j / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-            }
-            if (p0 + 32 <= p.n_rows) {
-              uint4* dh = (uint4*)(p.U_hi + off);
-              uint4* dl = (uint4*)(p.U_lo + off);
-#pragma unroll
-              for (int v = 0; v < 4; ++v) {
-                dh[v] = make_uint4(hw[4 * v], hw[4 * v + 1], hw[4 * v + 2], hw[4 * v + 3]);
-                dl[v] = make_uint4(lw[4 * v], lw[4 * v + 1], lw[4 * v + 2], lw[4 * v + 3]);
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                if (p0 + j < p.n_rows) {
-                  p.U_hi[off + j] = (uint16_t)(hw[j / 2] >> (16 * (j & 1)));
-                  p.U_lo[off + j] = (uint16_t)(lw[j / 2] >> (16 * (j & 1)));
-                }
-              }
-            }
-          }
-        }
-      } else {
-        // stage 2: I[plane][a = mo][b] = (out_scale)^2 sum_c (Re^2 + Im^2)
-        float s[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) s[j] = 0.f;
-        const bool want_f = p.F != nullptr;
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float v = __uint_as_float(r[j]);
-              s[h * 32 + j] = fmaf(v, v, s[h * 32 + j]);
-            }
-            if (want_f) {
-              // E = (-i) * out_scale * (Re + i Im): pair Re (even row) with Im
-              const int b0 = nt * BOUT + h * 32;
-              for (int j = 0; j < 32; ++j) {
-                const float v = p.out_scale * __uint_as_float(r[j]);
-                const float o = __shfl_xor_sync(0xffffffffu, v, 1);
-                const float re = part ? o : v, im = part ? v : o;
-                // even lane writes j < 16, odd lane j >= 16
-                if ((j < 16) == (part == 0) && mo < p.nx && b0 + j < p.ny)
-                  p.F[((size_t)(plane * 3 + c) * p.nx + mo) * p.ny + b0 + j] =
-                      make_float2(im, -re);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 64; ++j) s[j] += __shfl_xor_sync(0xffffffffu, s[j], 1);
-        const float sc = p.out_scale * p.out_scale;
-        const int b0 = nt * BOUT + part * 32;
-        // even lane (part 0) stores b0 + [0, 32), odd lane b0 + [32, 64):
-        // select with compile-time indices so s[] stays in registers
-        float o[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] = sc * (part ? s[32 + j] : s[j]);
-        if (mo < p.nx && b0 < p.ny) {
-          float* dst = p.I + ((size_t)plane * p.nx + mo) * p.ny + b0;
-          if (b0 + 32 <= p.ny && (p.ny & 3) == 0) {
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-              ((float4*)dst)[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (b0 + j < p.ny) dst[j] = o[j];
-          }
-        }
-      }
+      tile_epilogue(p, tbase, plane, mt, nt, quad, lane);
       tmem_fence_before();
       mbar_arrive(tempty_bar(acc));
       if (++acc == 2) {
@@ -785,42 +838,6 @@ constexpr int PB_BYTES = PB_ROWS * BK * 2;            // 12 KB
 constexpr int PSTAGE_BYTES = 2 * A_BYTES + 2 * PB_BYTES;
 constexpr int PSMEM_BYTES = PS_STAGES * PSTAGE_BYTES + 1024 + 1024;
 
-PSF_D uint4 shfl_xor4(uint4 v, int m) {
-  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
-  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
-  v.z = __shfl_xor_sync(0xffffffffu, v.z, m);
-  v.w = __shfl_xor_sync(0xffffffffu, v.w, m);
-  return v;
-}
-
-// Stores the 64-byte row pieces w[16] of the 32 lanes (row offset `off` in
-// 16-bit elements, valid rows only) after a 4 x 4 transpose of 16-byte units
-// within each group of four lanes (jj = lane & 3, k4 = lane & ~3).
-PSF_D void store_rows_t4(uint16_t* base, const uint32_t (&w)[16], int jj, int k4, int lane,
-                         bool row_ok, size_t off) {
-  uint4 u0 = make_uint4(w[0], w[1], w[2], w[3]), u1 = make_uint4(w[4], w[5], w[6], w[7]);
-  uint4 u2 = make_uint4(w[8], w[9], w[10], w[11]), u3 = make_uint4(w[12], w[13], w[14], w[15]);
-  const bool b1 = (jj & 2) != 0, b0 = (jj & 1) != 0;
-  // swap the off-diagonal 2 x 2 blocks (partner lane ^ 2)
-  uint4 s0 = b1 ? u0 : u2, s1 = b1 ? u1 : u3;
-  uint4 r0 = shfl_xor4(s0, 2), r1 = shfl_xor4(s1, 2);
-  if (b1) { u0 = r0; u1 = r1; } else { u2 = r0; u3 = r1; }
-  // then the off-diagonal units inside each 2 x 2 block (partner lane ^ 1)
-  s0 = b0 ? u0 : u1;
-  s1 = b0 ? u2 : u3;
-  r0 = shfl_xor4(s0, 1);
-  r1 = shfl_xor4(s1, 1);
-  if (b0) { u0 = r0; u2 = r1; } else { u1 = r0; u3 = r1; }
-  // u_i = unit jj of row k4 + i; row offsets and validity come from that lane
-  const uint4 us[4] = {u0, u1, u2, u3};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const unsigned long long ro = __shfl_sync(0xffffffffu, (unsigned long long)off, k4 + i);
-    const int ok = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, k4 + i);
-    if (ok) *(uint4*)(base + ro + (size_t)jj * 8) = us[i];
-  }
-  (void)lane;
-}
 
 PSF_D void decode_pair(const Params& p, int t, int& plane, int& mp, int& nt) {
   const int m_pairs = (p.m_tiles + 1) / 2;
@@ -975,8 +992,6 @@ k_split_cgemm_pair(const __grid_constant__ CUtensorMap mapA_hi,
   } else if (warp >= 2) {
     // ------------------------------ epilogue ----------------------------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
-    const int row = quad * 32 + lane;          // accumulator row = A row
-    const int oi = row >> 1, part = row & 1;   // output index within tile, re/im
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = cluster; t < total; t += n_clusters) {
@@ -989,99 +1004,7 @@ k_split_cgemm_pair(const __grid_constant__ CUtensorMap mapA_hi,
       decode_pair(p, t, plane, mp, nt);
       const int mt = 2 * mp + (int)rank;
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * ACC_COL);
-      const int mo = mt * BOUT + oi;           // output index along m
-      if (p.mode == 0) {
-        // stage 1: U[plane][c][b = mo][part * N + p] = split(out_scale * D)
-        const bool row_ok = mo < p.m_out;
-        for (int c = 0; c < 3; ++c) {
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-            const int p0 = nt * BOUT + h * 32;
-            if (p0 >= p.n_rows) continue;                 // uniform over the warp
-            const size_t off = ((size_t)(plane * 3 + c) * p.m_out + mo) * (size_t)(2 * p.N) +
-                               (size_t)part * p.N + p0;
-            uint32_t hw[16], lw[16];
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint16_t h0, l0, h1, l1;
-              split16(p.out_scale * __uint_as_float(r[j]), p.bf16, h0, l0);
-              split16(p.out_scale * __uint_as_float(r[j + 1]), p.bf16, h1, l1);
-              hw[j / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-              lw[j / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-            }
-            if (p0 + 32 <= p.n_rows) {
-              // Each lane holds 64 bytes (four 16-byte units) of its own row.
-              // A 4 x 4 transpose of units inside every group of four lanes
-              // gives lane 4k + j the unit j of rows 4k .. 4k + 3, so every
-              // store instruction writes eight contiguous 64-byte row pieces.
-              const int jj = lane & 3, k4 = lane & ~3;
-              store_rows_t4(p.U_hi, hw, jj, k4, lane, row_ok, off);
-              store_rows_t4(p.U_lo, lw, jj, k4, lane, row_ok, off);
-            } else if (row_ok) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                if (p0 + j < p.n_rows) {
-                  p.U_hi[off + j] = (uint16_t)(hw[j / 2] >> (16 * (j & 1)));
-                  p.U_lo[off + j] = (uint16_t)(lw[j / 2] >> (16 * (j & 1)));
-                }
-              }
-            }
-          }
-        }
-      } else {
-        // stage 2: I[plane][a = mo][b] = (out_scale)^2 sum_c (Re^2 + Im^2)
-        float s[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) s[j] = 0.f;
-        const bool want_f = p.F != nullptr;
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float v = __uint_as_float(r[j]);
-              s[h * 32 + j] = fmaf(v, v, s[h * 32 + j]);
-            }
-            if (want_f) {
-              // E = (-i) * out_scale * (Re + i Im): pair Re (even row) with Im
-              const int b0 = nt * BOUT + h * 32;
-              for (int j = 0; j < 32; ++j) {
-                const float v = p.out_scale * __uint_as_float(r[j]);
-                const float o = __shfl_xor_sync(0xffffffffu, v, 1);
-                const float re = part ? o : v, im = part ? v : o;
-                // even lane writes j < 16, odd lane j >= 16
-                if ((j < 16) == (part == 0) && mo < p.nx && b0 + j < p.ny)
-                  p.F[((size_t)(plane * 3 + c) * p.nx + mo) * p.ny + b0 + j] =
-                      make_float2(im, -re);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 64; ++j) s[j] += __shfl_xor_sync(0xffffffffu, s[j], 1);
-        const float sc = p.out_scale * p.out_scale;
-        const int b0 = nt * BOUT + part * 32;
-        // even lane (part 0) stores b0 + [0, 32), odd lane b0 + [32, 64):
-        // select with compile-time indices so s[] stays in registers
-        float o[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] = sc * (part ? s[32 + j] : s[j]);
-        if (mo < p.nx && b0 < p.ny) {
-          float* dst = p.I + ((size_t)plane * p.nx + mo) * p.ny + b0;
-          if (b0 + 32 <= p.ny && (p.ny & 3) == 0) {
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-              ((float4*)dst)[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (b0 + j < p.ny) dst[j] = o[j];
-          }
-        }
-      }
+      tile_epilogue(p, tbase, plane, mt, nt, quad, lane);
       tmem_fence_before();
       mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));   // the leader's barrier
       if (++acc == PS_ACCS) {
@@ -1119,7 +1042,7 @@ static uint32_t make_idesc_pair(int bf16) {
          ((uint32_t)((2 * BM) >> 4) << 24);
 }
 
-// Pair launch of a forward stage (modes 0 and 1): Bh, Bl must be 32-row maps.
+// Pair launch of a contraction (modes 0, 1, 3, 4): Bh, Bl must be 32-row maps.
 static int launch_gemm_pair(const CUtensorMap& Ah, const CUtensorMap& Al,
                             const CUtensorMap& Bh, const CUtensorMap& Bl, Params p,
                             cudaStream_t s) {
@@ -1163,14 +1086,35 @@ const char* tc_fourier_supported(int N, int nx, int ny) {
 }
 
 int tc_fourier_zchunk(int N, int nx, int ny, int nz) {
-  (void)nx;
-  // P (hi+lo) + U (hi+lo) per plane, keep the chunk near 64 MB
+  // P (hi+lo) + U (hi+lo) per plane; a chunk stays within 96 MB of the L2.
+  // Among the sizes from half that cap up to it, take the one whose chunks
+  // fill the persistent CTA-pair rounds best (stage-1 and stage-2 tile pairs
+  // over SMs / 2 clusters, summed over the stack); ties keep the larger.
   const double per_z = 3.0 * 2.0 * 2.0 * 2.0 * N * ((double)N + ny);
-  int zc = (int)(64.0 * 1048576.0 / per_z);
-  if (zc < 1) zc = 1;
-  if (zc > 64) zc = 64;
-  if (zc > nz) zc = nz;
-  return zc;
+  int cap = (int)(96.0 * 1048576.0 / per_z);
+  if (cap < 1) cap = 1;
+  if (cap > 64) cap = 64;
+  if (cap > nz) cap = nz;
+  int sms = tc::num_sms();
+  if (sms < 2) sms = 152;   // no device here: size for the target part
+  const long long clusters = sms / 2;
+  const long long per1 = (long long)((ceil_div(ny, tc::BOUT) + 1) / 2) * ceil_div(N, tc::BOUT);
+  const long long per2 = (long long)((ceil_div(nx, tc::BOUT) + 1) / 2) * ceil_div(ny, tc::BOUT);
+  int best = cap;
+  long long best_rounds = -1;
+  const int lo = cap / 2 > 1 ? cap / 2 : 1;
+  for (int zc = cap; zc >= lo; --zc) {
+    long long rounds = 0;
+    for (int z0 = 0; z0 < nz; z0 += zc) {
+      const long long n = nz - z0 < zc ? nz - z0 : zc;
+      rounds += (n * per1 + clusters - 1) / clusters + (n * per2 + clusters - 1) / clusters;
+    }
+    if (best_rounds < 0 || rounds < best_rounds) {
+      best_rounds = rounds;
+      best = zc;
+    }
+  }
+  return best;
 }
 
 void tc_fourier_carve(char* base, size_t* off, int N, int nx, int ny, int zc,
@@ -1441,7 +1385,7 @@ int tc_fourier_bwd_setup(const TcBwdOperands& ops, int N, int nx, int ny, double
 struct TcBwdMaps {
   CUtensorMap Ax_h, Ax_l, Ay_h, Ay_l, P_h, P_l, U_h, U_l;
   CUtensorMap AxH_h, AxH_l, AyH_h, AyH_l, R_h, R_l, V_h, V_l;
-  CUtensorMap P2_h, P2_l, R2_h, R2_l;   // 32-row maps of the CTA-pair kernel
+  CUtensorMap P2_h, P2_l, R2_h, R2_l, U2_h, U2_l, V2_h, V2_l;   // 32-row (pair) maps
 };
 
 void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* Zt,
@@ -1482,16 +1426,20 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
             make_map_3d(&m.V_h, ops.V_hi, 2 * ny, N, 3 * zc) &&
             make_map_3d(&m.V_l, ops.V_lo, 2 * ny, N, 3 * zc);
   if (!ok) return PSF_ERR_CUDA;
-  // the two mode-0 contractions (stage 1 and V = A_x^H R) run on the CTA-pair
-  // kernel unless PSF_TC_PAIR=0 or the cluster launch is refused
+  // the four contractions run on the CTA-pair kernel unless PSF_TC_PAIR=0 or
+  // the cluster launch is refused (then the single-CTA kernel, same results)
   const char* pe = getenv("PSF_TC_PAIR");
   bool pair = !(pe && pe[0] == '0');
   if (pair)
     pair = make_map_3d_rows32(&m.P2_h, f.P_hi, K, N, 3 * zc) &&
            make_map_3d_rows32(&m.P2_l, f.P_lo, K, N, 3 * zc) &&
            make_map_3d_rows32(&m.R2_h, ops.R_hi, 2 * nx, ny, 3 * zc) &&
-           make_map_3d_rows32(&m.R2_l, ops.R_lo, 2 * nx, ny, 3 * zc);
-  auto gemm0 = [&](const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
+           make_map_3d_rows32(&m.R2_l, ops.R_lo, 2 * nx, ny, 3 * zc) &&
+           make_map_3d_rows32(&m.U2_h, f.U_hi, K, ny, 3 * zc) &&
+           make_map_3d_rows32(&m.U2_l, f.U_lo, K, ny, 3 * zc) &&
+           make_map_3d_rows32(&m.V2_h, ops.V_hi, 2 * ny, N, 3 * zc) &&
+           make_map_3d_rows32(&m.V2_l, ops.V_lo, 2 * ny, N, 3 * zc);
+  auto gemm_any = [&](const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
                    const CUtensorMap& Bl, const CUtensorMap& Bh2, const CUtensorMap& Bl2,
                    const Params& p) {
     if (pair) {
@@ -1535,7 +1483,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
     p1.status = status;
     {
       TimingScope ts(kTimeStage1, s);
-      if ((r = gemm0(m.Ay_h, m.Ay_l, m.P_h, m.P_l, m.P2_h, m.P2_l, p1))) return r;
+      if ((r = gemm_any(m.Ay_h, m.Ay_l, m.P_h, m.P_l, m.P2_h, m.P2_l, p1))) return r;
     }
     // stage 2 recomputed: I, loss partials and R^T (BF16)
     Params p3 = p1;
@@ -1553,7 +1501,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
     p3.R_lo = ops.R_lo;
     {
       TimingScope ts(kTimeAdjoint, s);
-      if ((r = launch_gemm(m.Ax_h, m.Ax_l, m.U_h, m.U_l, p3, s))) return r;
+      if ((r = gemm_any(m.Ax_h, m.Ax_l, m.U_h, m.U_l, m.U2_h, m.U2_l, p3))) return r;
     }
     // V[c][p][b] = sum_a conj(Ax[a][p]) R_c[a][b]   (split BF16, stored like U)
     Params pv = p1;
@@ -1570,7 +1518,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
     pv.U_lo = ops.V_lo;
     {
       TimingScope ts(kTimeAdjoint, s);
-      if ((r = gemm0(m.AxH_h, m.AxH_l, m.R_h, m.R_l, m.R2_h, m.R2_l, pv))) return r;
+      if ((r = gemm_any(m.AxH_h, m.AxH_l, m.R_h, m.R_l, m.R2_h, m.R2_l, pv))) return r;
     }
     // Gh^T[q][p] = sum_b conj(Ay[b][q]) V[p][b] -> Ghf; then 2 s Re(conj(Gh) P)
     Params p4 = p1;
@@ -1586,7 +1534,7 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
     p4.gWz = ops.gWz;
     {
       TimingScope ts(kTimeAdjoint, s);
-      if ((r = launch_gemm(m.AyH_h, m.AyH_l, m.V_h, m.V_l, p4, s))) return r;
+      if ((r = gemm_any(m.AyH_h, m.AyH_l, m.V_h, m.V_l, m.V2_h, m.V2_l, p4))) return r;
       const int pk0 = z0 / nz, pk1 = (z0 + nzc - 1) / nz;
       k_gw_fold<<<dim3(ceil_div(N * N, 256), pk1 - pk0 + 1), 256, 0, s>>>(
           ops.gWz, tn, zz, N, z0, nzc, nz, 2.f * scale, gW);

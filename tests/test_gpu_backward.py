@@ -163,3 +163,32 @@ def test_split_backward_adjoint_config_sampled(lib):
         assert abs(loss[b] - L) <= 1e-4 * abs(L)
         assert rel_l2(gW[b], gWr) <= TOL_G
         assert rel_l2(gc[b], gcr) <= TOL_G
+
+
+@pytest.mark.parametrize("N,nx,ny,nz,batch", [(64, 72, 56, 5, 3), (48, 136, 40, 4, 2)])
+@pytest.mark.parametrize("use_target", [True, False])
+def test_backward_cta_pair_matches_single_cta(lib, N, nx, ny, nz, batch, use_target,
+                                              monkeypatch):
+    """The adjoint's four contractions on the CTA-pair kernel (default) and on
+    the single-CTA kernel give bitwise equal loss and gradients (odd numbers
+    of 64-row output tiles included: the last pair's peer tile is empty)."""
+    rng = np.random.default_rng(5 + N)
+    d = W.optics_gibson_lanni(1.0)
+    grid = dict(nx=nx, ny=ny, dx=0.03, dy=0.035, z=np.linspace(-0.5, 0.6, nz))
+    zern = np.zeros((batch, 21))
+    zern[:, 3:12] = rng.normal(0, 0.15, (batch, 9))
+    pm = rng.normal(0, 0.2, (batch, N, N))
+    T = rng.uniform(0, 2e-4, (batch, nz, nx, ny))
+    G = rng.normal(0, 1.0, (batch, nz, nx, ny))
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("PSF_TC_PAIR", mode)
+        out[mode] = gpu_backward(d, N, grid, zern, pm,
+                                 target=T if use_target else None,
+                                 grad_I=None if use_target else G, prec="split_fp16")
+    for a, b in zip(out["1"], out["0"]):
+        assert np.array_equal(a, b)
+    if use_target:   # and the pair result is the adjoint the oracle computes
+        L, gWr, gcr, _ = oa.loss_and_grad(oracle_optics(d), N, grid, zern[0], pm[0], T[0])
+        assert rel_l2(out["1"][1][0], gWr) <= 1e-4
+        assert rel_l2(out["1"][2][0], gcr) <= 1e-4
