@@ -42,11 +42,13 @@ FP32_LANES_PER_SM = 128
 # command and the figures).  A figure holds only for the source it was taken
 # on: when the kernel's sources hash differently, traffic is reported as null.
 PROFILED_TRAFFIC = {
-    # 13-plane z-chunk (256^2 pupil, 512^2 px), CTA-pair kernel: 43.06 MB read + 0.23 MB written
+    # 19-plane z-chunk (256^2 pupil, 512^2 px), CTA-pair kernel, stage 2:
+    # 61.96 MB read + 3.52 MB written
     "stage2_contraction_intensity": dict(
-        bytes_per_unit=(43.060e6 + 0.230e6) / 13, unit="plane",
-        sources=("tc_kernels.cu:k_split_cgemm_pair", "tc_ptx.cuh", "tc_pair_ptx.cuh"),
-        sha256_16="82c97c213905c89e", precision="split_fp16"),
+        bytes_per_unit=(61.956e6 + 3.516e6) / 19, unit="plane",
+        sources=("tc_kernels.cu:k_split_cgemm_pair", "tc_kernels.cu:tile_epilogue",
+                 "tc_kernels.cu:store_rows_t4", "tc_ptx.cuh", "tc_pair_ptx.cuh"),
+        sha256_16="0e6b71e56aaad66b", precision="split_fp16"),
     # 9442 slices of 128^2 px: 58.27 MB read + 557.25 MB written
     "bessel_radial_to_cartesian": dict(
         bytes_per_unit=(58.272e6 + 557.250e6) / 9442, unit="slice",
@@ -56,13 +58,14 @@ PROFILED_TRAFFIC = {
 
 
 def kernel_source(text, func):
-    """Bytes of the __global__ definition of `func` (through its closing brace)."""
-    key = ("\n" + func + "(").encode()
-    i = text.find(key)
-    if i < 0:
+    """Bytes of the definition of `func` (a __global__ kernel or a device
+    function), from its declaration line through its closing brace."""
+    import re
+    m = re.search(rb"\n(?:__global__[^\n]*\n)?[^\n;]*\b" + func.encode() + rb"\(", text)
+    if m is None:
         return text
-    i = text.rfind(b"__global__", 0, i)
-    j = text.find(b"{", i)
+    i = m.start() + 1
+    j = text.find(b"{", m.end())
     depth = 0
     for k in range(j, len(text)):
         c = text[k:k + 1]
