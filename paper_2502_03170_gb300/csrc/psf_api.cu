@@ -16,6 +16,7 @@
 #include "optics_models.cuh"
 #include "tc_kernels.cuh"
 #include "timing.cuh"
+#include "upload.cuh"
 
 namespace psf {
 
@@ -374,8 +375,7 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
     zz[i] = make_float2(v.hi, v.lo);
   }
   cudaMemsetAsync(workspace, 0, sizeof(int), s);
-  cudaMemcpyAsync(L.zz, zz.data(), zz.size() * sizeof(float2),
-                  cudaMemcpyHostToDevice, s);
+  upload_async(L.zz, zz.data(), zz.size() * sizeof(float2), s);
   if ((r = cuda_check("workspace init"))) return r;
 
   NodeParams np = node_params(opt, N, zernike, n_zern, phase_map);
@@ -392,8 +392,7 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
     std::vector<float2> words(L.czt_wx + L.czt_wy);
     czt_build_dir(N, grid->nx, f, grid->dx, 0.0, -ds * ds / (2.0 * kPi), words.data());
     czt_build_dir(N, grid->ny, f, grid->dy, 1.0, 0.0, words.data() + L.czt_wx);
-    cudaMemcpyAsync(L.czt_words, words.data(), words.size() * sizeof(float2),
-                    cudaMemcpyHostToDevice, s);
+    upload_async(L.czt_words, words.data(), words.size() * sizeof(float2), s);
     if ((r = cuda_check("chirp-Z tables"))) return r;
     const CztDir cx = czt_dir_view(L.czt_words, N, grid->nx);
     const CztDir cy = czt_dir_view(L.czt_words + L.czt_wx, N, grid->ny);
@@ -480,7 +479,7 @@ static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g,
   if (precision != PSF_PREC_FP32) {
     L.zc = tc_fourier_bwd_zchunk(N, g->nx, g->ny, g->nz);
     tc_fourier_bwd_carve(c.base, &c.off, N, g->nx, g->ny, g->nz, L.zc, &L.tc);
-    L.zpart = (double*)c.take<char>(zernike_grad_part_bytes(n_zern, L.tc.group));
+    L.zpart = (double*)c.take<char>(tc_zernike_parts_bytes(N, n_zern, L.tc.group));
     L.bytes = align_up(c.off, 256);
     return L;
   }
@@ -571,8 +570,7 @@ extern "C" int psf_fourier_vectorial_backward(
     zz[i] = make_float2(v.hi, v.lo);
   }
   cudaMemsetAsync(workspace, 0, sizeof(int), s);
-  cudaMemcpyAsync(L.zz, zz.data(), zz.size() * sizeof(float2),
-                  cudaMemcpyHostToDevice, s);
+  upload_async(L.zz, zz.data(), zz.size() * sizeof(float2), s);
   const double f = opt->NA / opt->lambda;
   const double ds = 2.0 * (opt->NA / opt->n_i) / N;
   const float scale = (float)(ds * ds / (2.0 * kPi));
@@ -598,8 +596,8 @@ extern "C" int psf_fourier_vectorial_backward(
     for (int b0 = 0; b0 < batch; b0 += gp) {
       const int nb = batch - b0 < gp ? batch - b0 : gp;
       if (n_zern > 0)
-        cudaMemcpyAsync(L.tc.coef, zernike + (size_t)b0 * n_zern,
-                        (size_t)nb * n_zern * sizeof(double), cudaMemcpyHostToDevice, s);
+        upload_async(L.tc.coef, zernike + (size_t)b0 * n_zern,
+                        (size_t)nb * n_zern * sizeof(double), s);
       {
         TimingScope ts(kTimeSetup, s);
         tc_group_phase(L.tc, L.nodes.wfr, L.Zt, L.tc.coef, n_zern,
@@ -609,12 +607,11 @@ extern "C" int psf_fourier_vectorial_backward(
       const float* Gb = grad_intensity ? grad_intensity + (size_t)b0 * vox : nullptr;
       float* gWb = grad_phase_map ? grad_phase_map + (size_t)b0 * NN : L.tc.gW;
       r = tc_fourier_backward(L.tc, L.nodes, L.zz, N, nx, ny, nz, nb, L.zc, scale, amp_bound,
-                              precision, Tb, Gb, gWb, loss ? loss + b0 : nullptr,
+                              precision, Tb, Gb, gWb, loss ? loss + b0 : nullptr, L.Zt,
+                              n_zern, L.zpart,
+                              grad_zernike ? grad_zernike + (size_t)b0 * n_zern : nullptr,
                               (int*)workspace, s);
       if (r) return fail(r, "split-precision adjoint launch failed");
-      if (grad_zernike)
-        launch_zernike_grad(zb, N, L.Zt, gWb, nb, L.zpart, grad_zernike + (size_t)b0 * n_zern,
-                            s);
     }
     return cuda_check("psf_fourier_vectorial_backward launch");
   }
@@ -885,10 +882,8 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
   bp.complex_g = fresnel ? 1 : 0;
 
   cudaMemsetAsync(workspace, 0, sizeof(int), s);
-  cudaMemcpyAsync(L.theta_tab, tab.data(), tab.size() * sizeof(double),
-                  cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(L.kappa, kap.data(), kap.size() * sizeof(float),
-                  cudaMemcpyHostToDevice, s);
+  upload_async(L.theta_tab, tab.data(), tab.size() * sizeof(double), s);
+  upload_async(L.kappa, kap.data(), kap.size() * sizeof(float), s);
   if ((r = cuda_check("workspace init"))) return r;
 
   R->split = !fp32_operand && precision != PSF_PREC_FP32;
@@ -1163,16 +1158,13 @@ extern "C" int psf_bessel_vectorial_backward(
     const bool sorted_form = B.sorted_form;
     const bool tc_adj = sorted_form && split;
     if (sorted_form) {
-      cudaMemcpyAsync(B.gpc, pt.pc.data(), ng * sizeof(int2), cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(B.gfg, pt.fg.data(), ng * sizeof(float4), cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(B.sorted_f, pt.sorted_f.data(), ng * sizeof(float),
-                      cudaMemcpyHostToDevice, s);
+      upload_async(B.gpc, pt.pc.data(), ng * sizeof(int2), s);
+      upload_async(B.gfg, pt.fg.data(), ng * sizeof(float4), s);
+      upload_async(B.sorted_f, pt.sorted_f.data(), ng * sizeof(float), s);
     } else {
-      cudaMemcpyAsync(B.groups, pt.sorted.data(), ng * sizeof(PixGroup),
-                      cudaMemcpyHostToDevice, s);
+      upload_async(B.groups, pt.sorted.data(), ng * sizeof(PixGroup), s);
     }
-    cudaMemcpyAsync(B.cell_start, pt.start.data(), pt.start.size() * sizeof(int),
-                    cudaMemcpyHostToDevice, s);
+    upload_async(B.cell_start, pt.start.data(), pt.start.size() * sizeof(int), s);
     // recompute the profiles (per-z recomputation: nothing of the forward is stored)
     if (split) {
       r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, precision, L.tc,
@@ -1410,8 +1402,8 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
   set(1, 2, 0.25 * (-pxi - pyr), 0.25 * (pxr - pyi));
   set(2, 3, -0.5 * am_r, -0.5 * am_i);
   set(2, 4, -0.5 * ap_r, -0.5 * ap_i);
-  cudaMemcpyAsync(H.Zr, zr.data(), zr.size() * sizeof(float), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(H.cs, cs.data(), cs.size() * sizeof(float2), cudaMemcpyHostToDevice, s);
+  upload_async(H.Zr, zr.data(), zr.size() * sizeof(float), s);
+  upload_async(H.cs, cs.data(), cs.size() * sizeof(float2), s);
   if ((r = cuda_check("harmonic tables"))) return r;
   {
     TimingScope ts(kTimeSetup, s);

@@ -600,38 +600,75 @@ __global__ void k_twiddle_adj_split(int N, int n_out, double alpha, uint16_t* hi
 // rebuilt from the node table exactly as the pupil planes were built, summed
 // into gW[pupil] in plane order (a pupil's first plane starts its sum).  One
 // thread per (pupil of the chunk, node).
-__global__ void k_gw_fold(const float* __restrict__ Ghf, NodeTable t,
-                          const float2* __restrict__ zz, int N, int p0, int planes,
-                          int nz_per, float scale, float* gW) {
+// When the chunk holds a pupil's last plane its gW is final here, and the
+// chain rule of Eq. 15 follows at once (Zt non-null): each warp reduces
+// Z_j gW over its 32 nodes for every j and writes one FP64 partial to
+// zpart[pupil][j][warp]; k_zernike_parts_fin sums them in a fixed order.
+__global__ void __launch_bounds__(256)
+k_gw_fold(const float* __restrict__ Ghf, NodeTable t, const float2* __restrict__ zz, int N,
+          int p0, int planes, int nz_per, float scale, float* gW,
+          const float* __restrict__ Zt, int n_zern, double* __restrict__ zpart) {
   const int NN = N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= NN) return;
-  const int pk = p0 / nz_per + (int)blockIdx.y;           // pupil of this thread
+  const int pk = p0 / nz_per + (int)blockIdx.y;           // pupil of this CTA
   const int a = max(pk * nz_per - p0, 0), b = min((pk + 1) * nz_per - p0, planes);
-  if (a >= b) return;
-  float amp[6];
+  const bool act = i < NN && a < b;
+  float v = 0.f;
+  if (act) {
+    float amp[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) amp[c] = t.amp[(size_t)c * NN + i];
-  const float w = t.wfr[(size_t)pk * NN + i];
-  const f2x kap{t.kh[i], t.kl[i]};
-  float* dst = gW + (size_t)pk * NN + i;
-  float v = (p0 + a - pk * nz_per == 0) ? 0.f : *dst;
+    for (int c = 0; c < 6; ++c) amp[c] = t.amp[(size_t)c * NN + i];
+    const float w = t.wfr[(size_t)pk * NN + i];
+    const f2x kap{t.kh[i], t.kl[i]};
+    float* dst = gW + (size_t)pk * NN + i;
+    v = (p0 + a - pk * nz_per == 0) ? 0.f : *dst;
 #pragma unroll 4
-  for (int pl = a; pl < b; ++pl) {
-    const float2 z = zz[p0 + pl - pk * nz_per];
-    const float2 e = cis_cycles(frac_mul_add(kap, f2x{z.x, z.y}, w));
-    float acc = 0.f;
+    for (int pl = a; pl < b; ++pl) {
+      const float2 z = zz[p0 + pl - pk * nz_per];
+      const float2 e = cis_cycles(frac_mul_add(kap, f2x{z.x, z.y}, w));
+      float acc = 0.f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const size_t gb = ((size_t)(pl * 3 + c) * 2) * NN + i;
-      const float pr = amp[2 * c] * e.x - amp[2 * c + 1] * e.y;
-      const float pi = amp[2 * c] * e.y + amp[2 * c + 1] * e.x;
-      acc = fmaf(Ghf[gb], pr, acc);
-      acc = fmaf(Ghf[gb + NN], pi, acc);
+      for (int c = 0; c < 3; ++c) {
+        const size_t gb = ((size_t)(pl * 3 + c) * 2) * NN + i;
+        const float pr = amp[2 * c] * e.x - amp[2 * c + 1] * e.y;
+        const float pi = amp[2 * c] * e.y + amp[2 * c + 1] * e.x;
+        acc = fmaf(Ghf[gb], pr, acc);
+        acc = fmaf(Ghf[gb + NN], pi, acc);
+      }
+      v = fmaf(scale, acc, v);
     }
-    v = fmaf(scale, acc, v);
+    *dst = v;
   }
-  *dst = v;
+  // uniform over the CTA: does this chunk finish pupil pk?
+  const bool last = a < b && (pk + 1) * nz_per - p0 <= planes;
+  if (Zt == nullptr || !last) return;
+  const int n_warps = (NN + 31) / 32, wg = i >> 5, lane = threadIdx.x & 31;
+  for (int j = 0; j < n_zern; ++j) {
+    float c = act ? Zt[(size_t)j * NN + i] * v : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && wg < n_warps) zpart[((size_t)pk * n_zern + j) * n_warps + wg] = (double)c;
+  }
+}
+
+// grad_c[k][j] = sum of zpart[k][j][0 .. n_parts) in order (FP64)
+__global__ void k_zernike_parts_fin(const double* __restrict__ zpart, int n_zern, int nb,
+                                    int n_parts, float* grad_c) {
+  __shared__ double red[8];
+  const int kj = blockIdx.x;
+  if (kj >= n_zern * nb) return;
+  const double* pp = zpart + (size_t)kj * n_parts;
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < n_parts; q += blockDim.x) acc += pp[q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    grad_c[kj] = (float)v;
+  }
 }
 
 // Phases of a group of pupils from the shared Gibson-Lanni phase:
@@ -1395,11 +1432,17 @@ void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* 
                                                                phase_map, N * N, ops.wfr);
 }
 
+size_t tc_zernike_parts_bytes(int N, int n_zern, int nb) {
+  return (size_t)nb * (n_zern > 0 ? n_zern : 1) * (((size_t)N * N + 31) / 32) * sizeof(double) +
+         sizeof(double);
+}
+
 int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2* zz,
                         int N, int nx, int ny, int nz, int n_pupils, int zc, float scale,
                         double amp_bound, int precision, const float* target,
-                        const float* grad_intensity, float* gW, float* loss, int* status,
-                        cudaStream_t s) {
+                        const float* grad_intensity, float* gW, float* loss,
+                        const float* Zt, int n_zern, double* zpart, float* grad_c,
+                        int* status, cudaStream_t s) {
   using namespace tc;
   const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
   const int K = 2 * N;
@@ -1537,11 +1580,15 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
       if ((r = gemm_any(m.AyH_h, m.AyH_l, m.V_h, m.V_l, m.V2_h, m.V2_l, p4))) return r;
       const int pk0 = z0 / nz, pk1 = (z0 + nzc - 1) / nz;
       k_gw_fold<<<dim3(ceil_div(N * N, 256), pk1 - pk0 + 1), 256, 0, s>>>(
-          ops.gWz, tn, zz, N, z0, nzc, nz, 2.f * scale, gW);
+          ops.gWz, tn, zz, N, z0, nzc, nz, 2.f * scale, gW, grad_c ? Zt : nullptr, n_zern,
+          zpart);
     }
   }
   if (target && loss)
     k_loss_group<<<n_pupils, 256, 0, s>>>(ops.loss_part, nz * tiles2 * 4, loss);
+  if (grad_c && n_zern > 0)
+    k_zernike_parts_fin<<<n_zern * n_pupils, 256, 0, s>>>(zpart, n_zern, n_pupils,
+                                                          (N * N + 31) / 32, grad_c);
   return cudaPeekAtLastError() == cudaSuccess ? PSF_OK : PSF_ERR_CUDA;
 }
 

@@ -114,11 +114,15 @@ void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* 
 // n_pupils (<= group) pupils whose phase tables are in ops.wfr: planes are
 // flat over (pupil, z); gW[k][N][N] = dL/dW_0 of pupil k (overwritten);
 // loss[k] (target only).  target / grad_intensity point at the group's first
-// plane.
+// plane.  With grad_c non-null, grad_c[k][j] = sum Z_j gW[k] (chain rule of
+// Eq. 15, Zt [n_zern][N][N]), formed as the fold finishes each pupil, through
+// zpart (tc_zernike_parts_bytes(N, n_zern, n_pupils) bytes).
 int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2* zz,
                         int N, int nx, int ny, int nz, int n_pupils, int zc, float scale,
                         double amp_bound, int precision, const float* target,
-                        const float* grad_intensity, float* gW, float* loss, int* status,
-                        cudaStream_t s);
+                        const float* grad_intensity, float* gW, float* loss,
+                        const float* Zt, int n_zern, double* zpart, float* grad_c,
+                        int* status, cudaStream_t s);
+size_t tc_zernike_parts_bytes(int N, int n_zern, int nb);
 
 }  // namespace psf
