@@ -500,7 +500,8 @@ def fourier_fwd_bwd(args, dev, stream, flush, world, check=True, steps=5):
     loss = torch.zeros(B, device=dev)
     gW = torch.zeros((B, N, N), device=dev)
     gc = torch.zeros((B, 21), device=dev)
-    need = lib.psf_fourier_backward_workspace_size(ctypes.byref(o), N, ctypes.byref(g.c), prec)
+    need = lib.psf_fourier_backward_workspace_size_batch(ctypes.byref(o), N, ctypes.byref(g.c),
+                                                         prec, B)
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
     p = api._ptr
 

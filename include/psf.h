@@ -184,6 +184,16 @@ int psf_fourier_vectorial_noalloc(const psf_optics* opt, int n_pupil,
 size_t psf_fourier_backward_workspace_size(const psf_optics* opt, int n_pupil,
                                            const psf_grid* grid, int precision);
 
+/* Workspace with which psf_fourier_vectorial_backward() handles `batch`
+ * pupils in one pass over all their planes (at most 2048 planes and 16 GB;
+ * split precisions).  The backward call takes the largest chunk of planes
+ * that fits the workspace it is given, from this size down to the one of
+ * psf_fourier_backward_workspace_size() (128 planes); longer chunks run the
+ * contractions in fewer, fuller launches. */
+size_t psf_fourier_backward_workspace_size_batch(const psf_optics* opt, int n_pupil,
+                                                 const psf_grid* grid, int precision,
+                                                 int batch);
+
 /* Gradient of L_b = sum_{z,x,y} g(I_b) for `batch` independent pupils, by the
  * adjoint of Eq. 8 with per-z recomputation (no pupil field is stored):
  *   dL/dW_0[p,q] = sum_{z,c} 2 Re(conj(G^_{c,z}[p,q]) i P_{c,z}[p,q]),

@@ -71,6 +71,7 @@ PROTOTYPES = {
     "psf_fourier_vectorial_noalloc": (_I, [_OPT, _I, _GRID, _P, _I, _P, _P,
                                            _P, _P]),
     "psf_fourier_backward_workspace_size": (_S, [_OPT, _I, _GRID, _I]),
+    "psf_fourier_backward_workspace_size_batch": (_S, [_OPT, _I, _GRID, _I, _I]),
     "psf_fourier_vectorial_backward": (_I, [_OPT, _I, _GRID, _I, _P, _I, _P,
                                             _I, _P, _P, _P, _P, _P, _P, _S,
                                             _P]),

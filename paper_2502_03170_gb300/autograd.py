@@ -34,8 +34,10 @@ def _backward_call(optics, n_pupil, grid, zernike, phase_map, target=None,
         zh = zh[None, :]
     B, nzern = zh.shape
     dev = torch.device("cuda", torch.cuda.current_device())
-    need = lib.psf_fourier_backward_workspace_size(ctypes.byref(o), n_pupil,
-                                                   ctypes.byref(g.c), prec)
+    # a workspace for the whole batch in one pass (the call falls back to
+    # shorter chunks when a smaller workspace is handed in)
+    need = lib.psf_fourier_backward_workspace_size_batch(ctypes.byref(o), n_pupil,
+                                                         ctypes.byref(g.c), prec, B)
     if need == 0:
         raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
     ws = (workspace or api.Workspace(dev)).get(need)

@@ -464,8 +464,11 @@ struct BackwardLayout {
   size_t bytes;
 };
 
+// max_planes: planes per chunk the split path may use (whole groups of
+// pupils share one pass; 128 unless the caller's workspace holds more)
 static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g,
-                                      int precision = PSF_PREC_FP32, int n_zern = 66) {
+                                      int precision = PSF_PREC_FP32, int n_zern = 66,
+                                      int max_planes = 128) {
   BackwardLayout L;
   memset(&L, 0, sizeof(L));
   Carver c(ws);
@@ -477,7 +480,7 @@ static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g,
   L.nodes.kl = c.take<float>(NN);
   L.zz = c.take<float2>(g->nz);
   if (precision != PSF_PREC_FP32) {
-    L.zc = tc_fourier_bwd_zchunk(N, g->nx, g->ny, g->nz);
+    L.zc = tc_fourier_bwd_zchunk(N, g->nx, g->ny, g->nz, max_planes);
     tc_fourier_bwd_carve(c.base, &c.off, N, g->nx, g->ny, g->nz, L.zc, &L.tc);
     L.zpart = (double*)c.take<char>(tc_zernike_parts_bytes(N, n_zern, L.tc.group));
     L.bytes = align_up(c.off, 256);
@@ -530,6 +533,16 @@ extern "C" size_t psf_fourier_backward_workspace_size(const psf_optics* opt,
   return backward_layout(nullptr, n_pupil, grid, precision).bytes;
 }
 
+extern "C" size_t psf_fourier_backward_workspace_size_batch(const psf_optics* opt,
+                                                             int n_pupil, const psf_grid* grid,
+                                                             int precision, int batch) {
+  const size_t base = psf_fourier_backward_workspace_size(opt, n_pupil, grid, precision);
+  if (base == 0 || batch < 1) return 0;
+  const long long planes = (long long)batch * grid->nz;
+  return backward_layout(nullptr, n_pupil, grid, precision, 66,
+                         (int)(planes < 2048 ? planes : 2048)).bytes;
+}
+
 extern "C" int psf_fourier_vectorial_backward(
     const psf_optics* opt, int n_pupil, const psf_grid* grid, int batch,
     const double* zernike, int n_zern, const float* phase_map, int precision,
@@ -557,7 +570,12 @@ extern "C" int psf_fourier_vectorial_backward(
     return fail(PSF_ERR_ARG, "no output requested");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   const int N = n_pupil;
-  BackwardLayout L = backward_layout(workspace, N, grid, precision);   // sized for 66 terms
+  // the largest chunk (up to the whole batch, 2048 planes) the workspace holds
+  int max_planes = (long long)batch * grid->nz < 2048 ? batch * grid->nz : 2048;
+  while (max_planes > 128 &&
+         backward_layout(nullptr, N, grid, precision, 66, max_planes).bytes > ws_bytes)
+    max_planes = max_planes / 2 > 128 ? max_planes / 2 : 128;
+  BackwardLayout L = backward_layout(workspace, N, grid, precision, 66, max_planes);
   if (ws_bytes < L.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
   cudaStream_t s = (cudaStream_t)stream;

@@ -98,7 +98,7 @@ struct TcBwdOperands {
   int group;                 // pupils per group (planes of a chunk span pupils)
 };
 const char* tc_fourier_bwd_supported(int N, int nx, int ny);
-int tc_fourier_bwd_zchunk(int N, int nx, int ny, int nz);
+int tc_fourier_bwd_zchunk(int N, int nx, int ny, int nz, int max_planes);
 int tc_fourier_bwd_group(int nz, int zc);
 void tc_fourier_bwd_carve(char* base, size_t* off, int N, int nx, int ny, int nz, int zc,
                           TcBwdOperands* out);

@@ -23,13 +23,13 @@ TOL_G = 1e-4
 PREC = {"fp32": 0, "split_fp16": 1, "split_bf16": 2}
 
 
-def gpu_backward(d, N, grid, zern, pm, target=None, grad_I=None, prec="fp32"):
+def gpu_backward(d, N, grid, zern, pm, target=None, grad_I=None, prec="fp32", ws_bytes=None):
     lib = _lib.load()
     o = api.make_optics(d)
     g = api.Grid(grid)
     batch = zern.shape[0]
-    need = lib.psf_fourier_backward_workspace_size(ctypes.byref(o), N,
-                                                   ctypes.byref(g.c), PREC[prec])
+    need = ws_bytes or lib.psf_fourier_backward_workspace_size(ctypes.byref(o), N,
+                                                               ctypes.byref(g.c), PREC[prec])
     assert need > 0, lib.psf_last_error()
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
@@ -192,3 +192,34 @@ def test_backward_cta_pair_matches_single_cta(lib, N, nx, ny, nz, batch, use_tar
         L, gWr, gcr, _ = oa.loss_and_grad(oracle_optics(d), N, grid, zern[0], pm[0], T[0])
         assert rel_l2(out["1"][1][0], gWr) <= 1e-4
         assert rel_l2(out["1"][2][0], gcr) <= 1e-4
+
+
+@pytest.mark.parametrize("use_target", [True, False])
+def test_backward_chunking_is_invisible(lib, use_target):
+    """Six pupils of 32 planes: with the default workspace the adjoint runs
+    two groups (128-plane chunks: 4 + 2 pupils), with the batch-sized one a
+    single 192-plane group.  Each plane's arithmetic and every summation
+    order are the same, so loss and gradients are bitwise equal."""
+    rng = np.random.default_rng(21)
+    d = W.optics_gibson_lanni(1.0)
+    N, nx, ny, nz, B = 32, 16, 24, 32, 6
+    grid = dict(nx=nx, ny=ny, dx=0.03, dy=0.035, z=np.linspace(-0.8, 0.8, nz))
+    zern = np.zeros((B, 21))
+    zern[:, 3:15] = rng.normal(0, 0.15, (B, 12))
+    pm = rng.normal(0, 0.2, (B, N, N))
+    T = rng.uniform(0, 2e-4, (B, nz, nx, ny))
+    G = rng.normal(0, 1.0, (B, nz, nx, ny))
+    lib_ = _lib.load()
+    o = api.make_optics(d)
+    g = api.Grid(grid)
+    small = lib_.psf_fourier_backward_workspace_size(ctypes.byref(o), N, ctypes.byref(g.c), 1)
+    big = lib_.psf_fourier_backward_workspace_size_batch(ctypes.byref(o), N, ctypes.byref(g.c),
+                                                         1, B)
+    assert big > small
+    out = []
+    for ws_bytes in (small, big):
+        out.append(gpu_backward(d, N, grid, zern, pm, target=T if use_target else None,
+                                grad_I=None if use_target else G, prec="split_fp16",
+                                ws_bytes=ws_bytes))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)

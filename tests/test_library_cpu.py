@@ -164,3 +164,19 @@ def test_harmonic_order_and_validation(cpu_lib):
                                               64, 8, 8, 0.02, 0.02, -1, d,
                                               ctypes.c_void_p(256), 1 << 30, None)
     assert r == _lib.PSF_ERR_ARG
+
+
+def test_backward_batch_workspace(cpu_lib):
+    """The batch-sized adjoint workspace grows with the batch up to its cap
+    and never falls below the default one."""
+    o = api.make_optics(W.optics_plain())
+    g = api.Grid(dict(nx=128, ny=128, dx=0.02, dy=0.02, z=np.linspace(-1, 1, 32)))
+    base = cpu_lib.psf_fourier_backward_workspace_size(ctypes.byref(o), 256, ctypes.byref(g.c), 1)
+    sizes = [cpu_lib.psf_fourier_backward_workspace_size_batch(ctypes.byref(o), 256,
+                                                               ctypes.byref(g.c), 1, b)
+             for b in (1, 4, 16, 64, 128)]
+    assert base > 0 and all(x > 0 for x in sizes)
+    assert sizes[0] <= base and sizes[1] == base          # 4 x 32 = 128 planes
+    assert sizes[1] < sizes[2] < sizes[3] == sizes[4]     # capped at 2048 planes
+    assert cpu_lib.psf_fourier_backward_workspace_size_batch(ctypes.byref(o), 256,
+                                                             ctypes.byref(g.c), 1, 0) == 0
