@@ -42,10 +42,10 @@ FP32_LANES_PER_SM = 128
 # command and the figures).  A figure holds only for the source it was taken
 # on: when the kernel's sources hash differently, traffic is reported as null.
 PROFILED_TRAFFIC = {
-    # 19-plane z-chunk (256^2 pupil, 512^2 px), CTA-pair kernel, stage 2:
-    # 61.96 MB read + 3.52 MB written
+    # one 128-plane launch (256^2 pupil, 512^2 px), CTA-pair kernel, stage 2:
+    # 404.86 MB read + 113.36 MB written (U streams from HBM at this chunk)
     "stage2_contraction_intensity": dict(
-        bytes_per_unit=(61.956e6 + 3.516e6) / 19, unit="plane",
+        bytes_per_unit=(404.857e6 + 113.357e6) / 128, unit="plane",
         sources=("tc_kernels.cu:k_split_cgemm_pair", "tc_kernels.cu:tile_epilogue",
                  "tc_kernels.cu:store_rows_t4", "tc_ptx.cuh", "tc_pair_ptx.cuh"),
         sha256_16="0e6b71e56aaad66b", precision="split_fp16"),
