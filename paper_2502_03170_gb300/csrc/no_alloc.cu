@@ -21,6 +21,12 @@
 #include "psf_common.cuh"
 
 namespace psf {
+// psf_api.cu: workspace of the Fourier forward at one plane per z-chunk
+size_t fourier_min_workspace_size(const psf_optics* opt, int n_pupil, const psf_grid* grid,
+                                  int precision);
+}  // namespace psf
+
+namespace psf {
 void set_last_error(const char* msg);
 }
 
@@ -63,13 +69,15 @@ extern "C" int psf_fourier_vectorial_noalloc(const psf_optics* opt, int n_pupil,
                                              const float* phase_map,
                                              float* intensity, void* fields,
                                              void* stream) {
-  const size_t need = psf_fourier_workspace_size(opt, n_pupil, grid, PSF_PREC_FP32);
-  if (need == 0) return PSF_ERR_ARG;   // message set by the size query
+  // the forward shortens its z-chunks to the array; reject what one plane
+  // per chunk does not fit
+  const size_t need = psf::fourier_min_workspace_size(opt, n_pupil, grid, PSF_PREC_FP32);
+  if (need == 0) return PSF_ERR_ARG;   // message set by the size check
   if (need > (size_t)PSF_NOALLOC_SCRATCH_BYTES) {
     char msg[200];
     snprintf(msg, sizeof(msg),
-             "noalloc: these sizes need %zu bytes of scratch; the fixed array "
-             "holds %zu (use psf_fourier_vectorial with a workspace)",
+             "noalloc: these sizes need %zu bytes of scratch even one plane at a "
+             "time; the fixed array holds %zu (use psf_fourier_vectorial with a workspace)",
              need, (size_t)PSF_NOALLOC_SCRATCH_BYTES);
     psf::set_last_error(msg);
     return PSF_ERR_WORKSPACE;

@@ -117,3 +117,27 @@ def test_cta_pair_kernel_matches_single_cta(lib, nx, ny, N, monkeypatch):
     Ir = of.psf_fourier(oracle_optics(c["optics"]), N, dict(grid, z=grid["z"][2:3]),
                         zernike=c["zernike"])
     assert max_rel(out["1"][2:3], Ir) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16", "chirpz_fp32"])
+def test_short_chunks_from_a_small_workspace(lib, prec):
+    """Handed a workspace below psf_fourier_workspace_size(), the forward
+    runs shorter z-chunks; every plane's arithmetic is the same, so the stack
+    is bitwise the one of the full workspace."""
+    import ctypes
+    c = W.fourier(n_pupil=64, nx=96, nz=40)
+    o = api.make_optics(c["optics"])
+    g = api.Grid(c["grid"])
+    p = api.PRECISIONS[prec]
+    full = lib.psf_fourier_workspace_size(ctypes.byref(o), 64, ctypes.byref(g.c), p)
+    zh = np.ascontiguousarray(c["zernike"], dtype=np.float64)
+    out = []
+    for ws_bytes in (full, full // 3):
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        I = torch.empty((g.c.nz, g.c.nx, g.c.ny), device="cuda")
+        _lib.check(lib, lib.psf_fourier_vectorial(
+            ctypes.byref(o), 64, ctypes.byref(g.c), zh.ctypes.data_as(ctypes.c_void_p),
+            len(zh), None, p, api._ptr(I), None, api._ptr(ws), ws_bytes, api._stream()))
+        torch.cuda.synchronize()
+        out.append(I.cpu().numpy())
+    assert np.array_equal(out[0], out[1])

@@ -55,17 +55,34 @@ def test_noalloc_matches_workspace_entry_point(lib):
             assert np.max(np.abs(F - F_ref)) <= TOL * np.max(np.abs(F_ref)), rep
 
 
-def test_noalloc_rejects_sizes_beyond_the_array(lib):
-    c = W.fourier()                       # 256^2 pupil, 512^2 px: too big
+def test_noalloc_runs_large_stacks_in_short_chunks(lib):
+    """The 256^2-pupil, 512^2-pixel stack needs far more than the 24 MiB array
+    in one launch; the forward shortens its z-chunks to the array and gives
+    the stack of the workspace entry point."""
+    c = W.fourier(nz=6)
     o = api.make_optics(c["optics"])
     g = api.Grid(c["grid"])
-    need = lib.psf_fourier_workspace_size(ctypes.byref(o), c["n_pupil"],
-                                          ctypes.byref(g.c), 0)
+    need = lib.psf_fourier_workspace_size(ctypes.byref(o), c["n_pupil"], ctypes.byref(g.c), 0)
     assert need > (24 << 20)
+    pm = torch.zeros((c["n_pupil"], c["n_pupil"]), device="cuda")
+    I, F = _noalloc(lib, c["optics"], c["n_pupil"], c["grid"], c["zernike"], pm)
+    I_ref, F_ref = api.fourier(c["optics"], c["n_pupil"], c["grid"], zernike=c["zernike"],
+                               fields=True)
+    I_ref, F_ref = I_ref.cpu().numpy(), F_ref.cpu().numpy()
+    assert np.max(np.abs(I - I_ref)) <= TOL * np.max(np.abs(I_ref))
+    assert np.max(np.abs(F - F_ref)) <= TOL * np.max(np.abs(F_ref))
+
+
+def test_noalloc_rejects_sizes_beyond_the_array(lib):
+    """A 1024^2 pupil does not fit the array even one plane at a time."""
+    c = W.fourier(nz=2)
+    N = 1024
+    o = api.make_optics(c["optics"])
+    g = api.Grid(c["grid"])
     I = torch.zeros(1, device="cuda")
     r = lib.psf_fourier_vectorial_noalloc(
-        ctypes.byref(o), c["n_pupil"], ctypes.byref(g.c), None, 0, None,
+        ctypes.byref(o), N, ctypes.byref(g.c), None, 0, None,
         api._ptr(I), None, api._stream())
     assert r == _lib.PSF_ERR_WORKSPACE
     msg = lib.psf_last_error().decode()
-    assert str(need) in msg and str(24 << 20) in msg
+    assert "one plane at a time" in msg and str(24 << 20) in msg
