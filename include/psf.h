@@ -140,8 +140,10 @@ size_t psf_fourier_workspace_size(const psf_optics* opt, int n_pupil,
  * I = |E_x|^2 + |E_y|^2 + |E_z|^2 (Eq. 8, Eq. 6, Eq. 12-17).
  *   zernike    host [n_zern] (may be NULL if n_zern == 0), 0 <= n_zern <= 66
  *   phase_map  device float [n_pupil][n_pupil] W_0 in radians, or NULL
- *   intensity  device float [nz][nx][ny]  (required)
- *   fields     device complex64 [nz][3][nx][ny], or NULL
+ *   intensity  float [nz][nx][ny] (required), device memory or pinned host
+ *              memory (written through its device alias; host memory that is
+ *              not pinned gives PSF_ERR_ARG before any launch)
+ *   fields     complex64 [nz][3][nx][ny], or NULL (same memory rules)
  * Sizes: 2 <= n_pupil <= 4096, nx, ny, nz >= 1. */
 int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
                           const psf_grid* grid, const double* zernike,
@@ -241,7 +243,8 @@ size_t psf_bessel_workspace_size(const psf_optics* base, int n_emitters,
  *   depth, zernike, z_offsets, z : DEVICE arrays (double, double, int, double)
  *   phase_theta  device float [n_emitters][n_theta] (radians) or NULL
  *   n_slices   = z_offsets[n_emitters] (host copy, for sizing)
- *   intensity  device float [n_slices][nx][ny] (packed); may be NULL when
+ *   intensity  float [n_slices][nx][ny] (packed; device or pinned host
+ *              memory, as for psf_fourier_vectorial); may be NULL when
  *              profiles is given (profiles only, no Cartesian epilogue)
  *   profiles   device complex64 [n_slices][3][n_r] (I_0, I_1, I_2) or NULL
  * A non-zero m != 0 coefficient without PSF_PROJECT_AXISYMMETRIC marks the

@@ -152,7 +152,7 @@ def harmonic_order(zernike, tol=1e-7):
 
 
 def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
-                    m_max=None, tol=1e-7, workspace=None, stream=None):
+                    m_max=None, tol=1e-7, workspace=None, stream=None, out=None):
     """Batched vectorial PSFs by the spherical strategy for pupils without
     axial symmetry (azimuthal harmonics |m| <= m_max of the pupil; m != 0
     Zernike terms enter exactly).  m_max defaults to harmonic_order(zernike,
@@ -168,7 +168,8 @@ def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, 
     if need == 0:
         raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
     buf = ws.get(need)
-    I = torch.empty((a.n_slices, nx, ny), dtype=torch.float32, device=dev)
+    I = out if out is not None else torch.empty((a.n_slices, nx, ny), dtype=torch.float32,
+                                                device=dev)
     check(lib, lib.psf_bessel_vectorial_harmonic(
         ctypes.byref(o), a.n_em, _ptr(a.depth), _ptr(a.zern), a.n_zern, _ptr(a.offs),
         _ptr(a.z), a.n_slices, n_theta, n_r, nx, ny, float(dx), float(dy), int(m_max),
@@ -205,14 +206,15 @@ class _BesselArgs:
 
 def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
            project=False, profiles=False, precision="fp32", workspace=None,
-           stream=None, intensity=True, phase_theta=None):
+           stream=None, intensity=True, phase_theta=None, out=None):
     """Batched vectorial PSFs by the Bessel strategy (Eq. 10-11).
 
     depth [n_em], zernike [n_em, n_zern], z_offsets [n_em + 1] (int32),
     z [n_slices]: torch tensors on the device (or arrays, copied there);
     phase_theta [n_em, n_theta] (optional): free radial phase at the
     Gauss-Legendre nodes, radians.
-    Returns intensity [n_slices, nx, ny] (and profiles [n_slices, 3, n_r]).
+    Returns intensity [n_slices, nx, ny] (and profiles [n_slices, 3, n_r]);
+    ``out`` (device or pinned host float32 [n_slices, nx, ny]) receives it.
     """
     lib = _lib.load()
     a = _BesselArgs(optics, depth, zernike, z_offsets, z, project, phase_theta)
@@ -226,8 +228,8 @@ def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
     if need == 0:
         raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
     buf = ws.get(need)
-    I = torch.empty((n_slices, nx, ny), dtype=torch.float32,
-                    device=dev) if intensity else None
+    I = (out if out is not None else torch.empty((n_slices, nx, ny), dtype=torch.float32,
+                                                 device=dev)) if intensity else None
     P = torch.empty((n_slices, 3, n_r), dtype=torch.complex64,
                     device=dev) if profiles else None
     check(lib, lib.psf_bessel_vectorial(

@@ -330,6 +330,28 @@ static NodeParams node_params(const psf_optics* opt, int N, const double* zern,
   return p;
 }
 
+// Output buffers may be device memory or pinned host memory (page-locked
+// and registered with CUDA): the kernels then store through its device alias
+// over the host link, so the transfer of the result overlaps the
+// computation.  Host memory that is not registered is rejected (the device
+// could not reach it); the check runs on the host before any launch.
+static int resolve_output(void** p, const char* what) {
+  if (!*p) return PSF_OK;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, *p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PSF_ERR_ARG, "%s: not a pointer CUDA knows", what);
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return PSF_OK;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *p = a.devicePointer;
+    return PSF_OK;
+  }
+  return fail(PSF_ERR_ARG,
+              "%s: host memory that is not pinned (use device memory or pinned host memory)",
+              what);
+}
+
 // Workspace of the Fourier forward with one plane per z-chunk (the least
 // psf_fourier_vectorial() runs with; the no-alloc entry point checks it).
 size_t fourier_min_workspace_size(const psf_optics* opt, int n_pupil, const psf_grid* grid,
@@ -390,6 +412,9 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed (one plane per chunk)",
                 ws_bytes, L.bytes);
   L = fourier_layout(workspace, N, grid, precision, max_planes);
+  if ((r = resolve_output((void**)&intensity, "intensity")) ||
+      (r = resolve_output(&fields, "fields")))
+    return r;
   cudaStream_t s = (cudaStream_t)stream;
 
   std::vector<float2> zz(grid->nz);
@@ -998,6 +1023,9 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
                                  profiles == nullptr, precision);
   if (ws_bytes < L.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
+  if ((r = resolve_output((void**)&intensity, "intensity")) ||
+      (r = resolve_output(&profiles, "profiles")))
+    return r;
   if (profiles) L.prof = (float2*)profiles;
   cudaStream_t s = (cudaStream_t)stream;
   BesselRun R;
@@ -1373,6 +1401,7 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
   HarmLayout H = harm_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny, m_max);
   if (ws_bytes < H.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, H.bytes);
+  if ((r = resolve_output((void**)&intensity, "intensity"))) return r;
   cudaStream_t s = (cudaStream_t)stream;
   // the emitter table carries the axisymmetric part (m != 0 terms dropped
   // there; they enter through the harmonics)

@@ -121,3 +121,21 @@ def test_bessel_config_full_size_sampled(lib, prec):
         assert max_rel(Ie, Ir) <= TOL[prec], e
     del I
     torch.cuda.empty_cache()
+
+
+def test_bessel_outputs_to_pinned_host_memory(lib):
+    """Both spherical entry points write straight into pinned host memory:
+    bitwise the device results."""
+    c = W.bessel(n_emitters=6, n_theta=48, n_r=40, nx=20, nz_lo=2, nz_hi=5)
+    args = (c["optics"], c["depth"], c["zernike"], c["z_offsets"], c["z"], 48, 40, 20, 20,
+            c["dx"], c["dy"])
+    n = int(c["z_offsets"][-1])
+    I_dev = api.bessel(*args, project=True)
+    I_pin = torch.empty((n, 20, 20), dtype=torch.float32, pin_memory=True)
+    api.bessel(*args, project=True, out=I_pin)
+    H_dev = api.bessel_harmonic(*args, m_max=5)
+    H_pin = torch.empty((n, 20, 20), dtype=torch.float32, pin_memory=True)
+    api.bessel_harmonic(*args, m_max=5, out=H_pin)
+    torch.cuda.synchronize()
+    assert np.array_equal(I_pin.numpy(), I_dev.cpu().numpy())
+    assert np.array_equal(H_pin.numpy(), H_dev.cpu().numpy())

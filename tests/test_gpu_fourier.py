@@ -141,3 +141,21 @@ def test_short_chunks_from_a_small_workspace(lib, prec):
         torch.cuda.synchronize()
         out.append(I.cpu().numpy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16", "chirpz_fp32"])
+def test_output_to_pinned_host_memory(lib, prec):
+    """The forward writes straight into pinned host memory (through its device
+    alias): bitwise the device result.  Host memory that is not pinned is
+    rejected before any launch."""
+    c = W.fourier(n_pupil=64, nx=72, nz=5)
+    I_dev = api.fourier(c["optics"], 64, c["grid"], zernike=c["zernike"], precision=prec)
+    I_pin = torch.empty(tuple(I_dev.shape), dtype=torch.float32, pin_memory=True)
+    api.fourier(c["optics"], 64, c["grid"], zernike=c["zernike"], precision=prec, out=I_pin)
+    torch.cuda.synchronize()
+    assert np.array_equal(I_pin.numpy(), I_dev.cpu().numpy())
+    I_page = torch.empty(tuple(I_dev.shape), dtype=torch.float32)
+    with pytest.raises(_lib.PsfError) as e:
+        api.fourier(c["optics"], 64, c["grid"], zernike=c["zernike"], precision=prec,
+                    out=I_page)
+    assert e.value.code == _lib.PSF_ERR_ARG
