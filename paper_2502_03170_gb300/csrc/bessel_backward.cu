@@ -494,8 +494,11 @@ __host__ __device__ inline SbLayout sb_layout(int npix, int n_r, int ng) {
   L.flag = take(sizeof(int), 4);
   L.gbuf = take(2 * (size_t)npix * sizeof(float), 128);
   L.pbuf = take(2 * rows * sizeof(float2), 128);
-  L.W = take((size_t)ng * sizeof(float2), 16);
-  L.sf = take((size_t)ng * sizeof(float), 16);
+  // sorted per-group values, padded by one entry per cell (index k + cell):
+  // the threads of pass 2a walk consecutive cells' runs in lockstep, and
+  // without the padding runs of ~16 entries put their lanes on the same banks
+  L.W = take(((size_t)ng + n_r) * sizeof(float2), 16);
+  L.sf = take(((size_t)ng + n_r) * sizeof(float), 16);
   L.cs = take((size_t)n_r * sizeof(int), 16);
   L.lo = take(rows * sizeof(float2), 16);
   L.hi = take(rows * sizeof(float2), 16);
@@ -583,7 +586,8 @@ k_bessel_adj_epilogue_staged(BesselParams p, float2* __restrict__ prof,
       tgm[k] = fg.y - fg.z;
     }
   }
-  for (int q = tid; q < ng; q += SB_THREADS) sf[q] = sorted_f[q];
+  for (int c = tid; c < n_r - 1; c += SB_THREADS)
+    for (int q = cell_start[c]; q < cell_start[c + 1]; ++q) sf[q + c] = sorted_f[q];
   for (int q = tid; q < n_r; q += SB_THREADS) cs[q] = cell_start[q];
   const float Nn = (float)(p.pol[0] * p.pol[0] + p.pol[1] * p.pol[1] +
                            p.pol[2] * p.pol[2] + p.pol[3] * p.pol[3]);
@@ -652,7 +656,8 @@ k_bessel_adj_epilogue_staged(BesselParams p, float2* __restrict__ prof,
           v3 = h3 ? 2.f * d3 : 0.f;
         }
         const float sp = v0 + v3, sm = v1 + v2;
-        W[tpc[k] & 0xFFFF] = make_float2(sp + sm, fmaf(tgp[k], sp, tgm[k] * sm));
+        W[(tpc[k] & 0xFFFF) + (tpc[k] >> 16)] =
+            make_float2(sp + sm, fmaf(tgp[k], sp, tgm[k] * sm));
       }
     }
     __syncthreads();
@@ -664,8 +669,8 @@ k_bessel_adj_epilogue_staged(BesselParams p, float2* __restrict__ prof,
         float M0 = 0.f, M1 = 0.f, M2 = 0.f, K0 = 0.f, K1 = 0.f, K2 = 0.f;
 #pragma unroll 4
         for (int k = half ? mid : k0; k < (half ? k1 : mid); ++k) {
-          const float2 w = W[k];
-          const float f = sf[k], u = 1.f - f;
+          const float2 w = W[k + c];
+          const float f = sf[k + c], u = 1.f - f;
           const float uu = u * u, uf = u * f, ff = f * f;
           M0 = fmaf(w.x, uu, M0);
           M1 = fmaf(w.x, uf, M1);
