@@ -592,8 +592,9 @@ def fourier_accuracy(I, c, planes=(0, 64, 127)):
 def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
     """The spherical strategy with every Zernike term (azimuthal harmonics,
     no axisymmetric projection) on emitters of the batched workload: voxels/s
-    at the tail-bound order for 1e-7 and at M = 8, error of one emitter
-    against the FP64 harmonic oracle at the same order."""
+    at the tail-bound order for 1e-7 with the adaptive per-emitter order
+    (tail_tol 1e-7) and without it, and at M = 8; error of one emitter
+    against the FP64 harmonic oracle with the same order rule."""
     import torch
 
     from oracle import bessel_harmonic as bh
@@ -606,10 +607,11 @@ def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
     out = {"n_emitters": n_em, "n_slices": int(c["z_offsets"][-1]),
            "tail_bound_tol": 1e-7}
     m_bound = api.harmonic_order(c["zernike"], 1e-7)
-    for name, m in (("m_bound", m_bound), ("m_8", 8)):
+    for name, m, tt in (("m_bound_adaptive", m_bound, 1e-7), ("m_bound", m_bound, 0.0),
+                        ("m_8", 8, 0.0)):
         run = lambda: api.bessel_harmonic(c["optics"], c["depth"], c["zernike"],
                                           c["z_offsets"], c["z"], *geo, m_max=m,
-                                          workspace=ws, stream=stream)
+                                          tail_tol=tt, workspace=ws, stream=stream)
         I = run()
         ms = 0.0
         for _ in range(steps):
@@ -622,14 +624,19 @@ def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
             ms += a.elapsed_time(b)
         e0, e1 = int(c["z_offsets"][0]), int(c["z_offsets"][1])
         Iref = bh.psf_harmonic_batch(Optics.from_dict(c["optics"]), c["depth"], c["zernike"],
-                                     c["z_offsets"], c["z"], *geo, m, emitters=[0])
+                                     c["z_offsets"], c["z"], *geo, m, emitters=[0],
+                                     tail_tol=tt)
         Ie = I[e0:e1].cpu().numpy()
-        out[name] = {"m_max": m, "ms": ms / steps,
+        out[name] = {"m_max": m, "tail_tol": tt, "ms": ms / steps,
                      "voxels_per_s": I.numel() / (ms / steps * 1e-3),
                      "max_rel_err_vs_oracle_emitter0":
                          float(np.max(np.abs(Ie - Iref)) / np.max(Iref))}
         if name == "m_bound":
             I_bound = I[e0:e1].cpu().numpy()
+            out["m_bound_adaptive"]["truncation_vs_m_bound_emitter0"] = float(
+                np.max(np.abs(I_adapt - I_bound)) / np.max(I_bound))
+        elif name == "m_bound_adaptive":
+            I_adapt = Ie
         else:
             out[name]["truncation_vs_m_bound_emitter0"] = float(
                 np.max(np.abs(Ie - I_bound)) / np.max(I_bound))

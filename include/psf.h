@@ -291,15 +291,24 @@ size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_emitters
 /* Batched PSFs with every Zernike term (any m) by the azimuthal harmonics
  * |m| <= m_max (0 <= m_max <= 64).  Arguments as psf_bessel_vectorial()
  * (device arrays depth [n_em], zernike [n_em][n_zern], z_offsets [n_em+1],
- * z [n_slices]; intensity device [n_slices][nx][ny]); no free radial phase,
- * no profiles output; the flags PSF_SCALAR / PSF_FRESNEL select the model
- * (PSF_PROJECT_AXISYMMETRIC is ignored: no term is dropped). */
+ * z [n_slices]; intensity device or pinned host [n_slices][nx][ny]); no free
+ * radial phase, no profiles output; the flags PSF_SCALAR / PSF_FRESNEL select
+ * the model (PSF_PROJECT_AXISYMMETRIC is ignored: no term is dropped).
+ * tail_tol in [0, 1): with tail_tol > 0 each emitter keeps only the
+ * harmonics |m| <= M_e, M_e the largest |m| <= m_max with
+ * max_theta |P_m(theta)| > tail_tol max_theta |P_0(theta)| (0 if none; the
+ * harmonics past those that carry W fall faster than geometrically, so the
+ * dropped tail is about tail_tol; the tail bound of
+ * psf_bessel_harmonic_order() is pessimistic and the adaptive order
+ * typically halves the orders); 0 keeps m_max for every emitter.
+ * PSF_ERR_ARG for tail_tol outside [0, 1). */
 int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_emitters,
                                   const double* depth, const double* zernike,
                                   int n_zern, const int* z_offsets, const double* z,
                                   int n_slices, int n_theta, int n_r, int nx, int ny,
-                                  double dx, double dy, int m_max, float* intensity,
-                                  void* workspace, size_t ws_bytes, void* stream);
+                                  double dx, double dy, int m_max, double tail_tol,
+                                  float* intensity, void* workspace, size_t ws_bytes,
+                                  void* stream);
 
 /* Workspace for psf_bessel_vectorial_backward() (0 if the arguments are
  * invalid; the backward takes nx, ny <= 4096). */

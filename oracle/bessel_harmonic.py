@@ -42,6 +42,15 @@ terms, so the harmonics |m| > K d carry at most alpha^{K+1} / (K+1)! e^alpha
 (l1).  `harmonic_order` returns the smallest M = K d with that below tol;
 aliasing in the DFT only folds harmonics |m| >= N_phi - M > 3 M, bounded by
 the same tail.
+
+Adaptive order (tail_tol > 0): the bound is pessimistic; with the computed
+harmonics (|m| <= m_max) each emitter keeps M_e = the largest |m| with
+max_theta |P_m| > tail_tol max_theta |P_0| (0 if none), and the harmonics
+beyond it are dropped.  Past the few harmonics that carry W, |P_m| falls
+faster than geometrically (as J_k(a) ~ (a/2)^k / k!), so the dropped tail is
+about its first term, below tail_tol; a per-harmonic test (not the summed
+tail) keeps the decision clear of the rounding floor of an FP32 DFT, a few
+1e-8 of P_0 on every harmonic.
 """
 import math
 
@@ -115,12 +124,29 @@ KIND_G = (0, 2, 2, 1, 1)         # which g_n
 KIND_SHIFT = (0, -2, 2, -1, 1)   # P index = l + shift
 
 
-def harmonic_profiles(opt, n_theta, r, zs, zernike, m_max, w0=None):
-    """I_{c,l}(r_i, z) -> complex [nz, 3, 2M+5, len(r)] (order index l + M + 2)."""
+def adaptive_order(P, m_max, tail_tol):
+    """Largest |m| <= m_max with max_theta |P_m| > tail_tol max_theta |P_0|,
+    0 if none (P [2 m_max + 1, n_theta], row m + m_max)."""
+    amax = np.max(np.abs(P), axis=1)
+    lim = tail_tol * amax[m_max]
+    for M in range(m_max, 0, -1):
+        if amax[m_max + M] > lim or amax[m_max - M] > lim:
+            return M
+    return 0
+
+
+def harmonic_profiles(opt, n_theta, r, zs, zernike, m_max, w0=None, tail_tol=0.0):
+    """I_{c,l}(r_i, z) -> complex [nz, 3, 2M+5, len(r)] (order index l + M + 2).
+    With tail_tol > 0 the harmonics beyond the emitter's adaptive order
+    (adaptive_order) are dropped (set to zero) first."""
     th, wt = gl_rule(n_theta, opt.theta_max)
     sin_t, cos_t = np.sin(th), np.cos(th)
     g = angular_weights(opt, sin_t, cos_t)
     P = pupil_harmonics(opt, th, zernike, m_max, w0)
+    if tail_tol > 0.0:
+        M = adaptive_order(P, m_max, tail_tol)
+        keep = np.abs(np.arange(-m_max, m_max + 1)) <= M
+        P = np.where(keep[:, None], P, 0.0)
     coef = channel_coeffs(model_pol(opt))
     arg = opt.k * np.outer(np.asarray(r, dtype=np.float64), sin_t)
     zs = np.asarray(zs, dtype=np.float64)
@@ -156,10 +182,11 @@ def field_from_harmonics(I, cos_p, sin_p):
     return out
 
 
-def field_harmonic(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, m_max, w0=None):
+def field_harmonic(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, m_max, w0=None,
+                   tail_tol=0.0):
     """E [nz, 3, nx, ny]: profiles on the radial grid, interpolated."""
     r, r_max = radial_grid(n_r, nx, ny, dx, dy)
-    prof = harmonic_profiles(opt, n_theta, r, zs, zernike, m_max, w0)
+    prof = harmonic_profiles(opt, n_theta, r, zs, zernike, m_max, w0, tail_tol)
     rho, cos_p, sin_p = pixel_polar(nx, ny, dx, dy)
     E = np.empty((len(zs), 3, nx, ny), dtype=np.complex128)
     for iz in range(len(zs)):
@@ -179,13 +206,14 @@ def field_harmonic_direct(opt, n_theta, nx, ny, dx, dy, zs, zernike, m_max):
     return E
 
 
-def psf_harmonic(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, m_max, w0=None):
-    E = field_harmonic(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, m_max, w0)
+def psf_harmonic(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, m_max, w0=None,
+                 tail_tol=0.0):
+    E = field_harmonic(opt, n_theta, n_r, nx, ny, dx, dy, zs, zernike, m_max, w0, tail_tol)
     return np.sum(E.real ** 2 + E.imag ** 2, axis=1)
 
 
 def psf_harmonic_batch(opt, depths, zernikes, z_offsets, zs, n_theta, n_r, nx, ny,
-                       dx, dy, m_max, emitters=None):
+                       dx, dy, m_max, emitters=None, tail_tol=0.0):
     """Batched emitters, packed [z_offsets[-1], nx, ny] (or the listed ones)."""
     z_offsets = np.asarray(z_offsets)
     zs = np.asarray(zs, dtype=np.float64)
@@ -195,5 +223,6 @@ def psf_harmonic_batch(opt, depths, zernikes, z_offsets, zs, n_theta, n_r, nx, n
         o = opt.with_depth(depths[e])
         out.append(psf_harmonic(o, n_theta, n_r, nx, ny, dx, dy,
                                 zs[z_offsets[e]:z_offsets[e + 1]],
-                                None if zernikes is None else zernikes[e], m_max))
+                                None if zernikes is None else zernikes[e], m_max,
+                                tail_tol=tail_tol))
     return np.concatenate(out, axis=0)

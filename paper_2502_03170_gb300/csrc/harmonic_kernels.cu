@@ -14,18 +14,17 @@ PSF_D int kind_shift(int kind) {
 PSF_D int kind_g(int kind) { return kind == 0 ? 0 : (kind <= 2 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
-// One CTA per (theta node, emitter): e^{i W_na(theta, phi_k)} on the N_phi
-// azimuths, its DFT (harmonics |m| <= M) times the axisymmetric integrand,
-// then the channel/order mixtures Bh.
+// One CTA per (emitter, theta node): e^{i W_na(theta, phi_k)} on the N_phi
+// azimuths and its DFT (harmonics |m| <= M) times the axisymmetric
+// integrand -> Pm[e][m + M][j].
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restrict__ zern,
              const float* __restrict__ Zr, const float2* __restrict__ cs,
-             float2* __restrict__ Bh) {
+             float2* __restrict__ Pm) {
   extern __shared__ float2 sh[];
   float2* Ek = sh;                 // [n_phi]
-  float2* Pm = sh + p.n_phi;       // [2 M + 1]
-  const int j = blockIdx.x, e = blockIdx.y;
+  const int e = blockIdx.x, j = blockIdx.y;
   const int nP = 2 * p.m_max + 1, mask = p.n_phi - 1;
   const size_t ej = (size_t)e * p.n_theta + j;
   for (int k = threadIdx.x; k < p.n_phi; k += blockDim.x) {
@@ -54,9 +53,59 @@ k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restri
       im = fmaf(x.y, a.x, fmaf(-x.x, a.y, im));
     }
     const float2 h = cmul(base, make_float2(re, im));
-    Pm[mi] = make_float2(scale * h.x, scale * h.y);
+    Pm[((size_t)e * nP + mi) * p.n_theta + j] = make_float2(scale * h.x, scale * h.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive order, one CTA per emitter: a_m = max_j |P_m(theta_j)| (one warp
+// per harmonic), then M_e = the largest |m| <= M with a_m > tail_tol a_0 (0
+// if none).  Each harmonic is tested on its own, not the summed tail: the
+// rounding floor of the FP32 DFT (a few 1e-8 of a_0 on every harmonic)
+// summed over tens of harmonics would exceed the tolerance.  tail_tol = 0
+// keeps M_e = M.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_harm_order(HarmParams p, const float2* __restrict__ Pm, int* __restrict__ ord) {
+  __shared__ float amax[2 * kHarmMaxM + 1];
+  const int e = blockIdx.x, nP = 2 * p.m_max + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!(p.tail_tol > 0.0)) {
+    if (threadIdx.x == 0) ord[e] = p.m_max;
+    return;
+  }
+  for (int mi = warp; mi < nP; mi += 8) {
+    const float2* row = Pm + ((size_t)e * nP + mi) * p.n_theta;
+    float v = 0.f;
+    for (int j = lane; j < p.n_theta; j += 32) {
+      const float2 x = row[j];
+      v = fmaxf(v, sqrtf(x.x * x.x + x.y * x.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) amax[mi] = v;
   }
   __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double lim = p.tail_tol * (double)amax[p.m_max];
+  int M = 0;
+  for (int m = p.m_max; m >= 1; --m)
+    if ((double)amax[p.m_max + m] > lim || (double)amax[p.m_max - m] > lim) {
+      M = m;
+      break;
+    }
+  ord[e] = M;
+}
+
+// ---------------------------------------------------------------------------
+// Channel/order mixtures from the harmonics |m| <= M_e, one CTA per (theta
+// emitter, theta node): Bh[e][c][l'][j] (zero for |l| > M_e + 2).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_harm_mix(HarmParams p, ThetaTable t, EmitterTable et, const float2* __restrict__ Pm,
+           const int* __restrict__ ord, float2* __restrict__ Bh) {
+  const int e = blockIdx.x, j = blockIdx.y;
+  const int nP = 2 * p.m_max + 1, Me = ord[e];
   const bool ok = et.valid[e] != 0;
   const int L = p.m_max + 2;
   for (int o = threadIdx.x; o < 3 * p.n_ord; o += blockDim.x) {
@@ -65,13 +114,14 @@ k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restri
 #pragma unroll
     for (int kind = 0; kind < 5; ++kind) {
       const int m = l + kind_shift(kind);
-      if (m < -p.m_max || m > p.m_max) continue;
+      if (m < -Me || m > Me) continue;
       const double cr = p.coef[c][kind][0], ci = p.coef[c][kind][1];
       if (cr == 0.0 && ci == 0.0) continue;
       const int gk = kind_g(kind);
       const float2 g = make_float2((float)t.g[(size_t)(2 * gk) * p.n_theta + j],
                                    (float)t.g[(size_t)(2 * gk + 1) * p.n_theta + j]);
-      const float2 v = cmul(cmul(make_float2((float)cr, (float)ci), g), Pm[m + p.m_max]);
+      const float2 pm = Pm[((size_t)e * nP + m + p.m_max) * p.n_theta + j];
+      const float2 v = cmul(cmul(make_float2((float)cr, (float)ci), g), pm);
       acc.x += v.x;
       acc.y += v.y;
     }
@@ -140,20 +190,31 @@ __global__ void k_harm_defocus(int n_theta, ThetaTable t, const float2* __restri
 // ---------------------------------------------------------------------------
 // Radial contraction, one order per grid z: C[i][(s, c)] = sum_j Jt[|l|][i][j]
 // D[s][j] Bh[e(s)][c][l'][j].  Tile 64 radii x 32 columns, K step 16, 256
-// threads with 4 x 2 complex accumulators.
+// threads with 4 x 2 complex accumulators.  A tile none of whose columns
+// needs order l (|l| > M_e + 2, or no valid emitter) returns at once: the
+// epilogue reads no profile beyond its emitter's orders.
 // ---------------------------------------------------------------------------
 constexpr int HP_BM = 64, HP_BN = 32, HP_BK = 16;
 
 __global__ void __launch_bounds__(256)
 k_harm_profiles(HarmParams p, const float* __restrict__ Jt, const float2* __restrict__ Bh,
                 const int* __restrict__ slice_em, const int* __restrict__ valid,
-                const float2* __restrict__ D, int s0, int ns, float2* __restrict__ prof) {
+                const int* __restrict__ ord, const float2* __restrict__ D, int s0, int ns,
+                float2* __restrict__ prof) {
   __shared__ float As[HP_BK][HP_BM + 1];
   __shared__ float2 Bs[HP_BK][HP_BN + 1];
   const int li = blockIdx.z, L = p.m_max + 2;
   const int n = li >= L ? li - L : L - li;
   const int i0 = blockIdx.y * HP_BM, c0 = blockIdx.x * HP_BN;
   const int ncol = 3 * ns;
+  {
+    bool need = false;
+    if (threadIdx.x < HP_BN && c0 + (int)threadIdx.x < ncol) {
+      const int e = slice_em[s0 + (c0 + (int)threadIdx.x) / 3];
+      need = e >= 0 && valid[e] && n <= ord[e] + 2;
+    }
+    if (!__syncthreads_or(need)) return;
+  }
   const float* A = Jt + (size_t)n * p.n_r * p.n_theta;
   const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
   float2 acc[4][2];
@@ -217,7 +278,8 @@ k_harm_profiles(HarmParams p, const float* __restrict__ Jt, const float2* __rest
 // interpolated I_{c,l}.  With T_l = (i e^{i phi})^l at (x, y):
 //   (x, y): sum T_l v_l          (-x, -y): sum (-1)^l T_l v_l
 //   (-x, y): sum conj(T_l) v_l   (x, -y): sum (-1)^l conj(T_l) v_l,
-// kept as even and odd partial sums.  T_l by forward and backward
+// kept as even and odd partial sums over |l| <= M_e + 2 (the slice's
+// emitter order).  T_l by forward and backward
 // recurrences from l = 0 (the large low orders carry the least rounding);
 // |E_c|^2 = |sum|^2 (the -i prefactor has modulus 1).
 // ---------------------------------------------------------------------------
@@ -237,8 +299,8 @@ PSF_D void harm_add(MirrorAcc& m, float2 t, float2 v, bool odd) {
 
 __global__ void __launch_bounds__(256)
 k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
-                 const int* __restrict__ slice_em, const int* __restrict__ valid, int s0,
-                 float* __restrict__ I) {
+                 const int* __restrict__ slice_em, const int* __restrict__ valid,
+                 const int* __restrict__ ord, int s0, float* __restrict__ I) {
   const int sl = blockIdx.y, s = s0 + sl;
   const int e = slice_em[s];
   if (e < 0 || !valid[e]) return;
@@ -255,13 +317,13 @@ k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
   const float cp = rho > 0 ? (float)(x / rho) : 1.f, sp = rho > 0 ? (float)(y / rho) : 0.f;
   const float2 w = make_float2(-sp, cp);    // i e^{i phi}
   const float2 wc = make_float2(-sp, -cp);  // its inverse
-  const int L = p.m_max + 2;
+  const int L = p.m_max + 2, Le = ord[e] + 2;
   const float2* base = prof + (size_t)sl * 3 * p.n_ord * p.n_r + i0;
   MirrorAcc acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) acc[c] = MirrorAcc{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   float2 tf = make_float2(1.f, 0.f);
-  for (int l = 0; l <= L; ++l) {
+  for (int l = 0; l <= Le; ++l) {
     const bool odd = l & 1;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -272,7 +334,7 @@ k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
     tf = cmul(tf, w);
   }
   tf = wc;
-  for (int l = -1; l >= -L; --l) {
+  for (int l = -1; l >= -Le; --l) {
     const bool odd = (-l) & 1;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -306,9 +368,12 @@ k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
 }  // namespace
 
 void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const double* zern,
-                       const float* Zr, const float2* cs, float2* Bh, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * ((size_t)p.n_phi + 2 * p.m_max + 1);
-  k_harm_pupil<<<dim3(p.n_theta, p.n_em), 128, smem, s>>>(p, t, e, zern, Zr, cs, Bh);
+                       const float* Zr, const float2* cs, float2* Pm, int* ord, float2* Bh,
+                       cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t)p.n_phi;
+  k_harm_pupil<<<dim3(p.n_em, p.n_theta), 128, smem, s>>>(p, t, e, zern, Zr, cs, Pm);
+  k_harm_order<<<p.n_em, 256, 0, s>>>(p, Pm, ord);
+  k_harm_mix<<<dim3(p.n_em, p.n_theta), 128, 0, s>>>(p, t, e, Pm, ord, Bh);
 }
 
 void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t s) {
@@ -318,19 +383,20 @@ void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t
 
 void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,
                           const float2* Bh, const int* slice_em, const int* valid,
-                          const float2* zz, int s0, int ns, float2* D, float2* prof,
-                          cudaStream_t s) {
+                          const int* ord, const float2* zz, int s0, int ns, float2* D,
+                          float2* prof, cudaStream_t s) {
   const long long nd = (long long)ns * p.n_theta;
   k_harm_defocus<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(p.n_theta, t, zz, s0, ns, D);
   const dim3 grid(ceil_div(3 * ns, HP_BN), ceil_div(p.n_r, HP_BM), p.n_ord);
-  k_harm_profiles<<<grid, 256, 0, s>>>(p, Jt, Bh, slice_em, valid, D, s0, ns, prof);
+  k_harm_profiles<<<grid, 256, 0, s>>>(p, Jt, Bh, slice_em, valid, ord, D, s0, ns, prof);
 }
 
 void launch_harm_intensity(const HarmParams& p, const float2* prof, const int* slice_em,
-                           const int* valid, int s0, int ns, float* I, cudaStream_t s) {
+                           const int* valid, const int* ord, int s0, int ns, float* I,
+                           cudaStream_t s) {
   const int quarter = ((p.nx + 1) / 2) * ((p.ny + 1) / 2);
   const dim3 grid(ceil_div(quarter, 256), ns);
-  k_harm_intensity<<<grid, 256, 0, s>>>(p, prof, slice_em, valid, s0, I);
+  k_harm_intensity<<<grid, 256, 0, s>>>(p, prof, slice_em, valid, ord, s0, I);
 }
 
 }  // namespace psf

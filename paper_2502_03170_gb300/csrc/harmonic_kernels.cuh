@@ -26,6 +26,7 @@ struct HarmParams {
   int n_theta, n_r, nx, ny, n_em, n_zern;
   int m_max, n_phi, n_ord;       // n_ord = 2 m_max + 5 orders l = -(m_max+2) ..
   double k, dr, r_max, dx, dy;
+  double tail_tol;               // adaptive order per emitter (0: M_e = m_max)
   int n_na;                      // m != 0 Noll terms j <= n_zern
   int na_j[kHarmMaxNA];          // their Noll indices
   int na_m[kHarmMaxNA];          // |m|
@@ -33,12 +34,15 @@ struct HarmParams {
   double coef[3][5][2];          // channel x kind, complex (Jones vector of the model)
 };
 
-// Bh[e][c][l'][theta] (complex) from the emitter table, the per-call
-// radial table Zr [n_na][n_theta] (N_j R_n^{|m|}(sin theta / s_max)) and the
-// azimuth table cs [n_phi] = e^{2 pi i k / n_phi}.
+// Pupil harmonics Pm[e][m + M][theta] (complex) from the emitter table, the
+// per-call radial table Zr [n_na][n_theta] (N_j R_n^{|m|}(sin theta / s_max))
+// and the azimuth table cs [n_phi] = e^{2 pi i k / n_phi}; the emitter
+// orders ord[e] = M_e (the largest |m| with max_theta |P_m| > tail_tol
+// max_theta |P_0|, 0 if none; m_max with tail_tol = 0); and the
+// channel/order mixtures Bh[e][c][l'][theta] from the harmonics |m| <= M_e.
 void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e,
                        const double* zern, const float* Zr, const float2* cs,
-                       float2* Bh, cudaStream_t s);
+                       float2* Pm, int* ord, float2* Bh, cudaStream_t s);
 
 // Jt[n][i][j] = w_j J_n(k r_i sin theta_j), n = 0 .. m_max + 2 (FP64 by
 // Miller's backward recurrence, all orders of one argument at once; stored
@@ -48,16 +52,18 @@ void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t
 // Profiles of the slices [s0, s0 + ns) (D: scratch [ns][n_theta] for the
 // defocus phasors e^{i k z_s cos theta_j}):
 //   prof[s - s0][c][l'][i] = sum_j Jt[|l|][i][j] D[s][j] Bh[e(s)][c][l'][j]
+// for |l| <= M_e(s) + 2 (other orders may be left unwritten).
 void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,
                           const float2* Bh, const int* slice_em, const int* valid,
-                          const float2* zz, int s0, int ns, float2* D, float2* prof,
-                          cudaStream_t s);
+                          const int* ord, const float2* zz, int s0, int ns, float2* D,
+                          float2* prof, cudaStream_t s);
 
-// I[s][a][b] = sum_c |sum_l i^l e^{i l phi} lerp(prof[s - s0][c][l'], rho)|^2
+// I[s][a][b] = sum_c |sum_{|l| <= M_e + 2} i^l e^{i l phi}
+//                     lerp(prof[s - s0][c][l'], rho)|^2
 // for the slices [s0, s0 + ns) whose emitter is valid (one thread per
 // quarter pixel and its three mirrors, which share the radius).
 void launch_harm_intensity(const HarmParams& p, const float2* prof,
-                           const int* slice_em, const int* valid, int s0, int ns,
-                           float* I, cudaStream_t s);
+                           const int* slice_em, const int* valid, const int* ord,
+                           int s0, int ns, float* I, cudaStream_t s);
 
 }  // namespace psf

@@ -1304,6 +1304,8 @@ struct HarmLayout {
   BesselLayout b;
   float2* cs;      // [n_phi] e^{2 pi i k / n_phi}
   float* Zr;       // [kHarmMaxNA][n_theta] N_j R_n^{|m|}(sin theta / s_max)
+  float2* Pm;      // [n_em][2 m_max + 1][n_theta] pupil harmonics
+  int* ord;        // [n_em] adaptive order M_e
   float2* Bh;      // [n_em][3][n_ord][n_theta]
   float* Jt;       // [m_max + 3][n_r][n_theta]
   float2* D;       // [chunk][n_theta]
@@ -1322,6 +1324,8 @@ static HarmLayout harm_layout(void* ws, int n_em, int n_slices, int n_theta, int
   const int n_ord = 2 * m_max + 5;
   H.cs = c.take<float2>(harm_n_phi(m_max));
   H.Zr = c.take<float>((size_t)kHarmMaxNA * n_theta);
+  H.Pm = c.take<float2>((size_t)n_em * (2 * m_max + 1) * n_theta);
+  H.ord = c.take<int>((size_t)(n_em > 0 ? n_em : 1));
   H.Bh = c.take<float2>((size_t)n_em * 3 * n_ord * n_theta);
   H.Jt = c.take<float>((size_t)(m_max + 3) * n_r * n_theta);
   // profiles of a slice chunk up to 1 GB
@@ -1389,13 +1393,16 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
                                              int n_zern, const int* z_offsets, const double* z,
                                              int n_slices, int n_theta, int n_r, int nx,
                                              int ny, double dx, double dy, int m_max,
-                                             float* intensity, void* workspace,
-                                             size_t ws_bytes, void* stream) {
+                                             double tail_tol, float* intensity,
+                                             void* workspace, size_t ws_bytes,
+                                             void* stream) {
   g_err[0] = 0;
   int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
                             n_theta, n_r, nx, ny, dx, dy, PSF_PREC_FP32);
   if (r) return r;
   if ((r = check_harm_args(m_max))) return r;
+  if (!(tail_tol >= 0.0 && tail_tol < 1.0))
+    return fail(PSF_ERR_ARG, "tail_tol %g outside [0, 1)", tail_tol);
   if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   HarmLayout H = harm_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny, m_max);
@@ -1428,6 +1435,7 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
   hp.r_max = bp.r_max;
   hp.dx = dx;
   hp.dy = dy;
+  hp.tail_tol = tail_tol;
   // host tables: m != 0 Zernike radial values at the nodes, azimuth phasors
   const double s_max = base->NA / base->n_i;
   std::vector<double> gx, gw;
@@ -1477,7 +1485,8 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
   if ((r = cuda_check("harmonic tables"))) return r;
   {
     TimingScope ts(kTimeSetup, s);
-    launch_harm_pupil(hp, R.tt, H.b.et, n_zern > 0 ? zernike : nullptr, H.Zr, H.cs, H.Bh, s);
+    launch_harm_pupil(hp, R.tt, H.b.et, n_zern > 0 ? zernike : nullptr, H.Zr, H.cs, H.Pm,
+                      H.ord, H.Bh, s);
   }
   {
     TimingScope ts(kTimeSetup, s);
@@ -1487,12 +1496,13 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
     const int ns = n_slices - s0 < H.chunk ? n_slices - s0 : H.chunk;
     {
       TimingScope ts(kTimeBesselRadial, s);
-      launch_harm_profiles(hp, R.tt, H.Jt, H.Bh, H.b.slice_em, H.b.et.valid, H.b.zz, s0,
-                           ns, H.D, H.prof, s);
+      launch_harm_profiles(hp, R.tt, H.Jt, H.Bh, H.b.slice_em, H.b.et.valid, H.ord,
+                           H.b.zz, s0, ns, H.D, H.prof, s);
     }
     {
       TimingScope ts(kTimeBesselEpilogue, s);
-      launch_harm_intensity(hp, H.prof, H.b.slice_em, H.b.et.valid, s0, ns, intensity, s);
+      launch_harm_intensity(hp, H.prof, H.b.slice_em, H.b.et.valid, H.ord, s0, ns,
+                            intensity, s);
     }
   }
   return cuda_check("psf_bessel_vectorial_harmonic launch");

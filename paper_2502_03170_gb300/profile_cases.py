@@ -16,7 +16,8 @@ the device), then exits.  Cases:
   32 planes) for ``--batch`` pupils against a seeded target.
 * ``bessel_harmonic`` - ``--emitters`` emitters of the batched workload with
   every Zernike term, by azimuthal harmonics at the tail-bound order
-  (``--mmax`` to set it).
+  (``--mmax`` to set it) with the adaptive per-emitter order
+  (``--tail-tol``, default 1e-7; 0 keeps the bound order).
 """
 import argparse
 
@@ -32,6 +33,7 @@ def main():
     ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward",
                                      "fourier_backward", "bessel_harmonic"])
     ap.add_argument("--mmax", type=int, default=-1)
+    ap.add_argument("--tail-tol", type=float, default=1e-7)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--emitters", type=int, default=256)
     ap.add_argument("--precision", default="fp32")
@@ -71,7 +73,7 @@ def main():
         for _ in range(2):
             I = api.bessel_harmonic(c["optics"], c["depth"], c["zernike"], c["z_offsets"],
                                     c["z"], c["n_theta"], c["n_r"], c["nx"], c["ny"],
-                                    c["dx"], c["dy"], m_max=m)
+                                    c["dx"], c["dy"], m_max=m, tail_tol=args.tail_tol)
         torch.cuda.synchronize()
         assert torch.isfinite(I).all()
     elif args.case == "bessel_backward":

@@ -161,9 +161,14 @@ def test_harmonic_order_and_validation(cpu_lib):
                                                       8, 8, 65) == 0
     d = ctypes.c_void_p(16)
     r = cpu_lib.psf_bessel_vectorial_harmonic(ctypes.byref(o), 4, d, d, 21, d, d, 16, 64,
-                                              64, 8, 8, 0.02, 0.02, -1, d,
+                                              64, 8, 8, 0.02, 0.02, -1, 0.0, d,
                                               ctypes.c_void_p(256), 1 << 30, None)
     assert r == _lib.PSF_ERR_ARG
+    for bad in (-1e-9, 1.0, float("nan")):
+        r = cpu_lib.psf_bessel_vectorial_harmonic(ctypes.byref(o), 4, d, d, 21, d, d, 16, 64,
+                                                  64, 8, 8, 0.02, 0.02, 12, bad, d,
+                                                  ctypes.c_void_p(256), 1 << 30, None)
+        assert r == _lib.PSF_ERR_ARG and b"tail_tol" in cpu_lib.psf_last_error(), bad
 
 
 def test_backward_batch_workspace(cpu_lib):

@@ -101,3 +101,24 @@ def test_pupil_harmonics_are_the_fourier_series():
     for m in range(-12, 13):
         expect = (1j ** (m // 2)) * jv(m // 2, a) if m % 2 == 0 else 0.0 * a
         assert np.allclose(P[m + 12], expect, atol=1e-13), m
+
+
+def test_adaptive_order_keeps_the_error_within_the_tolerance():
+    """The adaptive order from the computed harmonics is far below the bound
+    order, and the field it gives stays within the tolerance of the
+    bound-order field (and of the direct quadrature of Eq. 9)."""
+    o = opt_of(pol=W.CIRCULAR)
+    zc = nonaxial_zernike()
+    m_bound = bh.harmonic_order(zc, tol=1e-7)
+    th, _ = bessel.gl_rule(50, o.theta_max)
+    P = bh.pupil_harmonics(o, th, zc, m_bound)
+    m_eff = bh.adaptive_order(P, m_bound, 1e-7)
+    assert 0 < m_eff < m_bound
+    args = (50, 5, 5, 0.06, 0.06, [0.1, -0.3])
+    ref = bh.field_harmonic_direct(o, *args, zc, m_bound)
+    Eb = np.stack([bh.field_harmonic_direct(o, *args, zc, m_eff)])[0]
+    assert np.max(np.abs(Eb - ref)) <= 1e-6 * np.max(np.abs(ref))
+    # the same through the profile path with the adaptive switch
+    Ia = bh.psf_harmonic(o, 40, 48, 9, 11, 0.04, 0.035, [0.2], zc, m_bound, tail_tol=1e-7)
+    Ib = bh.psf_harmonic(o, 40, 48, 9, 11, 0.04, 0.035, [0.2], zc, m_bound)
+    assert np.max(np.abs(Ia - Ib)) <= 2e-6 * np.max(Ib)
