@@ -189,20 +189,25 @@ __global__ void k_harm_defocus(int n_theta, ThetaTable t, const float2* __restri
 
 // ---------------------------------------------------------------------------
 // Radial contraction, one order per grid z: C[i][(s, c)] = sum_j Jt[|l|][i][j]
-// D[s][j] Bh[e(s)][c][l'][j].  Tile 64 radii x 32 columns, K step 16, 256
-// threads with 4 x 2 complex accumulators.  A tile none of whose columns
-// needs order l (|l| > M_e + 2, or no valid emitter) returns at once: the
-// epilogue reads no profile beyond its emitter's orders.
+// D[s][j] Bh[e(s)][c][l'][j] (real x complex, FP32 FMA).  Tile 128 radii x 64
+// columns, K step 16, double-buffered in shared memory; 256 threads on a
+// 16 x 16 grid, each with 8 radii x 4 columns of complex accumulators (rows
+// 4 tr + {0..3} and 64 + 4 tr + {0..3}, columns 2 tc + {0, 1} and
+// 32 + 2 tc + {0, 1}; one float4 shared load feeds 16 FMAs).  A tile none of
+// whose columns needs order l (|l| > M_e + 2, or no valid emitter) returns
+// at once: the epilogue reads no profile beyond its emitter's orders.
 // ---------------------------------------------------------------------------
-constexpr int HP_BM = 64, HP_BN = 32, HP_BK = 16;
+constexpr int HP_BM = 128, HP_BN = 64, HP_BK = 16;
+constexpr int HP_APAD = HP_BM + 4;   // floats per As row (16 B multiple; 2-way stores)
+constexpr int HP_BPAD = HP_BN + 2;   // float2 per Bs row
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_harm_profiles(HarmParams p, const float* __restrict__ Jt, const float2* __restrict__ Bh,
                 const int* __restrict__ slice_em, const int* __restrict__ valid,
                 const int* __restrict__ ord, const float2* __restrict__ D, int s0, int ns,
                 float2* __restrict__ prof) {
-  __shared__ float As[HP_BK][HP_BM + 1];
-  __shared__ float2 Bs[HP_BK][HP_BN + 1];
+  __shared__ __align__(16) float As[2][HP_BK][HP_APAD];
+  __shared__ __align__(16) float2 Bs[2][HP_BK][HP_BPAD];
   const int li = blockIdx.z, L = p.m_max + 2;
   const int n = li >= L ? li - L : L - li;
   const int i0 = blockIdx.y * HP_BM, c0 = blockIdx.x * HP_BN;
@@ -217,57 +222,83 @@ k_harm_profiles(HarmParams p, const float* __restrict__ Jt, const float2* __rest
   }
   const float* A = Jt + (size_t)n * p.n_r * p.n_theta;
   const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
-  float2 acc[4][2];
+  // global -> register staging: A row tid / 2, k (tid & 1) * 8 + {0..7};
+  // B column tid / 4, k (tid & 3) * 4 + {0..3}
+  const int arow = tid >> 1, ak = (tid & 1) * 8;
+  const int bcol = tid >> 2, bk = (tid & 3) * 4;
+  const float* a_row = i0 + arow < p.n_r ? A + (size_t)(i0 + arow) * p.n_theta : nullptr;
+  const float2* bh_col = nullptr;
+  const float2* d_col = nullptr;
+  if (c0 + bcol < ncol) {
+    const int gc = c0 + bcol, sl = gc / 3, c = gc - 3 * sl;
+    const int e = slice_em[s0 + sl];
+    if (e >= 0 && valid[e]) {
+      bh_col = Bh + (((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta;
+      d_col = D + (size_t)sl * p.n_theta;
+    }
+  }
+  float ra[8];
+  float2 rb[4];
+  auto load = [&](int k0) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < p.n_theta; k0 += HP_BK) {
-    for (int x = tid; x < HP_BM * HP_BK; x += 256) {
-      const int r = x / HP_BK, kk = x - r * HP_BK;
-      const int gi = i0 + r, gk = k0 + kk;
-      As[kk][r] = (gi < p.n_r && gk < p.n_theta) ? A[(size_t)gi * p.n_theta + gk] : 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int gk = k0 + ak + q;
+      ra[q] = (a_row && gk < p.n_theta) ? a_row[gk] : 0.f;
     }
-    for (int x = tid; x < HP_BN * HP_BK; x += 256) {
-      const int col = x / HP_BK, kk = x - col * HP_BK;
-      const int gc = c0 + col, gk = k0 + kk;
-      float2 v = make_float2(0.f, 0.f);
-      if (gc < ncol && gk < p.n_theta) {
-        const int sl = gc / 3, c = gc - 3 * sl;
-        const int e = slice_em[s0 + sl];
-        if (e >= 0 && valid[e])
-          v = cmul(D[(size_t)sl * p.n_theta + gk],
-                   Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + gk]);
-      }
-      Bs[kk][col] = v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gk = k0 + bk + q;
+      rb[q] = (bh_col && gk < p.n_theta) ? cmul(d_col[gk], bh_col[gk]) : make_float2(0.f, 0.f);
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) As[buf][ak + q][arow] = ra[q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Bs[buf][bk + q][bcol] = rb[q];
+  };
+  float2 acc[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[r][u] = make_float2(0.f, 0.f);
+  const int nk = (p.n_theta + HP_BK - 1) / HP_BK;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int t = 0; t < nk; ++t) {
+    const int buf = t & 1;
+    if (t + 1 < nk) load((t + 1) * HP_BK);
 #pragma unroll
     for (int kk = 0; kk < HP_BK; ++kk) {
-      float a[4];
-      float2 b[2];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * tr]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * tr]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][2 * tc]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][32 + 2 * tc]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                           make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = As[kk][tr + 16 * q];
-      b[0] = Bs[kk][tc];
-      b[1] = Bs[kk][tc + 16];
+      for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          acc[q][u].x = fmaf(a[q], b[u].x, acc[q][u].x);
-          acc[q][u].y = fmaf(a[q], b[u].y, acc[q][u].y);
+        for (int u = 0; u < 4; ++u) {
+          acc[r][u].x = fmaf(a[r], b[u].x, acc[r][u].x);
+          acc[r][u].y = fmaf(a[r], b[u].y, acc[r][u].y);
         }
     }
+    if (t + 1 < nk) store(buf ^ 1);
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int gc = c0 + tc + 16 * u;
+  for (int u = 0; u < 4; ++u) {
+    const int gc = c0 + (u < 2 ? 2 * tc + u : 32 + 2 * tc + (u - 2));
     if (gc >= ncol) continue;
     const int sl = gc / 3, c = gc - 3 * sl;
+    float2* dst = prof + (((size_t)sl * 3 + c) * p.n_ord + li) * p.n_r;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gi = i0 + tr + 16 * q;
-      if (gi < p.n_r)
-        prof[(((size_t)sl * 3 + c) * p.n_ord + li) * p.n_r + gi] = acc[q][u];
+    for (int r = 0; r < 8; ++r) {
+      const int gi = i0 + (r < 4 ? 4 * tr + r : 64 + 4 * tr + (r - 4));
+      if (gi < p.n_r) dst[gi] = acc[r][u];
     }
   }
 }
@@ -365,6 +396,240 @@ k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
   out[(size_t)a * p.ny + bm] = i_pm;
 }
 
+// ---------------------------------------------------------------------------
+// Square geometry (nx = ny, dx = dy): each octant pixel (b <= a in the
+// quarter) and its seven images share the radius, so one set of profile
+// reads serves eight pixels.  With
+// T_l = (i e^{i phi})^l at (x, y) the images take
+//   (x, y): T_l            (-x, -y): (-1)^l T_l
+//   (-y, x): i^l T_l       (y, -x): (-i)^l T_l
+//   (-x, y): conj(T_l)     (x, -y): (-1)^l conj(T_l)
+//   (y, x): (-i)^l conj(T_l)   (-y, -x): i^l conj(T_l),
+// so the sums are kept by l mod 4 (S_r of T_l v_l, C_r of conj(T_l) v_l).
+// On the diagonal (a = b) the swapped images are the pixels themselves and
+// are not written again.
+//
+// A block holds 128 octant pixels x 3 channels (one thread per pixel and
+// channel: 16 accumulators, two profile pointers), so that enough warps are
+// resident to cover the profile-read latency; the channels' |E_c|^2 of the
+// eight images meet in shared memory and are summed in channel order.
+// Orders are taken in pairs +n, -n, read through pointers stepped by one
+// profile row per order; T_{+n} = w^n and T_{-n} = conj(w)^n by recurrences
+// outward from n = 0.  (Staging a block's radial run of the profiles in
+// shared memory was measured slower: the ~80-sample runs of the blocks of a
+// 128^2 slice re-read its profiles 3.4 times through L2, where L1 serves
+// the direct reads.)
+// ---------------------------------------------------------------------------
+constexpr int HO_PIX = 128;
+// prefetch distance in orders (256 workload emitters: none 12.0 ms per
+// call, 2 orders 11.2, 4 orders 11.3)
+constexpr int kHarmPrefetch = 2;
+
+struct OctAcc {
+  float2 s[4], c[4];
+};
+
+// sum_r w^r X_r for w = 1, -1, i, -i
+PSF_D float2 oct_sum(const float2* X, int w) {
+  float2 r;
+  if (w == 0) {          // 1
+    r.x = X[0].x + X[1].x + X[2].x + X[3].x;
+    r.y = X[0].y + X[1].y + X[2].y + X[3].y;
+  } else if (w == 1) {   // -1
+    r.x = X[0].x - X[1].x + X[2].x - X[3].x;
+    r.y = X[0].y - X[1].y + X[2].y - X[3].y;
+  } else if (w == 2) {   // i: X0 + i X1 - X2 - i X3
+    r.x = X[0].x - X[1].y - X[2].x + X[3].y;
+    r.y = X[0].y + X[1].x - X[2].y - X[3].x;
+  } else {               // -i: X0 - i X1 - X2 + i X3
+    r.x = X[0].x + X[1].y - X[2].x - X[3].y;
+    r.y = X[0].y - X[1].x - X[2].y + X[3].x;
+  }
+  return r;
+}
+
+PSF_D float norm2(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
+
+// one profile value pair at the thread's radius -> both sums of slot R
+template <int R>
+PSF_D void oct_add(OctAcc& acc, const float2* q, float f, float2 t) {
+  const float2 u = q[0], v0 = q[1];
+  const float2 v = make_float2(fmaf(f, v0.x - u.x, u.x), fmaf(f, v0.y - u.y, u.y));
+  const float2 tv = cmul(t, v);
+  const float2 cv = cmul(make_float2(t.x, -t.y), v);
+  acc.s[R].x += tv.x; acc.s[R].y += tv.y;
+  acc.c[R].x += cv.x; acc.c[R].y += cv.y;
+}
+
+template <int J>
+PSF_D void oct_pair(OctAcc& acc, const float2* pp, const float2* pm, int n, float f,
+                    float2 tp, float2 tn) {
+  oct_add<J>(acc, pp, f, tp);
+  if (n > 0) oct_add<(4 - J) & 3>(acc, pm, f, tn);
+}
+
+// Octant pixel geometry of the square grid: radius sample i0, weight f and
+// direction (cos, sin) of pixel (a, b), b <= a < ceil(n / 2).
+PSF_D OctPix oct_pixel(const HarmParams& p, int a, int b) {
+  const double x = (a - 0.5 * (p.nx - 1)) * p.dx, y = (b - 0.5 * (p.ny - 1)) * p.dy;
+  const double rho = sqrt(x * x + y * y);
+  const double tt = p.dr > 0 ? rho / p.dr : 0.0;   // r_max = 0: all r_i = 0
+  int i0 = (int)floor(tt);
+  i0 = i0 < 0 ? 0 : (i0 > p.n_r - 2 ? p.n_r - 2 : i0);
+  OctPix q;
+  q.a = a;
+  q.b = b;
+  q.i0 = i0;
+  q.f = (float)(tt - i0);
+  q.cp = rho > 0 ? (float)(x / rho) : 1.f;
+  q.sp = rho > 0 ? (float)(y / rho) : 0.f;
+  q.pad[0] = q.pad[1] = 0;
+  return q;
+}
+
+PSF_D void oct_index(int idx, int& a, int& b) {
+  // idx -> (a, b), b <= a: idx = a (a + 1) / 2 + b
+  a = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+  while (a * (a + 1) / 2 > idx) --a;
+  while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+  b = idx - a * (a + 1) / 2;
+}
+
+__global__ void k_oct_count(HarmParams p, int npx, int* __restrict__ cnt) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npx) return;
+  int a, b;
+  oct_index(idx, a, b);
+  atomicAdd(&cnt[oct_pixel(p, a, b).i0], 1);
+}
+
+// exclusive prefix sum of cnt[0 .. n) in place (one block of 1024 threads,
+// n <= 4096: four consecutive buckets per thread)
+__global__ void __launch_bounds__(1024) k_oct_scan(int* __restrict__ cnt, int n) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  int v[4], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = 4 * t + k;
+    v[k] = i < n ? cnt[i] : 0;
+    sum += v[k];
+  }
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int add = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  int run = part[t] - sum;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = 4 * t + k;
+    if (i < n) cnt[i] = run;
+    run += v[k];
+  }
+}
+
+__global__ void k_oct_fill(HarmParams p, int npx, int* __restrict__ cursor,
+                           OctPix* __restrict__ tab) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npx) return;
+  int a, b;
+  oct_index(idx, a, b);
+  const OctPix q = oct_pixel(p, a, b);
+  tab[atomicAdd(&cursor[q.i0], 1)] = q;
+}
+
+__global__ void __launch_bounds__(3 * HO_PIX)
+k_harm_intensity_oct(HarmParams p, const float2* __restrict__ prof,
+                     const int* __restrict__ slice_em, const int* __restrict__ valid,
+                     const int* __restrict__ ord, const OctPix* __restrict__ tab, int s0,
+                     float* __restrict__ I) {
+  __shared__ float part[3][8][HO_PIX];
+  const int sl = blockIdx.y, s = s0 + sl;
+  const int e = slice_em[s];
+  if (e < 0 || !valid[e]) return;   // uniform over the block
+  const int ch = threadIdx.x / HO_PIX, t = threadIdx.x - ch * HO_PIX;
+  const int h = (p.nx + 1) / 2;
+  const int idx = blockIdx.x * HO_PIX + t;
+  const bool act = idx < h * (h + 1) / 2;
+  int a = 0, b = 0;
+  if (act) {
+    const OctPix q = tab[idx];   // pixels in the order of their radius sample
+    a = q.a;
+    b = q.b;
+    const int i0 = q.i0;
+    const float f = q.f;
+    const float2 w = make_float2(-q.sp, q.cp);    // i e^{i phi}
+    const float2 wc = make_float2(-q.sp, -q.cp);  // its inverse
+    const int L = p.m_max + 2, Le = ord[e] + 2, n_r = p.n_r;
+    OctAcc acc;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc.s[r] = acc.c[r] = make_float2(0.f, 0.f);
+    const float2* pp =
+        prof + ((size_t)(sl * 3 + ch) * p.n_ord + L) * (size_t)n_r + i0;   // order +n
+    const float2* pm = pp;                                                 // order -n
+    float2 tp = make_float2(1.f, 0.f), tn = make_float2(1.f, 0.f);
+    // after each order, an L2 prefetch of the rows kHarmPrefetch orders ahead
+    // (within |l| <= Le, so inside this channel's rows)
+    int nn = 0;
+    auto step = [&]() {
+      tp = cmul(tp, w);
+      tn = cmul(tn, wc);
+      pp += n_r;
+      pm -= n_r;
+      ++nn;
+      const int ahead = min(kHarmPrefetch, Le - nn);
+      if (ahead > 0) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + (size_t)ahead * n_r));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pm - (size_t)ahead * n_r));
+      }
+    };
+    for (int n0 = 0; n0 <= Le; n0 += 4) {
+      oct_pair<0>(acc, pp, pm, n0, f, tp, tn);
+      step();
+      if (n0 + 1 > Le) break;
+      oct_pair<1>(acc, pp, pm, n0 + 1, f, tp, tn);
+      step();
+      if (n0 + 2 > Le) break;
+      oct_pair<2>(acc, pp, pm, n0 + 2, f, tp, tn);
+      step();
+      if (n0 + 3 > Le) break;
+      oct_pair<3>(acc, pp, pm, n0 + 3, f, tp, tn);
+      step();
+    }
+    // images: 0 (x,y) S.1, 1 (-x,-y) S.-1, 2 (-y,x) S.i, 3 (y,-x) S.-i,
+    //         4 (-x,y) C.1, 5 (x,-y) C.-1, 6 (y,x) C.-i, 7 (-y,-x) C.i
+    part[ch][0][t] = norm2(oct_sum(acc.s, 0));
+    part[ch][1][t] = norm2(oct_sum(acc.s, 1));
+    part[ch][2][t] = norm2(oct_sum(acc.s, 2));
+    part[ch][3][t] = norm2(oct_sum(acc.s, 3));
+    part[ch][4][t] = norm2(oct_sum(acc.c, 0));
+    part[ch][5][t] = norm2(oct_sum(acc.c, 1));
+    part[ch][6][t] = norm2(oct_sum(acc.c, 3));
+    part[ch][7][t] = norm2(oct_sum(acc.c, 2));
+  }
+  __syncthreads();
+  if (ch != 0 || !act) return;
+  float iv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) iv[k] = part[0][k][t] + part[1][k][t] + part[2][k][t];
+  float* out = I + (size_t)s * p.nx * p.ny;
+  const int n = p.nx, am = n - 1 - a, bm = n - 1 - b;
+  out[(size_t)a * n + b] = iv[0];
+  out[(size_t)am * n + bm] = iv[1];
+  out[(size_t)am * n + b] = iv[4];
+  out[(size_t)a * n + bm] = iv[5];
+  if (a != b) {
+    out[(size_t)bm * n + a] = iv[2];
+    out[(size_t)b * n + am] = iv[3];
+    out[(size_t)b * n + a] = iv[6];
+    out[(size_t)bm * n + am] = iv[7];
+  }
+}
+
 }  // namespace
 
 void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const double* zern,
@@ -391,9 +656,32 @@ void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,
   k_harm_profiles<<<grid, 256, 0, s>>>(p, Jt, Bh, slice_em, valid, ord, D, s0, ns, prof);
 }
 
+bool harm_square(const HarmParams& p) { return p.nx == p.ny && p.dx == p.dy; }
+
+int harm_octant_pixels(const HarmParams& p) {
+  const int h = (p.nx + 1) / 2;
+  return harm_square(p) ? h * (h + 1) / 2 : 0;
+}
+
+void launch_harm_octant_table(const HarmParams& p, int* cnt, OctPix* tab, cudaStream_t s) {
+  const int npx = harm_octant_pixels(p);
+  if (npx == 0) return;
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)p.n_r, s);
+  k_oct_count<<<ceil_div(npx, 256), 256, 0, s>>>(p, npx, cnt);
+  k_oct_scan<<<1, 1024, 0, s>>>(cnt, p.n_r);
+  k_oct_fill<<<ceil_div(npx, 256), 256, 0, s>>>(p, npx, cnt, tab);
+}
+
 void launch_harm_intensity(const HarmParams& p, const float2* prof, const int* slice_em,
-                           const int* valid, const int* ord, int s0, int ns, float* I,
-                           cudaStream_t s) {
+                           const int* valid, const int* ord, const OctPix* octab, int s0,
+                           int ns, float* I, cudaStream_t s) {
+  if (harm_square(p)) {
+    const int h = (p.nx + 1) / 2;
+    const dim3 grid(ceil_div(h * (h + 1) / 2, HO_PIX), ns);
+    k_harm_intensity_oct<<<grid, 3 * HO_PIX, 0, s>>>(p, prof, slice_em, valid, ord, octab,
+                                                     s0, I);
+    return;
+  }
   const int quarter = ((p.nx + 1) / 2) * ((p.ny + 1) / 2);
   const dim3 grid(ceil_div(quarter, 256), ns);
   k_harm_intensity<<<grid, 256, 0, s>>>(p, prof, slice_em, valid, ord, s0, I);

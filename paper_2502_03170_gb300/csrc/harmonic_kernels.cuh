@@ -58,12 +58,32 @@ void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,
                           const int* ord, const float2* zz, int s0, int ns, float2* D,
                           float2* prof, cudaStream_t s);
 
+// Octant pixel (a, b), b <= a, of a square grid with its radius sample i0,
+// interpolation weight f and direction (cp, sp) = (x, y) / rho.
+struct OctPix {
+  int a, b, i0;
+  float f, cp, sp;
+  int pad[2];
+};
+
+// Square geometry (nx = ny, dx = dy): the epilogue works on octant pixels
+// and their seven images.
+bool harm_square(const HarmParams& p);
+int harm_octant_pixels(const HarmParams& p);   // 0 unless square
+
+// The octant pixels ordered by radius sample (a counting sort over i0: cnt
+// [n_r] scratch, tab [harm_octant_pixels(p)]), so that the 32 pixels of a
+// warp read nearly the same profile entries; the order within a sample is
+// immaterial (every pixel is computed on its own).  No-op unless square.
+void launch_harm_octant_table(const HarmParams& p, int* cnt, OctPix* tab, cudaStream_t s);
+
 // I[s][a][b] = sum_c |sum_{|l| <= M_e + 2} i^l e^{i l phi}
 //                     lerp(prof[s - s0][c][l'], rho)|^2
-// for the slices [s0, s0 + ns) whose emitter is valid (one thread per
-// quarter pixel and its three mirrors, which share the radius).
+// for the slices [s0, s0 + ns) whose emitter is valid: by octant pixels
+// (octab) on a square grid, else one thread per quarter pixel and its three
+// mirrors, which share the radius.
 void launch_harm_intensity(const HarmParams& p, const float2* prof,
                            const int* slice_em, const int* valid, const int* ord,
-                           int s0, int ns, float* I, cudaStream_t s);
+                           const OctPix* octab, int s0, int ns, float* I, cudaStream_t s);
 
 }  // namespace psf

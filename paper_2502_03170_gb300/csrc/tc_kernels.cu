@@ -1646,36 +1646,52 @@ __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
 }
 
 // F rows (s, re) and (s, im): S_F amp e^{2 pi i (wfr + n_i z_s cos / lambda)};
-// S_F is the power of two that keeps the largest |F0| below 2^14.
-__global__ void k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable et,
-                                    const int* __restrict__ slice_em,
-                                    const float2* __restrict__ zz,
-                                    const unsigned* __restrict__ amp_max, int Kp,
-                                    int bf16, float sB, uint16_t* hi, uint16_t* lo,
-                                    float* out_scale) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)p.n_slices * Kp) return;
+// S_F is the power of two that keeps the largest |F0| below 2^14.  Block
+// (64, 4): one slice per threadIdx.y, each thread four consecutive theta
+// nodes (Kp is a multiple of 8), stored as 8-byte packs of four 16-bit
+// values per row.
+constexpr int FG_TX = 64, FG_TY = 4;
+
+PSF_D uint2 pack4(const uint16_t (&v)[4]) {
+  return make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
+                    (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+}
+
+__global__ void __launch_bounds__(FG_TX * FG_TY)
+k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable et,
+                    const int* __restrict__ slice_em, const float2* __restrict__ zz,
+                    const unsigned* __restrict__ amp_max, int Kp, int bf16, float sB,
+                    uint16_t* hi, uint16_t* lo, float* out_scale) {
   const float am = __uint_as_float(*amp_max);
   const float sF = am > 0.f ? exp2f(floorf(log2f(16384.f / am))) : 1.f;
-  if (idx == 0) *out_scale = 1.f / (sB * sF);
-  const int s = (int)(idx / Kp), j = (int)(idx - (long long)s * Kp);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *out_scale = 1.f / (sB * sF);
+  const int s = blockIdx.x * FG_TY + threadIdx.y;
+  if (s >= p.n_slices) return;
   const int e = slice_em[s];
-  float2 v = make_float2(0.f, 0.f);
-  if (j < p.n_theta && e >= 0) {
-    const size_t ej = (size_t)e * p.n_theta + j;
-    const float2 z = zz[s];
-    const float2 c = cis_cycles(frac_mul_add(f2x{t.kh[j], t.kl[j]}, f2x{z.x, z.y}, et.wfr[ej]));
-    const float a = sF * et.amp[ej];
-    v = make_float2(a * c.x, a * c.y);
+  const float2 z = zz[s];
+  const size_t row0 = (size_t)(2 * s) * Kp;
+  for (int q = threadIdx.x; q < (Kp >> 2); q += FG_TX) {
+    uint16_t hr[4], lr[4], hm[4], lm[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * q + u;
+      float2 v = make_float2(0.f, 0.f);
+      if (j < p.n_theta && e >= 0) {
+        const size_t ej = (size_t)e * p.n_theta + j;
+        const float2 c =
+            cis_cycles(frac_mul_add(f2x{t.kh[j], t.kl[j]}, f2x{z.x, z.y}, et.wfr[ej]));
+        const float a = sF * et.amp[ej];
+        v = make_float2(a * c.x, a * c.y);
+      }
+      split16(v.x, bf16, hr[u], lr[u]);
+      split16(v.y, bf16, hm[u], lm[u]);
+    }
+    const size_t r0 = row0 + 4 * q, r1 = r0 + Kp;
+    *reinterpret_cast<uint2*>(hi + r0) = pack4(hr);
+    *reinterpret_cast<uint2*>(lo + r0) = pack4(lr);
+    *reinterpret_cast<uint2*>(hi + r1) = pack4(hm);
+    *reinterpret_cast<uint2*>(lo + r1) = pack4(lm);
   }
-  const size_t r0 = (size_t)(2 * s) * Kp + j, r1 = r0 + Kp;
-  uint16_t h, l;
-  split16(v.x, bf16, h, l);
-  hi[r0] = h;
-  lo[r0] = l;
-  split16(v.y, bf16, h, l);
-  hi[r1] = h;
-  lo[r1] = l;
 }
 
 // Adjoint operand: A[j][row] = Bt[j][row] (FP32 J_n operand, theta-major)
@@ -1801,8 +1817,8 @@ int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
   const float sB = bessel_sB(max_w);
   {
     TimingScope ts(kTimeSetup, s);
-    const long long n = (long long)p.n_slices * Kp;
-    k_bessel_fgen_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+    const unsigned nb = (unsigned)(p.n_slices > 0 ? ceil_div(p.n_slices, FG_TY) : 1);
+    k_bessel_fgen_split<<<nb, dim3(FG_TX, FG_TY), 0, s>>>(
         p, t, et, slice_em, zz, ops.amp_max, Kp, bf16, sB, ops.F_hi, ops.F_lo,
         ops.out_scale);
   }

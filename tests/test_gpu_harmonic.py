@@ -110,3 +110,23 @@ def test_adaptive_order_orders_and_ragged(lib, tail_tol):
     zern[2] *= 0.05                              # a nearly axisymmetric emitter
     m_max = min(api.harmonic_order(zern, 1e-8), 40)
     check(d, depth, zern, offs, z, (41, 37, 17, 21, 0.04, 0.035), m_max, tail_tol=tail_tol)
+
+
+@pytest.mark.parametrize("n,n_r", [(1, 33), (2, 33), (15, 33), (16, 33), (40, 96),
+                                   (32, 2048)])
+def test_square_geometry_octant_epilogue(lib, n, n_r):
+    """nx = ny and dx = dy take the octant epilogue (one thread per pixel and
+    its seven images): odd sizes have a centre row and the diagonal, n = 1 a
+    single pixel; 40 px spans several blocks; with N_r = 2048 a block's
+    radial run is too long to stage and the profiles are read from global
+    memory.  Against the oracle, and against the quarter-pixel epilogue (dy
+    off by 1e-12 relative)."""
+    d = W.optics_gibson_lanni(0.0)
+    depth, zern, offs, z = batch(4, 23 + n)
+    m_max = api.harmonic_order(zern, 1e-6)
+    geo = (37, n_r, n, n, 0.045, 0.045)
+    I = check(d, depth, zern, offs, z, geo, m_max, tail_tol=1e-7)
+    geo4 = (37, n_r, n, n, 0.045, 0.045 * (1 + 1e-12))
+    I4 = api.bessel_harmonic(d, depth, zern, offs, z, *geo4, m_max=m_max, tail_tol=1e-7)
+    torch.cuda.synchronize()
+    assert max_rel(I, I4.cpu().numpy()) <= 2e-6
