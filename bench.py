@@ -593,8 +593,9 @@ def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
     """The spherical strategy with every Zernike term (azimuthal harmonics,
     no axisymmetric projection) on emitters of the batched workload: voxels/s
     at the tail-bound order for 1e-7 with the adaptive per-emitter order
-    (tail_tol 1e-7) and without it, and at M = 8; error of one emitter
-    against the FP64 harmonic oracle with the same order rule."""
+    (tail_tol 1e-7; radial contraction on the tensor cores and in FP32) and
+    without it, and at M = 8; error of one emitter against the FP64
+    harmonic oracle with the same order rule."""
     import torch
 
     from oracle import bessel_harmonic as bh
@@ -607,11 +608,13 @@ def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
     out = {"n_emitters": n_em, "n_slices": int(c["z_offsets"][-1]),
            "tail_bound_tol": 1e-7}
     m_bound = api.harmonic_order(c["zernike"], 1e-7)
-    for name, m, tt in (("m_bound_adaptive", m_bound, 1e-7), ("m_bound", m_bound, 0.0),
-                        ("m_8", 8, 0.0)):
+    for name, m, tt, prec in (("m_bound_adaptive", m_bound, 1e-7, "fp32"),
+                              ("m_bound", m_bound, 0.0, "fp32"), ("m_8", 8, 0.0, "fp32"),
+                              ("m_bound_adaptive_split_fp16", m_bound, 1e-7, "split_fp16")):
         run = lambda: api.bessel_harmonic(c["optics"], c["depth"], c["zernike"],
                                           c["z_offsets"], c["z"], *geo, m_max=m,
-                                          tail_tol=tt, workspace=ws, stream=stream)
+                                          tail_tol=tt, precision=prec, workspace=ws,
+                                          stream=stream)
         I = run()
         ms = 0.0
         for _ in range(steps):
@@ -627,7 +630,7 @@ def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
                                      c["z_offsets"], c["z"], *geo, m, emitters=[0],
                                      tail_tol=tt)
         Ie = I[e0:e1].cpu().numpy()
-        out[name] = {"m_max": m, "tail_tol": tt, "ms": ms / steps,
+        out[name] = {"m_max": m, "tail_tol": tt, "precision": prec, "ms": ms / steps,
                      "voxels_per_s": I.numel() / (ms / steps * 1e-3),
                      "max_rel_err_vs_oracle_emitter0":
                          float(np.max(np.abs(Ie - Iref)) / np.max(Iref))}
@@ -637,9 +640,12 @@ def bessel_harmonic_variant(flush, stream, n_em=256, steps=3):
                 np.max(np.abs(I_adapt - I_bound)) / np.max(I_bound))
         elif name == "m_bound_adaptive":
             I_adapt = Ie
-        else:
+        elif name == "m_8":
             out[name]["truncation_vs_m_bound_emitter0"] = float(
                 np.max(np.abs(Ie - I_bound)) / np.max(I_bound))
+        else:
+            out[name]["vs_fp32_contraction_emitter0"] = float(
+                np.max(np.abs(Ie - I_adapt)) / np.max(I_adapt))
     return out
 
 

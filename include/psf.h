@@ -274,7 +274,7 @@ int psf_bessel_vectorial(const psf_optics* base, int n_emitters,
  * (g_n of Eq. 11 and its Fresnel / scalar forms; Gauss-Legendre in theta;
  * I_{c,l} on the radial grid r_i = i r_max / (N_r - 1), linearly
  * interpolated).  With m = 0 terms only this is Eq. 10-11.  Cost grows with
- * the 2M + 5 orders; FP32 arithmetic.                                      */
+ * the 2M + 5 orders.                                                         */
 
 /* Truncation order: the largest over the emitters of the smallest M = K d
  * with alpha^{K+1} / (K+1)! e^alpha <= tol, alpha = sum |c_j| N_j and d =
@@ -286,7 +286,7 @@ int psf_bessel_harmonic_order(const double* zernike, int n_em, int n_zern, doubl
 /* Workspace for psf_bessel_vectorial_harmonic() (0 on invalid arguments). */
 size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_emitters,
                                           int n_slices, int n_theta, int n_r,
-                                          int nx, int ny, int m_max);
+                                          int nx, int ny, int m_max, int precision);
 
 /* Batched PSFs with every Zernike term (any m) by the azimuthal harmonics
  * |m| <= m_max (0 <= m_max <= 64).  Arguments as psf_bessel_vectorial()
@@ -301,14 +301,19 @@ size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_emitters
  * dropped tail is about tail_tol; the tail bound of
  * psf_bessel_harmonic_order() is pessimistic and the adaptive order
  * typically halves the orders); 0 keeps m_max for every emitter.
- * PSF_ERR_ARG for tail_tol outside [0, 1). */
+ * PSF_ERR_ARG for tail_tol outside [0, 1).
+ * precision: PSF_PREC_FP32 (the per-order radial contraction in FP32 FMA)
+ * or PSF_PREC_SPLIT_FP16 (the contraction on the tensor cores: w_j J_|l|
+ * and D Bh split into FP16 hi + lo, three products, FP32 accumulation);
+ * other modes give PSF_ERR_PRECISION (BF16 parts keep too few bits for
+ * the 1e-5 bound here). */
 int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_emitters,
                                   const double* depth, const double* zernike,
                                   int n_zern, const int* z_offsets, const double* z,
                                   int n_slices, int n_theta, int n_r, int nx, int ny,
                                   double dx, double dy, int m_max, double tail_tol,
-                                  float* intensity, void* workspace, size_t ws_bytes,
-                                  void* stream);
+                                  int precision, float* intensity, void* workspace,
+                                  size_t ws_bytes, void* stream);
 
 /* Workspace for psf_bessel_vectorial_backward() (0 if the arguments are
  * invalid; the backward takes nx, ny <= 4096). */

@@ -97,9 +97,9 @@ PROTOTYPES = {
     "psf_bessel_backward_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I,
                                                 _I]),
     "psf_bessel_harmonic_order": (_I, [_P, _I, _I, _D]),
-    "psf_bessel_harmonic_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I, _I]),
+    "psf_bessel_harmonic_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I, _I, _I]),
     "psf_bessel_vectorial_harmonic": (_I, [_OPT, _I, _P, _P, _I, _P, _P, _I, _I, _I,
-                                           _I, _I, _D, _D, _I, _D, _P, _P, _S, _P]),
+                                           _I, _I, _D, _D, _I, _D, _I, _P, _P, _S, _P]),
     "psf_bessel_vectorial_backward": (_I, [_OPT, _I, _P, _P, _I, _P, _P, _P,
                                            _I, _I, _I, _I, _I, _D, _D, _I, _P,
                                            _P, _P, _P, _P, _P, _P, _S, _P]),

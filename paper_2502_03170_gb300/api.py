@@ -152,14 +152,15 @@ def harmonic_order(zernike, tol=1e-7):
 
 
 def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
-                    m_max=None, tol=1e-7, tail_tol=None, workspace=None, stream=None,
-                    out=None):
+                    m_max=None, tol=1e-7, tail_tol=None, precision="fp32", workspace=None,
+                    stream=None, out=None):
     """Batched vectorial PSFs by the spherical strategy for pupils without
     axial symmetry (azimuthal harmonics |m| <= m_max of the pupil; m != 0
     Zernike terms enter exactly).  m_max defaults to harmonic_order(zernike,
     tol); each emitter then keeps the harmonics up to its adaptive order for
-    tail_tol (default tol; 0 keeps m_max for all).  Same array conventions
-    as bessel(); returns [n_slices, nx, ny]."""
+    tail_tol (default tol; 0 keeps m_max for all).  precision "fp32" or
+    "split_fp16" (the radial contraction on the tensor cores).  Same array
+    conventions as bessel(); returns [n_slices, nx, ny]."""
     lib = _lib.load()
     if m_max is None:
         m_max = 0 if zernike is None else harmonic_order(zernike, tol)
@@ -168,8 +169,9 @@ def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, 
     a = _BesselArgs(optics, depth, zernike, z_offsets, z, False, None)
     o, dev = a.o, a.dev
     ws = workspace or Workspace(dev)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     need = lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), a.n_em, a.n_slices,
-                                                  n_theta, n_r, nx, ny, int(m_max))
+                                                  n_theta, n_r, nx, ny, int(m_max), prec)
     if need == 0:
         raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
     buf = ws.get(need)
@@ -178,7 +180,7 @@ def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, 
     check(lib, lib.psf_bessel_vectorial_harmonic(
         ctypes.byref(o), a.n_em, _ptr(a.depth), _ptr(a.zern), a.n_zern, _ptr(a.offs),
         _ptr(a.z), a.n_slices, n_theta, n_r, nx, ny, float(dx), float(dy), int(m_max),
-        float(tail_tol), _ptr(I), _ptr(buf), buf.numel(), _stream(stream)))
+        float(tail_tol), prec, _ptr(I), _ptr(buf), buf.numel(), _stream(stream)))
     return I
 
 

@@ -2,6 +2,7 @@
 // J_n table, batched radial contraction per order and the Cartesian
 // epilogue (FP32 arithmetic, FP64 tables).
 #include "harmonic_kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace psf {
 
@@ -103,7 +104,7 @@ k_harm_order(HarmParams p, const float2* __restrict__ Pm, int* __restrict__ ord)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 k_harm_mix(HarmParams p, ThetaTable t, EmitterTable et, const float2* __restrict__ Pm,
-           const int* __restrict__ ord, float2* __restrict__ Bh) {
+           const int* __restrict__ ord, float2* __restrict__ Bh, unsigned* bh_max) {
   const int e = blockIdx.x, j = blockIdx.y;
   const int nP = 2 * p.m_max + 1, Me = ord[e];
   const bool ok = et.valid[e] != 0;
@@ -126,8 +127,9 @@ k_harm_mix(HarmParams p, ThetaTable t, EmitterTable et, const float2* __restrict
       acc.y += v.y;
     }
     if (l < 0 && ((-l) & 1)) acc = make_float2(-acc.x, -acc.y);   // J_{-n} = (-1)^n J_n
-    Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j] =
-        ok ? acc : make_float2(0.f, 0.f);
+    if (!ok) acc = make_float2(0.f, 0.f);
+    Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j] = acc;
+    if (bh_max) atomicMax(bh_max, __float_as_uint(fmaxf(fabsf(acc.x), fabsf(acc.y))));
   }
 }
 
@@ -164,8 +166,11 @@ PSF_D void bessel_j_all(double x, int nmax, double* out) {
   for (int n = 0; n <= nmax; ++n) out[n] *= norm;
 }
 
-// one thread per (r_i, theta_j): every order at once
-__global__ void k_harm_jtab(HarmParams p, ThetaTable t, float* __restrict__ Jt) {
+// one thread per (r_i, theta_j): every order at once; FP32 table Jt and/or
+// the split operand S_A w_j J_n in hi / lo planes [n][n_r_pad][kp]
+__global__ void k_harm_jtab(HarmParams p, ThetaTable t, float* __restrict__ Jt,
+                            uint16_t* __restrict__ a_hi, uint16_t* __restrict__ a_lo, int kp,
+                            int n_r_pad, double sA, int bf16) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)p.n_r * p.n_theta) return;
   const int i = (int)(idx / p.n_theta), j = (int)(idx - (long long)i * p.n_theta);
@@ -174,7 +179,96 @@ __global__ void k_harm_jtab(HarmParams p, ThetaTable t, float* __restrict__ Jt) 
   bessel_j_all(p.k * (i * p.dr) * t.sin_t[j], nmax, J);
   const double w = t.w[j];
   const size_t plane = (size_t)p.n_r * p.n_theta;
-  for (int n = 0; n <= nmax; ++n) Jt[n * plane + idx] = (float)(w * J[n]);
+  if (Jt)
+    for (int n = 0; n <= nmax; ++n) Jt[n * plane + idx] = (float)(w * J[n]);
+  if (a_hi)
+    for (int n = 0; n <= nmax; ++n) {
+      uint16_t h, l;
+      tc::split16d(sA * w * J[n], bf16, h, l);
+      const size_t o = ((size_t)n * n_r_pad + i) * kp + j;
+      a_hi[o] = h;
+      a_lo[o] = l;
+    }
+}
+
+// Split B operand of the tensor-core contraction for the slices [s0, s0+ns):
+// rows (l', 3 sl + c, re/im), 2 * 3 ns rows per order, value
+// S_F D[sl][j] Bh[e][c][l'][j] split hi + lo; S_F is the power of two that
+// keeps max |Bh| below 2^14.  Only (order, slice) pairs the epilogue reads
+// (valid emitter, |l| <= M_e + 2) are written.  Block (64, 4): one
+// (order, slice) pair per threadIdx.y, four theta nodes per thread.
+constexpr int HB_TX = 64, HB_TY = 4;
+
+PSF_D uint2 pack4h(const uint16_t (&v)[4]) {
+  return make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
+                    (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+}
+
+__global__ void __launch_bounds__(HB_TX * HB_TY)
+k_harm_bgen(HarmParams p, const float2* __restrict__ Bh, const float2* __restrict__ D,
+            const int* __restrict__ slice_em, const int* __restrict__ valid,
+            const int* __restrict__ ord, int s0, int ns, int kp, int bf16,
+            const unsigned* __restrict__ bh_max, float sA, uint16_t* __restrict__ b_hi,
+            uint16_t* __restrict__ b_lo, float* __restrict__ out_scale) {
+  const float bm = __uint_as_float(*bh_max);
+  const float sF = bm > 0.f ? exp2f(floorf(log2f(16384.f / bm))) : 1.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *out_scale = 1.f / (sA * sF);
+  const long long pair = (long long)blockIdx.x * HB_TY + threadIdx.y;   // li * ns + sl
+  if (pair >= (long long)p.n_ord * ns) return;
+  const int li = (int)(pair / ns), sl = (int)(pair - (long long)li * ns);
+  const int e = slice_em[s0 + sl];
+  const int L = p.m_max + 2, n = li >= L ? li - L : L - li;
+  if (e < 0 || !valid[e] || n > ord[e] + 2) return;
+  const float2* d = D + (size_t)sl * p.n_theta;
+  for (int q = threadIdx.x; q < (kp >> 2); q += HB_TX) {
+    uint16_t h[3][2][4], l[3][2][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * q + u;
+      const bool in = j < p.n_theta;
+      const float2 dj = in ? d[j] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 v = make_float2(0.f, 0.f);
+        if (in) {
+          const float2 b = Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j];
+          v = cmul(dj, b);
+        }
+        tc::split16(sF * v.x, bf16, h[c][0][u], l[c][0][u]);
+        tc::split16(sF * v.y, bf16, h[c][1][u], l[c][1][u]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ri = 0; ri < 2; ++ri) {
+        const size_t row = (size_t)li * 6 * ns + (size_t)(3 * sl + c) * 2 + ri;
+        *reinterpret_cast<uint2*>(b_hi + row * kp + 4 * q) = pack4h(h[c][ri]);
+        *reinterpret_cast<uint2*>(b_lo + row * kp + 4 * q) = pack4h(l[c][ri]);
+      }
+  }
+}
+
+// need[li][nt] = some column of B tile nt (slices nt * spt .. + spt - 1 of
+// the chunk) has a valid emitter with |l| <= M_e + 2
+__global__ void k_harm_tile_need(HarmParams p, const int* __restrict__ slice_em,
+                                 const int* __restrict__ valid, const int* __restrict__ ord,
+                                 int s0, int ns, int cols_per_tile, int n_tiles,
+                                 unsigned char* __restrict__ need) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)p.n_ord * n_tiles) return;
+  const int li = (int)(idx / n_tiles), nt = (int)(idx - (long long)li * n_tiles);
+  const int L = p.m_max + 2, n = li >= L ? li - L : L - li;
+  const int c0 = nt * cols_per_tile, c1 = min(3 * ns, c0 + cols_per_tile);
+  unsigned char f = 0;
+  for (int sl = c0 / 3; sl * 3 < c1; ++sl) {
+    const int e = slice_em[s0 + sl];
+    if (e >= 0 && valid[e] && n <= ord[e] + 2) {
+      f = 1;
+      break;
+    }
+  }
+  need[idx] = f;
 }
 
 // D[s][j] = e^{i k z_s cos theta_j} for the slices of a chunk
@@ -634,16 +728,42 @@ k_harm_intensity_oct(HarmParams p, const float2* __restrict__ prof,
 
 void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const double* zern,
                        const float* Zr, const float2* cs, float2* Pm, int* ord, float2* Bh,
-                       cudaStream_t s) {
+                       unsigned* bh_max, cudaStream_t s) {
   const size_t smem = sizeof(float2) * (size_t)p.n_phi;
   k_harm_pupil<<<dim3(p.n_em, p.n_theta), 128, smem, s>>>(p, t, e, zern, Zr, cs, Pm);
   k_harm_order<<<p.n_em, 256, 0, s>>>(p, Pm, ord);
-  k_harm_mix<<<dim3(p.n_em, p.n_theta), 128, 0, s>>>(p, t, e, Pm, ord, Bh);
+  if (bh_max) cudaMemsetAsync(bh_max, 0, sizeof(unsigned), s);
+  k_harm_mix<<<dim3(p.n_em, p.n_theta), 128, 0, s>>>(p, t, e, Pm, ord, Bh, bh_max);
 }
 
-void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t s) {
+void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, const TcHarm* tc_ops,
+                      double sA, int bf16, cudaStream_t s) {
   const long long total = (long long)p.n_r * p.n_theta;
-  k_harm_jtab<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(p, t, Jt);
+  uint16_t* a_hi = tc_ops ? tc_ops->A_hi : nullptr;
+  uint16_t* a_lo = tc_ops ? tc_ops->A_lo : nullptr;
+  if (tc_ops) {
+    cudaMemsetAsync(a_hi, 0, tc_ops->a_bytes, s);
+    cudaMemsetAsync(a_lo, 0, tc_ops->a_bytes, s);
+  }
+  k_harm_jtab<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(
+      p, t, Jt, a_hi, a_lo, tc_ops ? tc_ops->kp : 0, tc_ops ? tc_ops->n_r_pad : 0, sA, bf16);
+}
+
+void launch_harm_operands(const HarmParams& p, ThetaTable t, const float2* Bh,
+                          const int* slice_em, const int* valid, const int* ord,
+                          const float2* zz, int s0, int ns, float2* D, const TcHarm& ops,
+                          float sA, int bf16, cudaStream_t s) {
+  const long long nd = (long long)ns * p.n_theta;
+  k_harm_defocus<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(p.n_theta, t, zz, s0, ns, D);
+  const long long pairs = (long long)p.n_ord * ns;
+  k_harm_bgen<<<(unsigned)((pairs + HB_TY - 1) / HB_TY), dim3(HB_TX, HB_TY), 0, s>>>(
+      p, Bh, D, slice_em, valid, ord, s0, ns, ops.kp, bf16, ops.bh_max, sA, ops.B_hi,
+      ops.B_lo, ops.out_scale);
+  const int cpt = tc_harm_cols_per_tile();
+  const int n_tiles = ceil_div(3 * ns, cpt);
+  const long long nf = (long long)p.n_ord * n_tiles;
+  k_harm_tile_need<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(p, slice_em, valid, ord, s0, ns,
+                                                                 cpt, n_tiles, ops.need);
 }
 
 void launch_harm_profiles(const HarmParams& p, ThetaTable t, const float* Jt,

@@ -16,6 +16,7 @@
 
 #include "bessel_kernels.cuh"
 #include "psf_common.cuh"
+#include "tc_kernels.cuh"
 
 namespace psf {
 
@@ -42,12 +43,24 @@ struct HarmParams {
 // channel/order mixtures Bh[e][c][l'][theta] from the harmonics |m| <= M_e.
 void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e,
                        const double* zern, const float* Zr, const float2* cs,
-                       float2* Pm, int* ord, float2* Bh, cudaStream_t s);
+                       float2* Pm, int* ord, float2* Bh, unsigned* bh_max, cudaStream_t s);
 
 // Jt[n][i][j] = w_j J_n(k r_i sin theta_j), n = 0 .. m_max + 2 (FP64 by
 // Miller's backward recurrence, all orders of one argument at once; stored
-// FP32).
-void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, cudaStream_t s);
+// FP32 when Jt is given, and as the split operand S_A w_j J_n of the
+// tensor-core contraction when tc_ops is given).  bh_max of
+// launch_harm_pupil (device max of |Re Bh|, |Im Bh|, or null) feeds the
+// B operand's scale.
+void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, const TcHarm* tc_ops,
+                      double sA, int bf16, cudaStream_t s);
+
+// Split-precision path, per slice chunk: the defocus phasors D, the B
+// operand of the orders each slice needs, and the tile flags of the
+// contraction (tc_harm_contract runs it).
+void launch_harm_operands(const HarmParams& p, ThetaTable t, const float2* Bh,
+                          const int* slice_em, const int* valid, const int* ord,
+                          const float2* zz, int s0, int ns, float2* D, const TcHarm& ops,
+                          float sA, int bf16, cudaStream_t s);
 
 // Profiles of the slices [s0, s0 + ns) (D: scratch [ns][n_theta] for the
 // defocus phasors e^{i k z_s cos theta_j}):

@@ -1312,12 +1312,19 @@ struct HarmLayout {
   float2* prof;    // [chunk][3][n_ord][n_r]
   int* octcnt;     // [n_r] counting-sort scratch (square grids)
   OctPix* octab;   // [octant pixels] ordered by radius sample (square grids)
+  TcHarm tc;       // split operands of the tensor-core contraction
   int chunk;
   size_t bytes;
 };
 
+// The split form takes FP16 parts only: hi + lo in BF16 keeps 16 mantissa
+// bits, and on the parity cases the harmonic stacks then missed the 1e-5
+// bound (2.9e-5).
+static bool harm_split(int precision) { return precision == PSF_PREC_SPLIT_FP16; }
+
 static HarmLayout harm_layout(void* ws, int n_em, int n_slices, int n_theta, int n_r,
-                              int nx, int ny, int m_max) {
+                              int nx, int ny, int m_max, int precision) {
+  const bool split = harm_split(precision);
   HarmLayout H;
   memset(&H, 0, sizeof(H));
   H.b = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, false, PSF_PREC_FP32);
@@ -1329,9 +1336,10 @@ static HarmLayout harm_layout(void* ws, int n_em, int n_slices, int n_theta, int
   H.Pm = c.take<float2>((size_t)n_em * (2 * m_max + 1) * n_theta);
   H.ord = c.take<int>((size_t)(n_em > 0 ? n_em : 1));
   H.Bh = c.take<float2>((size_t)n_em * 3 * n_ord * n_theta);
-  H.Jt = c.take<float>((size_t)(m_max + 3) * n_r * n_theta);
-  // profiles of a slice chunk up to 1 GB
-  const double per_slice = 8.0 * (3.0 * n_ord * n_r + n_theta);
+  H.Jt = split ? nullptr : c.take<float>((size_t)(m_max + 3) * n_r * n_theta);
+  // profiles (and the split B operand) of a slice chunk up to 1 GB
+  double per_slice = 8.0 * (3.0 * n_ord * n_r + n_theta);
+  if (split) per_slice += 4.0 * 6.0 * n_ord * tc_bessel_kp(n_theta);
   // (measured on the 256-emitter workload: 1 GB 12.0 ms, 256 MB 12.0, 96 MB
   // 12.9, 48 MB 14.5: the epilogue does not gain from profiles left in L2)
   long long chunk = (long long)(1024.0 * 1048576.0 / per_slice);
@@ -1345,6 +1353,11 @@ static HarmLayout harm_layout(void* ws, int n_em, int n_slices, int n_theta, int
   const long long npx = nx == ny ? h * (h + 1) / 2 : 0;   // used when also dx = dy
   H.octcnt = c.take<int>((size_t)n_r);
   H.octab = c.take<OctPix>((size_t)(npx > 0 ? npx : 1));
+  if (split) {
+    size_t off = c.off;
+    tc_harm_carve((char*)ws, &off, n_theta, n_r, m_max, (int)chunk, &H.tc);
+    c.off = off;
+  }
   H.bytes = align_up(c.off, 256);
   return H;
 }
@@ -1382,18 +1395,22 @@ extern "C" int psf_bessel_harmonic_order(const double* zernike, int n_em, int n_
   return best;
 }
 
-static int check_harm_args(int m_max) {
+static int check_harm_args(int m_max, int precision) {
   if (m_max < 0 || m_max > kHarmMaxM)
     return fail(PSF_ERR_ARG, "m_max %d outside [0, %d]", m_max, kHarmMaxM);
+  if (precision != PSF_PREC_FP32 && !harm_split(precision))
+    return fail(PSF_ERR_PRECISION, "harmonic path: precision %d is not FP32 or split FP16",
+                precision);
   return PSF_OK;
 }
 
 extern "C" size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_em,
                                                      int n_slices, int n_theta, int n_r,
-                                                     int nx, int ny, int m_max) {
+                                                     int nx, int ny, int m_max,
+                                                     int precision) {
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, PSF_PREC_FP32)) return 0;
-  if (check_harm_args(m_max)) return 0;
-  return harm_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, m_max).bytes;
+  if (check_harm_args(m_max, precision)) return 0;
+  return harm_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, m_max, precision).bytes;
 }
 
 extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
@@ -1401,19 +1418,21 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
                                              int n_zern, const int* z_offsets, const double* z,
                                              int n_slices, int n_theta, int n_r, int nx,
                                              int ny, double dx, double dy, int m_max,
-                                             double tail_tol, float* intensity,
-                                             void* workspace, size_t ws_bytes,
-                                             void* stream) {
+                                             double tail_tol, int precision,
+                                             float* intensity, void* workspace,
+                                             size_t ws_bytes, void* stream) {
   g_err[0] = 0;
   int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
                             n_theta, n_r, nx, ny, dx, dy, PSF_PREC_FP32);
   if (r) return r;
-  if ((r = check_harm_args(m_max))) return r;
+  if ((r = check_harm_args(m_max, precision))) return r;
   if (!(tail_tol >= 0.0 && tail_tol < 1.0))
     return fail(PSF_ERR_ARG, "tail_tol %g outside [0, 1)", tail_tol);
   if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
-  HarmLayout H = harm_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny, m_max);
+  HarmLayout H = harm_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny, m_max, precision);
+  const bool split = harm_split(precision);
+  const int bf16 = 0;
   if (ws_bytes < H.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, H.bytes);
   if ((r = resolve_output((void**)&intensity, "intensity"))) return r;
@@ -1491,19 +1510,30 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
   upload_async(H.Zr, zr.data(), zr.size() * sizeof(float), s);
   upload_async(H.cs, cs.data(), cs.size() * sizeof(float2), s);
   if ((r = cuda_check("harmonic tables"))) return r;
+  const float sA = split ? tc_harm_scale_a(R.max_w) : 1.f;
   {
     TimingScope ts(kTimeSetup, s);
     launch_harm_pupil(hp, R.tt, H.b.et, n_zern > 0 ? zernike : nullptr, H.Zr, H.cs, H.Pm,
-                      H.ord, H.Bh, s);
+                      H.ord, H.Bh, split ? H.tc.bh_max : nullptr, s);
   }
   {
     TimingScope ts(kTimeSetup, s);
-    launch_harm_jtab(hp, R.tt, H.Jt, s);
+    launch_harm_jtab(hp, R.tt, H.Jt, split ? &H.tc : nullptr, sA, bf16, s);
     launch_harm_octant_table(hp, H.octcnt, H.octab, s);
   }
   for (int s0 = 0; s0 < n_slices; s0 += H.chunk) {
     const int ns = n_slices - s0 < H.chunk ? n_slices - s0 : H.chunk;
-    {
+    if (split) {
+      {
+        TimingScope ts(kTimeSetup, s);
+        launch_harm_operands(hp, R.tt, H.Bh, H.b.slice_em, H.b.et.valid, H.ord, H.b.zz, s0,
+                             ns, H.D, H.tc, sA, bf16, s);
+      }
+      TimingScope ts(kTimeBesselRadial, s);
+      if ((r = tc_harm_contract(H.tc, n_theta, n_r, m_max, 3 * ns, precision, H.prof,
+                                (int*)workspace, s)))
+        return fail(r, "harmonic tensor-core contraction launch failed");
+    } else {
       TimingScope ts(kTimeBesselRadial, s);
       launch_harm_profiles(hp, R.tt, H.Jt, H.Bh, H.b.slice_em, H.b.et.valid, H.ord,
                            H.b.zz, s0, ns, H.D, H.prof, s);

@@ -87,7 +87,19 @@ struct Params {
   uint16_t* R_lo;
   // mode 4 (adjoint stage 2): Gh stored as FP32 gWz[plane][c][re/im][p][q]
   float* gWz;
+  // mode 5 (harmonic radial contraction, one plane per order l' = l + hL):
+  // A rows (|l|, i) with n_r_pad rows per order, B rows (l', column, re/im)
+  // with b_rows_per_plane rows per order; D columns = (column, re/im);
+  // prof[column][l'][i] complex (rows_total = N_r, n_slices = columns);
+  // tiles with need[plane * n_tiles + nt] == 0 are skipped by every role
+  const unsigned char* need;
+  int n_ord, hL, n_r_pad, b_rows_per_plane;
 };
+
+// Mode 5 tiles none of whose columns needs the tile's order.
+PSF_D bool tile_skipped(const Params& p, int plane, int nt) {
+  return p.mode == 5 && !p.need[(size_t)plane * p.n_tiles + nt];
+}
 
 // Tile index -> (plane, m-tile, n-tile).
 PSF_D void decode_tile(const Params& p, int t, int& plane, int& mt, int& nt) {
@@ -149,6 +161,7 @@ PSF_D void store_rows_t4(uint16_t* base, const uint32_t (&w)[16], int jj, int k4
 //   mode 2  Bessel radial profiles
 //   mode 3  adjoint source R = g E with the loss partials
 //   mode 4  Gh stored in FP32
+//   mode 5  harmonic radial profiles of one order
 // --------------------------------------------------------------------------
 PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int nt,
                          int quad, int lane) {
@@ -168,6 +181,24 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
               const int s = nt * (BN / 2) + h * 16 + k;
               if (s < p.n_slices)
                 p.prof[(size_t)s * p.rows_total + grow] =
+                    make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
+            }
+          }
+        }
+      } else if (p.mode == 5) {
+        // harmonic: prof[col][plane][i] = scale * (D[i][2k], D[i][2k+1]),
+        // col = nt * 96 + k, i = mt * 128 + row
+        const int gi = mt * BM + row;
+        const float sc = *p.scale_ptr;
+        for (int h = 0; h < BN / 32; ++h) {
+          uint32_t r[32];
+          tmem_ld32(tbase + (uint32_t)(h * 32), r);
+          if (gi < p.rows_total) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int col = nt * (BN / 2) + h * 16 + k;
+              if (col < p.n_slices)
+                p.prof[((size_t)col * p.n_ord + plane) * p.rows_total + gi] =
                     make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
             }
           }
@@ -420,6 +451,10 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
       int plane, mt, nt;
       decode_tile(p, t, plane, mt, nt);
+      if (tile_skipped(p, plane, nt)) continue;
+      // mode 5: the order's A plane and B rows
+      const int arow = p.mode == 5 ? abs(plane - p.hL) * p.n_r_pad + mt * BM : mt * BM;
+      const int brow = p.mode == 5 ? plane * p.b_rows_per_plane + nt * BN : nt * BN;
       for (int kc = 0; kc < p.k_chunks; ++kc) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.status)) {
           ok = false;
@@ -427,11 +462,11 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
         }
         const uint32_t base = smem_u32(smem + stage * STAGE_BYTES);
         mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
-        tma_load_2d(base, &mapA_hi, kc * BK, mt * BM, full_bar(stage));
-        tma_load_2d(base + A_BYTES, &mapA_lo, kc * BK, mt * BM, full_bar(stage));
-        if (p.mode == 2) {
-          tma_load_2d(base + 2 * A_BYTES, &mapB_hi, kc * BK, nt * BN, full_bar(stage));
-          tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mapB_lo, kc * BK, nt * BN,
+        tma_load_2d(base, &mapA_hi, kc * BK, arow, full_bar(stage));
+        tma_load_2d(base + A_BYTES, &mapA_lo, kc * BK, arow, full_bar(stage));
+        if (p.mode == 2 || p.mode == 5) {
+          tma_load_2d(base + 2 * A_BYTES, &mapB_hi, kc * BK, brow, full_bar(stage));
+          tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mapB_lo, kc * BK, brow,
                       full_bar(stage));
         } else {
           tma_load_3d(base + 2 * A_BYTES, &mapB_hi, kc * BK, nt * BOUT, plane * 3,
@@ -463,7 +498,14 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
+    bool any = false;   // an MMA was issued (mode 5 may skip every tile of a CTA)
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      if (p.mode == 5) {
+        int plane, mt, nt;
+        decode_tile(p, t, plane, mt, nt);
+        if (tile_skipped(p, plane, nt)) continue;
+      }
+      any = true;
       if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.status)) {
         ok = false;
         break;
@@ -502,21 +544,24 @@ k_split_cgemm(const __grid_constant__ CUtensorMap mapA_hi,
       }
     }
     // make sure every issued MMA has finished before TMEM is released
-    mma_commit(drain_bar);
-    mbar_drain_wait(drain_bar, 0);
+    if (any) {
+      mma_commit(drain_bar);
+      mbar_drain_wait(drain_bar, 0);
+    }
   } else if (warp >= 2) {
     // ------------------------------ epilogue ----------------------------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      int plane, mt, nt;
+      decode_tile(p, t, plane, mt, nt);
+      if (tile_skipped(p, plane, nt)) continue;
       int okw = 1;
       if (lane == 0) okw = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, p.status) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) break;
       tmem_fence_after();
-      int plane, mt, nt;
-      decode_tile(p, t, plane, mt, nt);
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * ACC_COL);
       tile_epilogue(p, tbase, plane, mt, nt, quad, lane);
       tmem_fence_before();
@@ -1604,18 +1649,6 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
 // ==========================================================================
 namespace tc {
 
-PSF_D void split16d(double v, int bf16, uint16_t& hi, uint16_t& lo) {
-  if (bf16) {
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    hi = __bfloat16_as_ushort(h);
-    lo = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
-  } else {
-    const __half h = __double2half(v);
-    hi = __half_as_ushort(h);
-    lo = __half_as_ushort(__double2half(v - (double)__half2float(h)));
-  }
-}
-
 // B[(n, i)][j] = S_B w_j g_n(theta_j) J_n(k r_i sin theta_j) (Eq. 11), FP64,
 // columns j >= n_theta zero.
 __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
@@ -1858,6 +1891,89 @@ int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
   q.status = status;
   TimingScope ts(kTimeBesselRadial, s);
   return launch_gemm(mBh, mBl, mFh, mFl, q, s);
+}
+
+// ---------------------------------------------------------------------------
+// Harmonic radial contraction (mode 5): per order l' a tile grid over
+// (radius, column) with A = S_A w_j J_|l|(k r_i sin theta_j) and
+// B = S_F D[s][j] Bh[e][c][l'][j], split hi + lo; K = theta.
+// ---------------------------------------------------------------------------
+int tc_harm_cols_per_tile() { return tc::BN / 2; }
+
+int tc_harm_n_r_pad(int n_r) { return ceil_div(n_r, tc::BM) * tc::BM; }
+
+void tc_harm_carve(char* base, size_t* off, int n_theta, int n_r, int m_max, int chunk,
+                   TcHarm* out) {
+  using namespace tc;
+  auto take = [&](size_t bytes) -> char* {
+    *off = align_up(*off, 1024);
+    char* p = base ? base + *off : nullptr;
+    *off += bytes;
+    return p;
+  };
+  out->kp = tc_bessel_kp(n_theta);
+  out->n_r_pad = tc_harm_n_r_pad(n_r);
+  const size_t kp = out->kp, n_ord = 2 * (size_t)m_max + 5;
+  const size_t a_rows = (size_t)(m_max + 3) * out->n_r_pad;
+  const size_t b_rows = n_ord * 6 * (size_t)chunk;
+  out->a_bytes = a_rows * kp * 2;
+  out->A_hi = (uint16_t*)take(out->a_bytes);
+  out->A_lo = (uint16_t*)take(out->a_bytes);
+  out->B_hi = (uint16_t*)take(b_rows * kp * 2);
+  out->B_lo = (uint16_t*)take(b_rows * kp * 2);
+  const size_t tiles = (size_t)ceil_div(6 * chunk, BN);
+  out->need = (unsigned char*)take(n_ord * tiles);
+  out->bh_max = (unsigned*)take(sizeof(unsigned));
+  out->out_scale = (float*)take(sizeof(float));
+}
+
+float tc_harm_scale_a(double max_w) { return pow2_scale(max_w, 16384.0); }
+
+int tc_harm_contract(const TcHarm& ops, int n_theta, int n_r, int m_max, int n_cols,
+                     int precision, float2* prof, int* status, cudaStream_t s) {
+  using namespace tc;
+  const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
+  const int n_ord = 2 * m_max + 5;
+  auto map2 = [&](CUtensorMap* m, const uint16_t* base, long long rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n_theta, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ops.kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void*)base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE,
+              SWZ == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  CUtensorMap mAh, mAl, mBh, mBl;
+  const long long a_rows = (long long)(m_max + 3) * ops.n_r_pad;
+  const long long b_rows = (long long)n_ord * 2 * n_cols;
+  if (!(map2(&mAh, ops.A_hi, a_rows, BM) && map2(&mAl, ops.A_lo, a_rows, BM) &&
+        map2(&mBh, ops.B_hi, b_rows, BN) && map2(&mBl, ops.B_lo, b_rows, BN)))
+    return PSF_ERR_CUDA;
+  Params q;
+  memset(&q, 0, sizeof(q));
+  q.planes = n_ord;
+  q.m_tiles = ops.n_r_pad / BM;
+  q.n_tiles = ceil_div(2 * n_cols, BN);
+  q.k_chunks = ceil_div(n_theta, BK);
+  q.idesc = make_idesc(bf16);
+  q.mode = 5;
+  q.bf16 = bf16;
+  q.prof = prof;
+  q.rows_total = n_r;
+  q.n_slices = n_cols;
+  q.scale_ptr = ops.out_scale;
+  q.m_fastest = 1;
+  q.status = status;
+  q.need = ops.need;
+  q.n_ord = n_ord;
+  q.hL = m_max + 2;
+  q.n_r_pad = ops.n_r_pad;
+  q.b_rows_per_plane = 2 * n_cols;
+  return launch_gemm(mAh, mAl, mBh, mBl, q, s);
 }
 
 }  // namespace psf

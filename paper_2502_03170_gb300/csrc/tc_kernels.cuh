@@ -42,6 +42,28 @@ int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
 // Split-precision operands of the Bessel adjoint contraction
 //   g_F[s][j] = sum_row Bt[j][row] g_P[s][row]   (real Bt, complex g_P):
 // A rows j x K columns (3 N_r, pitch kp), g_P rows (s, re/im), BF16 hi + lo.
+// Harmonic radial contraction on the tensor cores (split hi + lo operands):
+// per order l' = l + m_max + 2, prof[col][l'][i] = sum_j A[|l|][i][j] B[l'][col][j]
+// over the columns col = 3 s + c of a slice chunk.
+struct TcHarm {
+  int kp, n_r_pad;
+  size_t a_bytes;            // bytes of one of A_hi / A_lo
+  uint16_t *A_hi, *A_lo;     // [(m_max + 3) n_r_pad][kp]: S_A w_j J_n(k r_i sin theta_j)
+  uint16_t *B_hi, *B_lo;     // [n_ord][chunk columns][re/im][kp]: S_F D Bh
+  unsigned char* need;       // [n_ord][tiles]: a column of the tile needs the order
+  unsigned* bh_max;          // device max |Re Bh|, |Im Bh| (float bits), zeroed per call
+  float* out_scale;          // device 1 / (S_A S_F)
+};
+int tc_harm_cols_per_tile();          // columns (s, c) per B tile
+int tc_harm_n_r_pad(int n_r);         // N_r rounded up to the A tile height
+void tc_harm_carve(char* base, size_t* off, int n_theta, int n_r, int m_max, int chunk,
+                   TcHarm* out);
+float tc_harm_scale_a(double max_w);  // S_A: power of two with max |A| < 2^14
+// The contraction of n_cols columns (all orders; tiles flagged unneeded are
+// skipped).  Returns PSF_OK or PSF_ERR_CUDA.
+int tc_harm_contract(const TcHarm& ops, int n_theta, int n_r, int m_max, int n_cols,
+                     int precision, float2* prof, int* status, cudaStream_t s);
+
 struct TcBesselAdj {
   int kp;
   uint16_t *A_hi, *A_lo;     // [n_theta][kp]

@@ -176,6 +176,18 @@ PSF_D void split16(float x, int bf16, uint16_t& hi, uint16_t& lo) {
   }
 }
 
+// The same split of an FP64 value (hi rounded from x, lo from x - hi).
+PSF_D void split16d(double v, int bf16, uint16_t& hi, uint16_t& lo) {
+  if (bf16) {
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
+  } else {
+    const __half h = __double2half(v);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__double2half(v - (double)__half2float(h)));
+  }
+}
 
 }  // namespace tc
 }  // namespace psf

@@ -17,7 +17,8 @@ the device), then exits.  Cases:
 * ``bessel_harmonic`` - ``--emitters`` emitters of the batched workload with
   every Zernike term, by azimuthal harmonics at the tail-bound order
   (``--mmax`` to set it) with the adaptive per-emitter order
-  (``--tail-tol``, default 1e-7; 0 keeps the bound order).
+  (``--tail-tol``, default 1e-7; 0 keeps the bound order); ``--precision
+  split_fp16`` puts the radial contraction on the tensor cores.
 """
 import argparse
 
@@ -73,7 +74,8 @@ def main():
         for _ in range(2):
             I = api.bessel_harmonic(c["optics"], c["depth"], c["zernike"], c["z_offsets"],
                                     c["z"], c["n_theta"], c["n_r"], c["nx"], c["ny"],
-                                    c["dx"], c["dy"], m_max=m, tail_tol=args.tail_tol)
+                                    c["dx"], c["dy"], m_max=m, tail_tol=args.tail_tol,
+                                    precision=args.precision)
         torch.cuda.synchronize()
         assert torch.isfinite(I).all()
     elif args.case == "bessel_backward":

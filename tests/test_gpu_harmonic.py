@@ -32,8 +32,9 @@ def batch(n_em, seed, n_zern=21, scale=0.08):
     return depth, zern, offs, z
 
 
-def check(d, depth, zern, offs, z, geo, m_max, tail_tol=0.0):
-    I = api.bessel_harmonic(d, depth, zern, offs, z, *geo, m_max=m_max, tail_tol=tail_tol)
+def check(d, depth, zern, offs, z, geo, m_max, tail_tol=0.0, precision="fp32"):
+    I = api.bessel_harmonic(d, depth, zern, offs, z, *geo, m_max=m_max, tail_tol=tail_tol,
+                            precision=precision)
     torch.cuda.synchronize()
     I = I.cpu().numpy()
     o = oracle_optics(d)
@@ -45,16 +46,20 @@ def check(d, depth, zern, offs, z, geo, m_max, tail_tol=0.0):
     return I
 
 
+@pytest.mark.parametrize("precision", ["fp32", "split_fp16"])
 @pytest.mark.parametrize("kw", [dict(pol=W.CIRCULAR), dict(pol=(0.6, 0.48 + 0.64j)),
                                 dict(pol=(1.0, 0.0)), dict(scalar=True),
                                 dict(fresnel=True, pol=W.CIRCULAR)])
-def test_harmonic_matches_oracle(lib, kw):
+def test_harmonic_matches_oracle(lib, kw, precision):
+    """FP32 contraction and the tensor-core (split) contraction, every
+    polarisation and model, with and without the adaptive order."""
     d = dict(W.optics_gibson_lanni(0.0), **kw)
     depth, zern, offs, z = batch(5, 3)
     m_max = api.harmonic_order(zern, 1e-6)
     assert m_max > 4
-    check(d, depth, zern, offs, z, (48, 40, 19, 16, 0.035, 0.03), m_max)
-    check(d, depth, zern, offs, z, (48, 40, 19, 16, 0.035, 0.03), m_max, tail_tol=1e-6)
+    geo = (48, 40, 19, 16, 0.035, 0.03)
+    check(d, depth, zern, offs, z, geo, m_max, precision=precision)
+    check(d, depth, zern, offs, z, geo, m_max, tail_tol=1e-6, precision=precision)
 
 
 @pytest.mark.parametrize("m_max", [0, 1, 7, 40])
@@ -78,14 +83,15 @@ def test_axisymmetric_pupil_equals_the_axisymmetric_path(lib):
     assert max_rel(Ih.cpu().numpy(), Iref) <= TOL
 
 
-def test_harmonic_workload_emitters_sampled(lib):
+@pytest.mark.parametrize("precision", ["fp32", "split_fp16"])
+def test_harmonic_workload_emitters_sampled(lib, precision):
     """Emitters of the batched workload (4..11 Zernike terms, all of them,
     depth up to 10 um) at the order the tail bound gives for 1e-7."""
     c = W.bessel(n_emitters=24)
     m_max = api.harmonic_order(c["zernike"], 1e-7)
     geo = (c["n_theta"], 128, 64, 64, c["dx"], c["dy"])
     I = api.bessel_harmonic(c["optics"], c["depth"], c["zernike"], c["z_offsets"], c["z"],
-                            *geo, m_max=m_max, tail_tol=1e-7)
+                            *geo, m_max=m_max, tail_tol=1e-7, precision=precision)
     torch.cuda.synchronize()
     I = I.cpu().numpy()
     o = oracle_optics(c["optics"])
@@ -100,16 +106,35 @@ def test_harmonic_workload_emitters_sampled(lib):
         assert max_rel(I[a:b], Ifull) <= TOL, e
 
 
+@pytest.mark.parametrize("precision", ["fp32", "split_fp16"])
 @pytest.mark.parametrize("tail_tol", [1e-3, 1e-5])
-def test_adaptive_order_orders_and_ragged(lib, tail_tol):
+def test_adaptive_order_orders_and_ragged(lib, tail_tol, precision):
     """Coarse tolerances give emitters of different orders in one batch
     (tiles of the contraction mix emitters that need an order and emitters
-    that do not); ragged sizes, an emitter without slices."""
+    that do not, and the tensor-core contraction skips tiles no column
+    needs); ragged sizes, an emitter without slices."""
     d = W.optics_gibson_lanni(0.0)
     depth, zern, offs, z = batch(6, 17, scale=0.06)
     zern[2] *= 0.05                              # a nearly axisymmetric emitter
     m_max = min(api.harmonic_order(zern, 1e-8), 40)
-    check(d, depth, zern, offs, z, (41, 37, 17, 21, 0.04, 0.035), m_max, tail_tol=tail_tol)
+    check(d, depth, zern, offs, z, (41, 37, 17, 21, 0.04, 0.035), m_max, tail_tol=tail_tol,
+          precision=precision)
+
+
+@pytest.mark.parametrize("n_em,n_r", [(2, 2), (7, 300), (40, 129)])
+def test_split_contraction_tiles(lib, n_em, n_r):
+    """The tensor-core contraction against the FP32 one and the oracle:
+    N_r not a multiple of the 128-row tile (129, 300: padded A planes), the
+    two-sample radial grid, and enough slices for several column tiles per
+    order (40 emitters)."""
+    d = W.optics_gibson_lanni(0.0)
+    depth, zern, offs, z = batch(n_em, 31 + n_em, scale=0.07)
+    m_max = min(api.harmonic_order(zern, 1e-7), 24)
+    geo = (45, n_r, 20, 20, 0.04, 0.04)
+    Is = check(d, depth, zern, offs, z, geo, m_max, tail_tol=1e-7, precision="split_fp16")
+    If = api.bessel_harmonic(d, depth, zern, offs, z, *geo, m_max=m_max, tail_tol=1e-7)
+    torch.cuda.synchronize()
+    assert max_rel(Is, If.cpu().numpy()) <= 5e-6
 
 
 @pytest.mark.parametrize("n,n_r", [(1, 33), (2, 33), (15, 33), (16, 33), (40, 96),

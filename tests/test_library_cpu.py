@@ -155,19 +155,31 @@ def test_harmonic_order_and_validation(cpu_lib):
     assert cpu_lib.psf_bessel_harmonic_order(zs.ctypes.data_as(ctypes.c_void_p), 4,
                                              zs.shape[1], 0.0) == _lib.PSF_ERR_ARG
     o = api.make_optics(W.optics_plain())
+    for prec in (_lib.PSF_PREC_FP32, _lib.PSF_PREC_SPLIT_FP16):
+        assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
+                                                          8, 8, 12, prec) > 0
+    assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64, 8, 8,
+                                                      12, _lib.PSF_PREC_SPLIT_BF16) == 0
     assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
-                                                      8, 8, 12) > 0
-    assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64,
-                                                      8, 8, 65) == 0
+                                                      8, 8, 65, _lib.PSF_PREC_FP32) == 0
+    assert cpu_lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), 4, 16, 64, 64, 8, 8,
+                                                      12, _lib.PSF_PREC_FP32_CHIRPZ) == 0
     d = ctypes.c_void_p(16)
     r = cpu_lib.psf_bessel_vectorial_harmonic(ctypes.byref(o), 4, d, d, 21, d, d, 16, 64,
-                                              64, 8, 8, 0.02, 0.02, -1, 0.0, d,
-                                              ctypes.c_void_p(256), 1 << 30, None)
+                                              64, 8, 8, 0.02, 0.02, -1, 0.0,
+                                              _lib.PSF_PREC_FP32, d, ctypes.c_void_p(256),
+                                              1 << 30, None)
     assert r == _lib.PSF_ERR_ARG
+    r = cpu_lib.psf_bessel_vectorial_harmonic(ctypes.byref(o), 4, d, d, 21, d, d, 16, 64,
+                                              64, 8, 8, 0.02, 0.02, 12, 0.0,
+                                              _lib.PSF_PREC_FP32_CHIRPZ, d,
+                                              ctypes.c_void_p(256), 1 << 30, None)
+    assert r == _lib.PSF_ERR_PRECISION
     for bad in (-1e-9, 1.0, float("nan")):
         r = cpu_lib.psf_bessel_vectorial_harmonic(ctypes.byref(o), 4, d, d, 21, d, d, 16, 64,
-                                                  64, 8, 8, 0.02, 0.02, 12, bad, d,
-                                                  ctypes.c_void_p(256), 1 << 30, None)
+                                                  64, 8, 8, 0.02, 0.02, 12, bad,
+                                                  _lib.PSF_PREC_FP32, d, ctypes.c_void_p(256),
+                                                  1 << 30, None)
         assert r == _lib.PSF_ERR_ARG and b"tail_tol" in cpu_lib.psf_last_error(), bad
 
 
