@@ -15,46 +15,73 @@ PSF_D int kind_shift(int kind) {
 PSF_D int kind_g(int kind) { return kind == 0 ? 0 : (kind <= 2 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
-// One CTA per (emitter, theta node): e^{i W_na(theta, phi_k)} on the N_phi
-// azimuths and its DFT (harmonics |m| <= M) times the axisymmetric
-// integrand -> Pm[e][m + M][j].
+// One CTA (64 threads) per (emitter, group of HP_G theta nodes):
+// e^{i W_na(theta, phi_k)} on the N_phi azimuths of the group's nodes, then
+// its DFT to the harmonics |m| <= M times the axisymmetric integrand ->
+// Pm[e][m + M][j].  A thread takes the pair +m, -m (e^{-i m phi} is the
+// conjugate twiddle) for all nodes of the group, so one twiddle load feeds
+// 32 FMAs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+constexpr int HP_G = 4;
+constexpr int HP_THREADS = 64;
+
+__global__ void __launch_bounds__(HP_THREADS)
 k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restrict__ zern,
              const float* __restrict__ Zr, const float2* __restrict__ cs,
              float2* __restrict__ Pm) {
-  extern __shared__ float2 sh[];
-  float2* Ek = sh;                 // [n_phi]
-  const int e = blockIdx.x, j = blockIdx.y;
+  extern __shared__ float4 ek4[];                        // [n_phi][HP_G] float2
+  float2* Ek = reinterpret_cast<float2*>(ek4);
+  const int e = blockIdx.x, j0 = blockIdx.y * HP_G;
   const int nP = 2 * p.m_max + 1, mask = p.n_phi - 1;
-  const size_t ej = (size_t)e * p.n_theta + j;
-  for (int k = threadIdx.x; k < p.n_phi; k += blockDim.x) {
-    float w = 0.f;
-    for (int q = 0; q < p.n_na; ++q) {
-      const float c = (float)zern[(size_t)e * p.n_zern + p.na_j[q] - 1];
-      if (c == 0.f) continue;
-      const float2 a = cs[(p.na_m[q] * k) & mask];   // e^{i m phi_k}
-      w = fmaf(c * Zr[q * p.n_theta + j], p.na_cos[q] ? a.x : a.y, w);
+  for (int idx = threadIdx.x; idx < p.n_phi * HP_G; idx += HP_THREADS) {
+    const int k = idx / HP_G, j = j0 + (idx - k * HP_G);
+    float2 v = make_float2(0.f, 0.f);
+    if (j < p.n_theta) {
+      float w = 0.f;
+      for (int q = 0; q < p.n_na; ++q) {
+        const float c = (float)zern[(size_t)e * p.n_zern + p.na_j[q] - 1];
+        if (c == 0.f) continue;
+        const float2 a = cs[(p.na_m[q] * k) & mask];   // e^{i m phi_k}
+        w = fmaf(c * Zr[q * p.n_theta + j], p.na_cos[q] ? a.x : a.y, w);
+      }
+      sincosf(w, &v.y, &v.x);
     }
-    float sn, cn;
-    sincosf(w, &sn, &cn);
-    Ek[k] = make_float2(cn, sn);
+    Ek[idx] = v;
   }
   __syncthreads();
-  const float amp = et.amp[ej];
-  const float2 base = cis_cycles(et.wfr[ej]);
-  const float scale = amp / (float)p.n_phi;
-  for (int mi = threadIdx.x; mi < nP; mi += blockDim.x) {
-    const int m = mi - p.m_max;
-    float re = 0.f, im = 0.f;
+  for (int m = threadIdx.x; m <= p.m_max; m += HP_THREADS) {
+    float2 pp[HP_G], pn[HP_G];   // sum x e^{-i m phi}, sum x e^{+i m phi}
+#pragma unroll
+    for (int g = 0; g < HP_G; ++g) pp[g] = pn[g] = make_float2(0.f, 0.f);
     for (int k = 0; k < p.n_phi; ++k) {
-      const float2 a = cs[(m * k) & mask];   // e^{i m phi_k}; times conj
-      const float2 x = Ek[k];
-      re = fmaf(x.x, a.x, fmaf(x.y, a.y, re));
-      im = fmaf(x.y, a.x, fmaf(-x.x, a.y, im));
+      const float2 a = cs[(m * k) & mask];   // e^{i m phi_k}
+      const float4 x01 = ek4[2 * k], x23 = ek4[2 * k + 1];
+      const float2 x[HP_G] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w),
+                              make_float2(x23.x, x23.y), make_float2(x23.z, x23.w)};
+#pragma unroll
+      for (int g = 0; g < HP_G; ++g) {
+        pp[g].x = fmaf(x[g].x, a.x, fmaf(x[g].y, a.y, pp[g].x));
+        pp[g].y = fmaf(x[g].y, a.x, fmaf(-x[g].x, a.y, pp[g].y));
+        pn[g].x = fmaf(x[g].x, a.x, fmaf(-x[g].y, a.y, pn[g].x));
+        pn[g].y = fmaf(x[g].y, a.x, fmaf(x[g].x, a.y, pn[g].y));
+      }
     }
-    const float2 h = cmul(base, make_float2(re, im));
-    Pm[((size_t)e * nP + mi) * p.n_theta + j] = make_float2(scale * h.x, scale * h.y);
+#pragma unroll
+    for (int g = 0; g < HP_G; ++g) {
+      const int j = j0 + g;
+      if (j >= p.n_theta) continue;
+      const size_t ej = (size_t)e * p.n_theta + j;
+      const float2 base = cis_cycles(et.wfr[ej]);
+      const float scale = et.amp[ej] / (float)p.n_phi;
+      const float2 hp = cmul(base, pp[g]);
+      Pm[((size_t)e * nP + p.m_max + m) * p.n_theta + j] =
+          make_float2(scale * hp.x, scale * hp.y);
+      if (m > 0) {
+        const float2 hn = cmul(base, pn[g]);
+        Pm[((size_t)e * nP + p.m_max - m) * p.n_theta + j] =
+            make_float2(scale * hn.x, scale * hn.y);
+      }
+    }
   }
 }
 
@@ -515,9 +542,10 @@ k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
 // the direct reads.)
 // ---------------------------------------------------------------------------
 constexpr int HO_PIX = 128;
-// prefetch distance in orders (256 workload emitters: none 12.0 ms per
-// call, 2 orders 11.2, 4 orders 11.3)
-constexpr int kHarmPrefetch = 2;
+// prefetch distance in orders (256 workload emitters, split contraction:
+// none 8.68 ms per call, 1 order 7.77, 2 orders 7.85, 3 orders 7.91; an L1
+// prefetch measured the same as L2)
+constexpr int kHarmPrefetch = 1;
 
 struct OctAcc {
   float2 s[4], c[4];
@@ -549,10 +577,11 @@ template <int R>
 PSF_D void oct_add(OctAcc& acc, const float2* q, float f, float2 t) {
   const float2 u = q[0], v0 = q[1];
   const float2 v = make_float2(fmaf(f, v0.x - u.x, u.x), fmaf(f, v0.y - u.y, u.y));
-  const float2 tv = cmul(t, v);
-  const float2 cv = cmul(make_float2(t.x, -t.y), v);
-  acc.s[R].x += tv.x; acc.s[R].y += tv.y;
-  acc.c[R].x += cv.x; acc.c[R].y += cv.y;
+  // S_R += t v, C_R += conj(t) v, each product folded into the sums
+  acc.s[R].x = fmaf(-t.y, v.y, fmaf(t.x, v.x, acc.s[R].x));
+  acc.s[R].y = fmaf(t.y, v.x, fmaf(t.x, v.y, acc.s[R].y));
+  acc.c[R].x = fmaf(t.y, v.y, fmaf(t.x, v.x, acc.c[R].x));
+  acc.c[R].y = fmaf(-t.y, v.x, fmaf(t.x, v.y, acc.c[R].y));
 }
 
 template <int J>
@@ -636,7 +665,10 @@ __global__ void k_oct_fill(HarmParams p, int npx, int* __restrict__ cursor,
   tab[atomicAdd(&cursor[q.i0], 1)] = q;
 }
 
-__global__ void __launch_bounds__(3 * HO_PIX)
+// (four blocks of 384 threads per SM cap the registers at 40 with a small
+// spill; 256 workload emitters, split contraction: 6.76 ms per call against
+// 7.67 ms at three blocks)
+__global__ void __launch_bounds__(3 * HO_PIX, 4)
 k_harm_intensity_oct(HarmParams p, const float2* __restrict__ prof,
                      const int* __restrict__ slice_em, const int* __restrict__ valid,
                      const int* __restrict__ ord, const OctPix* __restrict__ tab, int s0,
@@ -729,8 +761,9 @@ k_harm_intensity_oct(HarmParams p, const float2* __restrict__ prof,
 void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const double* zern,
                        const float* Zr, const float2* cs, float2* Pm, int* ord, float2* Bh,
                        unsigned* bh_max, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * (size_t)p.n_phi;
-  k_harm_pupil<<<dim3(p.n_em, p.n_theta), 128, smem, s>>>(p, t, e, zern, Zr, cs, Pm);
+  const size_t smem = sizeof(float2) * (size_t)p.n_phi * HP_G;
+  k_harm_pupil<<<dim3(p.n_em, ceil_div(p.n_theta, HP_G)), HP_THREADS, smem, s>>>(
+      p, t, e, zern, Zr, cs, Pm);
   k_harm_order<<<p.n_em, 256, 0, s>>>(p, Pm, ord);
   if (bh_max) cudaMemsetAsync(bh_max, 0, sizeof(unsigned), s);
   k_harm_mix<<<dim3(p.n_em, p.n_theta), 128, 0, s>>>(p, t, e, Pm, ord, Bh, bh_max);
