@@ -43,12 +43,12 @@ FP32_LANES_PER_SM = 128
 # on: when the kernel's sources hash differently, traffic is reported as null.
 PROFILED_TRAFFIC = {
     # one 128-plane launch (256^2 pupil, 512^2 px), CTA-pair kernel, stage 2:
-    # 404.86 MB read + 113.36 MB written (U streams from HBM at this chunk)
+    # 404.92 MB read + 116.17 MB written (U streams from HBM at this chunk)
     "stage2_contraction_intensity": dict(
-        bytes_per_unit=(404.857e6 + 113.357e6) / 128, unit="plane",
+        bytes_per_unit=(404.92e6 + 116.17e6) / 128, unit="plane",
         sources=("tc_kernels.cu:k_split_cgemm_pair", "tc_kernels.cu:tile_epilogue",
                  "tc_kernels.cu:store_rows_t4", "tc_ptx.cuh", "tc_pair_ptx.cuh"),
-        sha256_16="0e6b71e56aaad66b", precision="split_fp16"),
+        sha256_16="c0e85c2a303767e2", precision="split_fp16"),
     # 9442 slices of 128^2 px: 58.27 MB read + 557.25 MB written
     "bessel_radial_to_cartesian": dict(
         bytes_per_unit=(58.272e6 + 557.250e6) / 9442, unit="slice",
