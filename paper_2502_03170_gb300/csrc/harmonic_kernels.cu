@@ -16,11 +16,12 @@ PSF_D int kind_g(int kind) { return kind == 0 ? 0 : (kind <= 2 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
 // One CTA (64 threads) per (emitter, group of HP_G theta nodes):
-// e^{i W_na(theta, phi_k)} on the N_phi azimuths of the group's nodes, then
-// its DFT to the harmonics |m| <= M times the axisymmetric integrand ->
-// Pm[e][m + M][j].  A thread takes the pair +m, -m (e^{-i m phi} is the
-// conjugate twiddle) for all nodes of the group, so one twiddle load feeds
-// 32 FMAs.
+// e^{i W_na(theta_j, phi_k)} on the N_phi azimuths of each node, its DFT
+// X_m = sum_k x_k e^{-2 pi i m k / N_phi} by a radix-2 decimation-in-time
+// FFT in shared memory (inputs stored in bit-reversed order, log2 N_phi
+// butterfly stages with twiddles conj(cs)), then P_m = A e^{i W_ax} X_m /
+// N_phi for |m| <= M (X_{N_phi - m} for -m) -> Pm[e][m + M][j].  The
+// products c_q N_q R_q(theta_j) of the m != 0 terms are formed once per CTA.
 // ---------------------------------------------------------------------------
 constexpr int HP_G = 4;
 constexpr int HP_THREADS = 64;
@@ -29,59 +30,56 @@ __global__ void __launch_bounds__(HP_THREADS)
 k_harm_pupil(HarmParams p, ThetaTable t, EmitterTable et, const double* __restrict__ zern,
              const float* __restrict__ Zr, const float2* __restrict__ cs,
              float2* __restrict__ Pm) {
-  extern __shared__ float4 ek4[];                        // [n_phi][HP_G] float2
-  float2* Ek = reinterpret_cast<float2*>(ek4);
+  extern __shared__ float2 X[];                // [HP_G][n_phi]
+  __shared__ float cz[kHarmMaxNA][HP_G];
   const int e = blockIdx.x, j0 = blockIdx.y * HP_G;
-  const int nP = 2 * p.m_max + 1, mask = p.n_phi - 1;
-  for (int idx = threadIdx.x; idx < p.n_phi * HP_G; idx += HP_THREADS) {
-    const int k = idx / HP_G, j = j0 + (idx - k * HP_G);
-    float2 v = make_float2(0.f, 0.f);
-    if (j < p.n_theta) {
-      float w = 0.f;
-      for (int q = 0; q < p.n_na; ++q) {
-        const float c = (float)zern[(size_t)e * p.n_zern + p.na_j[q] - 1];
-        if (c == 0.f) continue;
-        const float2 a = cs[(p.na_m[q] * k) & mask];   // e^{i m phi_k}
-        w = fmaf(c * Zr[q * p.n_theta + j], p.na_cos[q] ? a.x : a.y, w);
-      }
-      sincosf(w, &v.y, &v.x);
-    }
-    Ek[idx] = v;
+  const int N = p.n_phi, mask = N - 1, nP = 2 * p.m_max + 1;
+  const int logN = 31 - __clz(N);
+  for (int idx = threadIdx.x; idx < p.n_na * HP_G; idx += HP_THREADS) {
+    const int q = idx / HP_G, g = idx - q * HP_G, j = j0 + g;
+    cz[q][g] = j < p.n_theta
+                   ? (float)zern[(size_t)e * p.n_zern + p.na_j[q] - 1] * Zr[q * p.n_theta + j]
+                   : 0.f;
   }
   __syncthreads();
-  for (int m = threadIdx.x; m <= p.m_max; m += HP_THREADS) {
-    float2 pp[HP_G], pn[HP_G];   // sum x e^{-i m phi}, sum x e^{+i m phi}
-#pragma unroll
-    for (int g = 0; g < HP_G; ++g) pp[g] = pn[g] = make_float2(0.f, 0.f);
-    for (int k = 0; k < p.n_phi; ++k) {
-      const float2 a = cs[(m * k) & mask];   // e^{i m phi_k}
-      const float4 x01 = ek4[2 * k], x23 = ek4[2 * k + 1];
-      const float2 x[HP_G] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w),
-                              make_float2(x23.x, x23.y), make_float2(x23.z, x23.w)};
-#pragma unroll
-      for (int g = 0; g < HP_G; ++g) {
-        pp[g].x = fmaf(x[g].x, a.x, fmaf(x[g].y, a.y, pp[g].x));
-        pp[g].y = fmaf(x[g].y, a.x, fmaf(-x[g].x, a.y, pp[g].y));
-        pn[g].x = fmaf(x[g].x, a.x, fmaf(-x[g].y, a.y, pn[g].x));
-        pn[g].y = fmaf(x[g].y, a.x, fmaf(x[g].x, a.y, pn[g].y));
-      }
+  // x_k = e^{i W_na(theta_j, phi_k)}, stored at the bit-reversed index of k
+  for (int idx = threadIdx.x; idx < N * HP_G; idx += HP_THREADS) {
+    const int g = idx / N, k = idx - g * N;
+    float w = 0.f;
+    for (int q = 0; q < p.n_na; ++q) {
+      const float2 a = cs[(p.na_m[q] * k) & mask];   // e^{i m phi_k}
+      w = fmaf(cz[q][g], p.na_cos[q] ? a.x : a.y, w);
     }
-#pragma unroll
-    for (int g = 0; g < HP_G; ++g) {
-      const int j = j0 + g;
-      if (j >= p.n_theta) continue;
-      const size_t ej = (size_t)e * p.n_theta + j;
-      const float2 base = cis_cycles(et.wfr[ej]);
-      const float scale = et.amp[ej] / (float)p.n_phi;
-      const float2 hp = cmul(base, pp[g]);
-      Pm[((size_t)e * nP + p.m_max + m) * p.n_theta + j] =
-          make_float2(scale * hp.x, scale * hp.y);
-      if (m > 0) {
-        const float2 hn = cmul(base, pn[g]);
-        Pm[((size_t)e * nP + p.m_max - m) * p.n_theta + j] =
-            make_float2(scale * hn.x, scale * hn.y);
-      }
+    float2 v;
+    sincosf(w, &v.y, &v.x);
+    X[g * N + (int)(__brev((unsigned)k) >> (32 - logN))] = v;
+  }
+  __syncthreads();
+  // butterflies: stage h = 1, 2, 4, ..: (a, b) -> (a + w b, a - w b),
+  // w = e^{-2 pi i r / (2 h)} = conj(cs[r N / (2 h)])
+  for (int h = 1; h < N; h <<= 1) {
+    const int step = N / (2 * h);
+    for (int idx = threadIdx.x; idx < (N / 2) * HP_G; idx += HP_THREADS) {
+      const int g = idx / (N / 2), bf = idx - g * (N / 2);
+      const int r = bf & (h - 1), i0 = ((bf - r) << 1) + r;
+      float2* base = X + g * N;
+      const float2 c = cs[r * step];
+      const float2 a = base[i0], b = base[i0 + h];
+      const float2 wb = make_float2(fmaf(c.x, b.x, c.y * b.y), fmaf(c.x, b.y, -c.y * b.x));
+      base[i0] = make_float2(a.x + wb.x, a.y + wb.y);
+      base[i0 + h] = make_float2(a.x - wb.x, a.y - wb.y);
     }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < nP * HP_G; idx += HP_THREADS) {
+    const int g = idx / nP, mi = idx - g * nP, j = j0 + g;
+    if (j >= p.n_theta) continue;
+    const int m = mi - p.m_max;
+    const size_t ej = (size_t)e * p.n_theta + j;
+    const float2 base = cis_cycles(et.wfr[ej]);
+    const float scale = et.amp[ej] / (float)N;
+    const float2 h = cmul(base, X[g * N + (m & mask)]);
+    Pm[((size_t)e * nP + mi) * p.n_theta + j] = make_float2(scale * h.x, scale * h.y);
   }
 }
 
@@ -534,14 +532,20 @@ k_harm_intensity(HarmParams p, const float2* __restrict__ prof,
 // channel: 16 accumulators, two profile pointers), so that enough warps are
 // resident to cover the profile-read latency; the channels' |E_c|^2 of the
 // eight images meet in shared memory and are summed in channel order.
-// Orders are taken in pairs +n, -n, read through pointers stepped by one
-// profile row per order; T_{+n} = w^n and T_{-n} = conj(w)^n by recurrences
-// outward from n = 0.  (Staging a block's radial run of the profiles in
-// shared memory was measured slower: the ~80-sample runs of the blocks of a
-// 128^2 slice re-read its profiles 3.4 times through L2, where L1 serves
-// the direct reads.)
+// The pixels are taken in the order of their radius sample (table built
+// per call), so a block's 128 pixels span a short run [lo, hi] of radial
+// samples: the block stages that window of its emitter's orders |l| <= Le
+// for the three channels in shared memory (read once per slice in all)
+// and reads the profiles from there; a window too long for the budget
+// (large N_r on a small grid) is read from global memory, with an L2
+// prefetch one order ahead.  Orders are taken in pairs +n, -n, read through
+// pointers stepped by one row per order; T_{+n} = w^n and T_{-n} =
+// conj(w)^n by recurrences outward from n = 0.
 // ---------------------------------------------------------------------------
 constexpr int HO_PIX = 128;
+// staged profile window per block (dynamic; with the 12 KB of channel
+// partials the block stays under the 48 KB default)
+constexpr int HO_SMEM = 35 * 1024;
 // prefetch distance in orders (256 workload emitters, split contraction:
 // none 8.68 ms per call, 1 order 7.77, 2 orders 7.85, 3 orders 7.91; an L1
 // prefetch measured the same as L2)
@@ -673,42 +677,61 @@ k_harm_intensity_oct(HarmParams p, const float2* __restrict__ prof,
                      const int* __restrict__ slice_em, const int* __restrict__ valid,
                      const int* __restrict__ ord, const OctPix* __restrict__ tab, int s0,
                      float* __restrict__ I) {
+  extern __shared__ float2 stg[];   // staged window [3][2 Le + 1][range]
   __shared__ float part[3][8][HO_PIX];
   const int sl = blockIdx.y, s = s0 + sl;
   const int e = slice_em[s];
   if (e < 0 || !valid[e]) return;   // uniform over the block
   const int ch = threadIdx.x / HO_PIX, t = threadIdx.x - ch * HO_PIX;
-  const int h = (p.nx + 1) / 2;
-  const int idx = blockIdx.x * HO_PIX + t;
-  const bool act = idx < h * (h + 1) / 2;
+  const int h = (p.nx + 1) / 2, npx = h * (h + 1) / 2;
+  const int first = blockIdx.x * HO_PIX, idx = first + t;
+  const bool act = idx < npx;
+  const int L = p.m_max + 2, Le = ord[e] + 2, n_r = p.n_r, nrow = 2 * Le + 1;
+  // the block's pixels are sorted by radius sample: their radii lie in
+  // [lo, hi] with lo, hi from the first and the last pixel
+  const int lo = tab[first].i0;
+  const int hi = tab[min(first + HO_PIX, npx) - 1].i0 + 1;
+  const int range = hi - lo + 1;
+  const bool staged = (size_t)3 * nrow * range * sizeof(float2) <= (size_t)HO_SMEM;
+  const float2* slice_prof = prof + (size_t)sl * 3 * p.n_ord * n_r;
+  if (staged) {
+    for (int x = threadIdx.x; x < 3 * nrow * range; x += 3 * HO_PIX) {
+      const int r = x / range, ii = x - r * range;
+      const int c = r / nrow, li = r - c * nrow;   // order l = li - Le
+      stg[x] = slice_prof[((size_t)c * p.n_ord + (li - Le + L)) * n_r + lo + ii];
+    }
+    __syncthreads();
+  }
   int a = 0, b = 0;
   if (act) {
-    const OctPix q = tab[idx];   // pixels in the order of their radius sample
+    const OctPix q = tab[idx];
     a = q.a;
     b = q.b;
-    const int i0 = q.i0;
     const float f = q.f;
     const float2 w = make_float2(-q.sp, q.cp);    // i e^{i phi}
     const float2 wc = make_float2(-q.sp, -q.cp);  // its inverse
-    const int L = p.m_max + 2, Le = ord[e] + 2, n_r = p.n_r;
     OctAcc acc;
 #pragma unroll
     for (int r = 0; r < 4; ++r) acc.s[r] = acc.c[r] = make_float2(0.f, 0.f);
-    const float2* pp =
-        prof + ((size_t)(sl * 3 + ch) * p.n_ord + L) * (size_t)n_r + i0;   // order +n
-    const float2* pm = pp;                                                 // order -n
+    // order +n / -n rows of this channel: in the staged window (row stride
+    // range) or in the profiles (row stride n_r)
+    const int stride = staged ? range : n_r;
+    const float2* pp = staged ? stg + ((size_t)ch * nrow + Le) * range + (q.i0 - lo)
+                              : slice_prof + ((size_t)ch * p.n_ord + L) * n_r + q.i0;
+    const float2* pm = pp;
     float2 tp = make_float2(1.f, 0.f), tn = make_float2(1.f, 0.f);
-    // after each order, an L2 prefetch of the rows kHarmPrefetch orders ahead
-    // (within |l| <= Le, so inside this channel's rows)
+    // after each order, unless staged, an L2 prefetch of the rows
+    // kHarmPrefetch orders ahead (within |l| <= Le, so inside this
+    // channel's rows)
     int nn = 0;
     auto step = [&]() {
       tp = cmul(tp, w);
       tn = cmul(tn, wc);
-      pp += n_r;
-      pm -= n_r;
+      pp += stride;
+      pm -= stride;
       ++nn;
       const int ahead = min(kHarmPrefetch, Le - nn);
-      if (ahead > 0) {
+      if (!staged && ahead > 0) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + (size_t)ahead * n_r));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(pm - (size_t)ahead * n_r));
       }
@@ -831,8 +854,8 @@ void launch_harm_intensity(const HarmParams& p, const float2* prof, const int* s
   if (harm_square(p)) {
     const int h = (p.nx + 1) / 2;
     const dim3 grid(ceil_div(h * (h + 1) / 2, HO_PIX), ns);
-    k_harm_intensity_oct<<<grid, 3 * HO_PIX, 0, s>>>(p, prof, slice_em, valid, ord, octab,
-                                                     s0, I);
+    k_harm_intensity_oct<<<grid, 3 * HO_PIX, HO_SMEM, s>>>(p, prof, slice_em, valid, ord,
+                                                           octab, s0, I);
     return;
   }
   const int quarter = ((p.nx + 1) / 2) * ((p.ny + 1) / 2);
