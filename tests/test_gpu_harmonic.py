@@ -32,7 +32,7 @@ def batch(n_em, seed, n_zern=21, scale=0.08):
     return depth, zern, offs, z
 
 
-def check(d, depth, zern, offs, z, geo, m_max, tail_tol=0.0, precision="fp32"):
+def check(d, depth, zern, offs, z, geo, m_max, tail_tol=0.0, precision="fp32", tol=TOL):
     I = api.bessel_harmonic(d, depth, zern, offs, z, *geo, m_max=m_max, tail_tol=tail_tol,
                             precision=precision)
     torch.cuda.synchronize()
@@ -42,7 +42,7 @@ def check(d, depth, zern, offs, z, geo, m_max, tail_tol=0.0, precision="fp32"):
     for e in range(len(depth)):
         a, b = offs[e], offs[e + 1]
         if b > a:
-            assert max_rel(I[a:b], Iref[a:b]) <= TOL, e
+            assert max_rel(I[a:b], Iref[a:b]) <= tol, e
     return I
 
 
@@ -155,3 +155,18 @@ def test_square_geometry_octant_epilogue(lib, n, n_r):
     I4 = api.bessel_harmonic(d, depth, zern, offs, z, *geo4, m_max=m_max, tail_tol=1e-7)
     torch.cuda.synchronize()
     assert max_rel(I, I4.cpu().numpy()) <= 2e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_fp16"])
+@pytest.mark.parametrize("px", [(9, 11, 0.05, 0.04), (12, 12, 0.045, 0.045)])
+def test_maximum_order_and_nodes(lib, precision, px):
+    """The largest sizes the call takes: m_max = 64 (133 orders, a 512-point
+    azimuthal FFT) with every order kept, and 880 Gauss-Legendre nodes; the
+    quarter-pixel and the octant epilogue.  The split form keeps about 21
+    bits per product; with 880 strongly oscillating terms per integral
+    (aberrations of 0.15 rad per term) it measured 1.2e-5, so it is held to
+    2e-5 here (the FP32 contraction to the 1e-5 bound)."""
+    d = W.optics_gibson_lanni(0.0)
+    depth, zern, offs, z = batch(3, 91, scale=0.15)
+    check(d, depth, zern, offs, z, (880, 40) + px, 64, tail_tol=0.0, precision=precision,
+          tol=TOL if precision == "fp32" else 2e-5)
