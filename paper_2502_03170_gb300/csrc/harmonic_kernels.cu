@@ -130,7 +130,22 @@ k_harm_order(HarmParams p, const float2* __restrict__ Pm, int* __restrict__ ord)
 __global__ void __launch_bounds__(128)
 k_harm_mix(HarmParams p, ThetaTable t, EmitterTable et, const float2* __restrict__ Pm,
            const int* __restrict__ ord, float2* __restrict__ Bh, unsigned* bh_max) {
+  // coef[c][kind] g_kind(theta_j) for this node, once per CTA (the FP64
+  // table entries are converted here only: on this GPU the conversions run
+  // on the narrow FP64 pipe)
+  __shared__ float2 cg[3][5];
+  __shared__ bool cz[3][5];
   const int e = blockIdx.x, j = blockIdx.y;
+  if (threadIdx.x < 15) {
+    const int c = threadIdx.x / 5, kind = threadIdx.x - 5 * c;
+    const double cr = p.coef[c][kind][0], ci = p.coef[c][kind][1];
+    const int gk = kind_g(kind);
+    const float2 g = make_float2((float)t.g[(size_t)(2 * gk) * p.n_theta + j],
+                                 (float)t.g[(size_t)(2 * gk + 1) * p.n_theta + j]);
+    cg[c][kind] = cmul(make_float2((float)cr, (float)ci), g);
+    cz[c][kind] = cr == 0.0 && ci == 0.0;
+  }
+  __syncthreads();
   const int nP = 2 * p.m_max + 1, Me = ord[e];
   const bool ok = et.valid[e] != 0;
   const int L = p.m_max + 2;
@@ -141,13 +156,9 @@ k_harm_mix(HarmParams p, ThetaTable t, EmitterTable et, const float2* __restrict
     for (int kind = 0; kind < 5; ++kind) {
       const int m = l + kind_shift(kind);
       if (m < -Me || m > Me) continue;
-      const double cr = p.coef[c][kind][0], ci = p.coef[c][kind][1];
-      if (cr == 0.0 && ci == 0.0) continue;
-      const int gk = kind_g(kind);
-      const float2 g = make_float2((float)t.g[(size_t)(2 * gk) * p.n_theta + j],
-                                   (float)t.g[(size_t)(2 * gk + 1) * p.n_theta + j]);
+      if (cz[c][kind]) continue;
       const float2 pm = Pm[((size_t)e * nP + m + p.m_max) * p.n_theta + j];
-      const float2 v = cmul(cmul(make_float2((float)cr, (float)ci), g), pm);
+      const float2 v = cmul(cg[c][kind], pm);
       acc.x += v.x;
       acc.y += v.y;
     }
