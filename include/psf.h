@@ -141,8 +141,14 @@ size_t psf_fourier_workspace_size(const psf_optics* opt, int n_pupil,
  *   zernike    host [n_zern] (may be NULL if n_zern == 0), 0 <= n_zern <= 66
  *   phase_map  device float [n_pupil][n_pupil] W_0 in radians, or NULL
  *   intensity  float [nz][nx][ny] (required), device memory or pinned host
- *              memory (written through its device alias; host memory that is
- *              not pinned gives PSF_ERR_ARG before any launch)
+ *              memory; host memory that is not pinned gives PSF_ERR_ARG
+ *              before any launch.  A pinned host intensity without fields
+ *              on the split precisions is streamed: the stack is computed
+ *              in eight z-chunks into a staging area of the workspace (when
+ *              it has room beyond the chunk layout) and each chunk is copied
+ *              to the host while the next one runs; the call completes on
+ *              `stream` once the stack is on the host.  Otherwise the
+ *              kernels store through the host memory's device alias.
  *   fields     complex64 [nz][3][nx][ny], or NULL (same memory rules)
  * Sizes: 2 <= n_pupil <= 4096, nx, ny, nz >= 1. */
 int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,

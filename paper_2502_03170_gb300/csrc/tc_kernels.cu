@@ -1274,12 +1274,45 @@ static SideStream* side_stream() {
   return &x;
 }
 
+// Copies of finished z-chunks to a pinned host output run on a per-device
+// stream of their own: stage 2 of chunk i writes staging buffer i mod 2, an
+// event hands it to the copy stream, and stage 2 of chunk i + 2 waits for
+// that copy before it reuses the buffer.
+struct CopyStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t done[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+};
+
+static CopyStream* copy_stream() {
+  static thread_local CopyStream cs[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  CopyStream& x = cs[dev];
+  if (x.dev != dev) {
+    bool ok = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+      ok = cudaEventCreateWithFlags(&x.done[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x.copied[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    x.dev = dev;
+  }
+  return &x;
+}
+
+bool tc_host_streaming_available() { return copy_stream() != nullptr; }
+
 int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
                        int N, int nx, int ny, double dx, double dy, int nz,
                        int zc, double na_over_lambda, float scale,
                        double amp_bound, int precision, float* intensity,
-                       float2* fields, int* status, cudaStream_t s) {
+                       float2* fields, float* host_out, int* status, cudaStream_t s) {
   using namespace tc;
+  CopyStream* cps = host_out ? copy_stream() : nullptr;
+  if (host_out && !cps) return PSF_ERR_CUDA;
   const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
   const int K = 2 * N;
   const double target = 16384.0;             // keep |scaled value| <= 2^14
@@ -1377,7 +1410,16 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     p2.n_rows = ny;
     p2.mode = 1;
     p2.out_scale = scale / (sA * sU);
-    p2.I = intensity + (size_t)z0 * nx * ny;
+    const int buf = (z0 / zc) & 1;
+    const size_t plane = (size_t)nx * ny;
+    if (cps) {
+      // `intensity` is the two-chunk staging area; wait until the copy of
+      // chunk i - 2 has left this buffer
+      p2.I = intensity + (size_t)buf * zc * plane;
+      cudaStreamWaitEvent(s, cps->copied[buf], 0);
+    } else {
+      p2.I = intensity + (size_t)z0 * plane;
+    }
     p2.F = fields ? fields + (size_t)z0 * 3 * nx * ny : nullptr;
     {
       TimingScope ts(kTimeStage2, s);
@@ -1385,12 +1427,24 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
                : launch_gemm(mAx_h, mAx_l, mU_h, mU_l, p2, s);
     }
     if (r) return r;
+    if (cps) {
+      cudaEventRecord(cps->done[buf], s);
+      cudaStreamWaitEvent(cps->s, cps->done[buf], 0);
+      cudaMemcpyAsync(host_out + (size_t)z0 * plane, p2.I, (size_t)nzc * plane * sizeof(float),
+                      cudaMemcpyDeviceToHost, cps->s);
+      cudaEventRecord(cps->copied[buf], cps->s);
+    }
     if (more) {
       if (side)
         cudaStreamWaitEvent(s, side->ready, 0);
       else
         pupil(z0 + zc, s);
     }
+  }
+  if (cps) {
+    // the call completes on the caller's stream once the stack is on the host
+    cudaStreamWaitEvent(s, cps->copied[0], 0);
+    cudaStreamWaitEvent(s, cps->copied[1], 0);
   }
   return PSF_OK;
 }

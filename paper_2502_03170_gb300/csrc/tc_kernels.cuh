@@ -96,11 +96,16 @@ void tc_fourier_carve(char* base, size_t* off, int N, int nx, int ny, int zc,
 // Upper bound of |P_c| over the pupil (for the power-of-two operand scales).
 double tc_pupil_amplitude_bound(const NodeParams& np);
 
+// The forward over the z-chunks of zc planes.  With host_out (pinned host
+// memory of the whole stack) `intensity` is a device staging area of two
+// chunks: each chunk is copied to host_out on a copy stream while the next
+// one is computed, and the call completes on s once the stack is on the host.
 int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
                        int N, int nx, int ny, double dx, double dy, int nz,
                        int zc, double na_over_lambda, float scale,
                        double amp_bound, int precision, float* intensity,
-                       float2* fields, int* status, cudaStream_t s);
+                       float2* fields, float* host_out, int* status, cudaStream_t s);
+bool tc_host_streaming_available();
 
 // Split-precision Fourier adjoint (tensor cores).  Per z-chunk: pupil fields,
 // stage 1, stage 2 recomputed with the adjoint source R = g E written as BF16

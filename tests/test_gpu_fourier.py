@@ -6,6 +6,8 @@ split-fp16 contractions.  Split-bf16 keeps only 16 significant bits per
 operand (hi + lo of 8 bits each), so its bound is the one its representation
 error gives: 2^-16 per operand and product, i.e. a few 1e-5 on |E|^2; it is
 tested at 1e-4 and its measured error is reported by the benchmark."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -159,3 +161,37 @@ def test_output_to_pinned_host_memory(lib, prec):
         api.fourier(c["optics"], 64, c["grid"], zernike=c["zernike"], precision=prec,
                     out=I_page)
     assert e.value.code == _lib.PSF_ERR_ARG
+
+
+def test_streamed_host_output(lib):
+    """With a pinned host output the split path computes the stack in eight
+    z-chunks into a device staging area and copies each chunk to the host
+    while the next one runs (37 planes: chunks of 5, the last one short);
+    with a workspace too small for the staging area it stores through the
+    host memory's device alias instead.  Both are bitwise the device
+    result."""
+    c = W.fourier(n_pupil=64, nx=96, nz=37)
+    o = api.make_optics(c["optics"])
+    g = api.Grid(c["grid"])
+    zh = np.ascontiguousarray(c["zernike"], dtype=np.float64)
+    p = api.PRECISIONS["split_fp16"]
+    full = lib.psf_fourier_workspace_size(ctypes.byref(o), 64, ctypes.byref(g.c), p)
+    I_dev = api.fourier(c["optics"], 64, c["grid"], zernike=c["zernike"],
+                        precision="split_fp16").cpu().numpy()
+    done = 0
+    # the full workspace streams; the smaller ones stream shorter chunks or,
+    # without room for the staging area, take the device alias
+    for ws_bytes in (full, full // 3, full // 8, full // 24):
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        host = torch.full(tuple(I_dev.shape), float("nan"), dtype=torch.float32,
+                          pin_memory=True)
+        r = lib.psf_fourier_vectorial(
+            ctypes.byref(o), 64, ctypes.byref(g.c), zh.ctypes.data_as(ctypes.c_void_p),
+            len(zh), None, p, api._ptr(host), None, api._ptr(ws), ws_bytes, api._stream())
+        if r == _lib.PSF_ERR_WORKSPACE:
+            continue                  # smaller than one plane's layout
+        _lib.check(lib, r)
+        torch.cuda.synchronize()
+        assert np.array_equal(host.numpy(), I_dev), ws_bytes
+        done += 1
+    assert done >= 2
