@@ -527,22 +527,22 @@ k_bessel_adj_epilogue_staged(BesselParams p, float2* __restrict__ prof,
                              float* __restrict__ loss_slice, uint16_t* __restrict__ g_hi,
                              uint16_t* __restrict__ g_lo, int kp, int* status) {
   using namespace tc;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_sb[];
   const int n_r = p.n_r, rows = 3 * n_r, n_cells = n_r - 1;
   const int hb = (p.ny + 1) / 2, ng = ((p.nx + 1) / 2) * hb;
   const int npix = p.nx * p.ny;
   const SbLayout L = sb_layout(npix, n_r, ng);
-  const uint32_t bar0 = smem_u32(smem + L.bars);
-  volatile int* flag = reinterpret_cast<volatile int*>(smem + L.flag);
-  float* Gb = reinterpret_cast<float*>(smem + L.gbuf);
-  float2* Pb = reinterpret_cast<float2*>(smem + L.pbuf);
-  float2* W = reinterpret_cast<float2*>(smem + L.W);
-  float* sf = reinterpret_cast<float*>(smem + L.sf);
-  int* cs = reinterpret_cast<int*>(smem + L.cs);
-  float2* lo = reinterpret_cast<float2*>(smem + L.lo);
-  float2* hi = reinterpret_cast<float2*>(smem + L.hi);
-  float* mp = reinterpret_cast<float*>(smem + L.mp);
-  float* red = reinterpret_cast<float*>(smem + L.red);
+  const uint32_t bar0 = smem_u32(smem_sb + L.bars);
+  volatile int* flag = reinterpret_cast<volatile int*>(smem_sb + L.flag);
+  float* Gb = reinterpret_cast<float*>(smem_sb + L.gbuf);
+  float2* Pb = reinterpret_cast<float2*>(smem_sb + L.pbuf);
+  float2* W = reinterpret_cast<float2*>(smem_sb + L.W);
+  float* sf = reinterpret_cast<float*>(smem_sb + L.sf);
+  int* cs = reinterpret_cast<int*>(smem_sb + L.cs);
+  float2* lo = reinterpret_cast<float2*>(smem_sb + L.lo);
+  float2* hi = reinterpret_cast<float2*>(smem_sb + L.hi);
+  float* mp = reinterpret_cast<float*>(smem_sb + L.mp);
+  float* red = reinterpret_cast<float*>(smem_sb + L.red);
   const int tid = threadIdx.x;
   const uint32_t g_bytes = (uint32_t)npix * 4u, p_bytes = (uint32_t)rows * 8u;
 

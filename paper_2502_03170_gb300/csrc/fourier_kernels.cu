@@ -467,7 +467,6 @@ void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s)
 // Z_j once and reduces it against every pupil's gradient (FP64, fixed order);
 // one thread per (k, j) then adds the parts in order.
 constexpr int kZgParts = 64;
-constexpr int kZgMaxPupils = 128;
 
 // One CTA per (Zernike term j, node part): every pupil of the group at once.
 // Each thread reads Z_j at its nodes once and keeps one FP32 partial per

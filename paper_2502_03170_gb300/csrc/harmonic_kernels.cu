@@ -124,48 +124,68 @@ k_harm_order(HarmParams p, const float2* __restrict__ Pm, int* __restrict__ ord)
 }
 
 // ---------------------------------------------------------------------------
-// Channel/order mixtures from the harmonics |m| <= M_e, one CTA per (theta
-// emitter, theta node): Bh[e][c][l'][j] (zero for |l| > M_e + 2).
+// Channel/order mixtures from the harmonics |m| <= M_e: Bh[e][c][l'][j]
+// (zero for |l| > M_e + 2).  One CTA (256 threads) per (emitter, 32 theta
+// nodes): the lanes run over the nodes, so the harmonics are read and the
+// mixtures written in coalesced rows; the eight warps share the outputs
+// (c, l').  The coefficient x g products are formed once per node (the FP64
+// tables are converted here only: on this GPU the conversions run on the
+// narrow FP64 pipe).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+constexpr int HM_NODES = 32;
+
+__global__ void __launch_bounds__(256)
 k_harm_mix(HarmParams p, ThetaTable t, EmitterTable et, const float2* __restrict__ Pm,
            const int* __restrict__ ord, float2* __restrict__ Bh, unsigned* bh_max) {
-  // coef[c][kind] g_kind(theta_j) for this node, once per CTA (the FP64
-  // table entries are converted here only: on this GPU the conversions run
-  // on the narrow FP64 pipe)
-  __shared__ float2 cg[3][5];
+  __shared__ float2 pcol[2 * kHarmMaxM + 1][HM_NODES];   // P_m of the nodes
+  __shared__ float2 cg[3][5][HM_NODES];                  // coef[c][kind] g_kind
   __shared__ bool cz[3][5];
-  const int e = blockIdx.x, j = blockIdx.y;
-  if (threadIdx.x < 15) {
-    const int c = threadIdx.x / 5, kind = threadIdx.x - 5 * c;
+  const int e = blockIdx.x, j0 = blockIdx.y * HM_NODES;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = j0 + tx;
+  const bool jin = j < p.n_theta;
+  const int nP = 2 * p.m_max + 1;
+  for (int mi = ty; mi < nP; mi += 8)
+    pcol[mi][tx] = jin ? Pm[((size_t)e * nP + mi) * p.n_theta + j] : make_float2(0.f, 0.f);
+  for (int ck = ty; ck < 15; ck += 8) {
+    const int c = ck / 5, kind = ck - 5 * c;
     const double cr = p.coef[c][kind][0], ci = p.coef[c][kind][1];
     const int gk = kind_g(kind);
-    const float2 g = make_float2((float)t.g[(size_t)(2 * gk) * p.n_theta + j],
-                                 (float)t.g[(size_t)(2 * gk + 1) * p.n_theta + j]);
-    cg[c][kind] = cmul(make_float2((float)cr, (float)ci), g);
-    cz[c][kind] = cr == 0.0 && ci == 0.0;
+    float2 g = make_float2(0.f, 0.f);
+    if (jin)
+      g = make_float2((float)t.g[(size_t)(2 * gk) * p.n_theta + j],
+                      (float)t.g[(size_t)(2 * gk + 1) * p.n_theta + j]);
+    cg[c][kind][tx] = cmul(make_float2((float)cr, (float)ci), g);
+    if (tx == 0) cz[c][kind] = cr == 0.0 && ci == 0.0;
   }
   __syncthreads();
-  const int nP = 2 * p.m_max + 1, Me = ord[e];
+  const int Me = ord[e];
   const bool ok = et.valid[e] != 0;
   const int L = p.m_max + 2;
-  for (int o = threadIdx.x; o < 3 * p.n_ord; o += blockDim.x) {
-    const int c = o / p.n_ord, li = o - c * p.n_ord, l = li - L;
-    float2 acc = make_float2(0.f, 0.f);
+  float vmax = 0.f;
+  if (jin)
+    for (int o = ty; o < 3 * p.n_ord; o += 8) {
+      const int c = o / p.n_ord, li = o - c * p.n_ord, l = li - L;
+      float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int kind = 0; kind < 5; ++kind) {
-      const int m = l + kind_shift(kind);
-      if (m < -Me || m > Me) continue;
-      if (cz[c][kind]) continue;
-      const float2 pm = Pm[((size_t)e * nP + m + p.m_max) * p.n_theta + j];
-      const float2 v = cmul(cg[c][kind], pm);
-      acc.x += v.x;
-      acc.y += v.y;
+      for (int kind = 0; kind < 5; ++kind) {
+        const int m = l + kind_shift(kind);
+        if (m < -Me || m > Me) continue;
+        if (cz[c][kind]) continue;
+        const float2 v = cmul(cg[c][kind][tx], pcol[m + p.m_max][tx]);
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+      if (l < 0 && ((-l) & 1)) acc = make_float2(-acc.x, -acc.y);   // J_{-n} = (-1)^n J_n
+      if (!ok) acc = make_float2(0.f, 0.f);
+      Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j] = acc;
+      vmax = fmaxf(vmax, fmaxf(fabsf(acc.x), fabsf(acc.y)));
     }
-    if (l < 0 && ((-l) & 1)) acc = make_float2(-acc.x, -acc.y);   // J_{-n} = (-1)^n J_n
-    if (!ok) acc = make_float2(0.f, 0.f);
-    Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j] = acc;
-    if (bh_max) atomicMax(bh_max, __float_as_uint(fmaxf(fabsf(acc.x), fabsf(acc.y))));
+  if (bh_max) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+      vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    if (tx == 0) atomicMax(bh_max, __float_as_uint(vmax));   // vmax >= 0
   }
 }
 
@@ -229,21 +249,26 @@ __global__ void k_harm_jtab(HarmParams p, ThetaTable t, float* __restrict__ Jt,
 
 // Split B operand of the tensor-core contraction for the slices [s0, s0+ns):
 // rows (l', 3 sl + c, re/im), 2 * 3 ns rows per order, value
-// S_F D[sl][j] Bh[e][c][l'][j] split hi + lo; S_F is the power of two that
+// S_F D[sl][j] Bh[e][c][l'][j] split into FP16 hi + lo; S_F is the power of two that
 // keeps max |Bh| below 2^14.  Only (order, slice) pairs the epilogue reads
 // (valid emitter, |l| <= M_e + 2) are written.  Block (64, 4): one
 // (order, slice) pair per threadIdx.y, four theta nodes per thread.
 constexpr int HB_TX = 64, HB_TY = 4;
 
-PSF_D uint2 pack4h(const uint16_t (&v)[4]) {
-  return make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
-                    (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+// hi + lo FP16 parts of two values as packed pairs (low half = a): the same
+// rounding as a scalar split, two conversions per instruction
+PSF_D void split_pair16(float a, float b, uint32_t& h, uint32_t& l) {
+  const __half2 hh = __floats2half2_rn(a, b);
+  const float2 back = __half22float2(hh);
+  const __half2 ll = __floats2half2_rn(a - back.x, b - back.y);
+  h = *reinterpret_cast<const uint32_t*>(&hh);
+  l = *reinterpret_cast<const uint32_t*>(&ll);
 }
 
 __global__ void __launch_bounds__(HB_TX * HB_TY)
 k_harm_bgen(HarmParams p, const float2* __restrict__ Bh, const float2* __restrict__ D,
             const int* __restrict__ slice_em, const int* __restrict__ valid,
-            const int* __restrict__ ord, int s0, int ns, int kp, int bf16,
+            const int* __restrict__ ord, int s0, int ns, int kp,
             const unsigned* __restrict__ bh_max, float sA, uint16_t* __restrict__ b_hi,
             uint16_t* __restrict__ b_lo, float* __restrict__ out_scale) {
   const float bm = __uint_as_float(*bh_max);
@@ -257,7 +282,7 @@ k_harm_bgen(HarmParams p, const float2* __restrict__ Bh, const float2* __restric
   if (e < 0 || !valid[e] || n > ord[e] + 2) return;
   const float2* d = D + (size_t)sl * p.n_theta;
   for (int q = threadIdx.x; q < (kp >> 2); q += HB_TX) {
-    uint16_t h[3][2][4], l[3][2][4];
+    float2 v[3][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = 4 * q + u;
@@ -265,23 +290,24 @@ k_harm_bgen(HarmParams p, const float2* __restrict__ Bh, const float2* __restric
       const float2 dj = in ? d[j] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        float2 v = make_float2(0.f, 0.f);
-        if (in) {
-          const float2 b = Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j];
-          v = cmul(dj, b);
-        }
-        tc::split16(sF * v.x, bf16, h[c][0][u], l[c][0][u]);
-        tc::split16(sF * v.y, bf16, h[c][1][u], l[c][1][u]);
+        float2 x = make_float2(0.f, 0.f);
+        if (in) x = cmul(dj, Bh[(((size_t)e * 3 + c) * p.n_ord + li) * p.n_theta + j]);
+        v[c][u] = make_float2(sF * x.x, sF * x.y);
       }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ri = 0; ri < 2; ++ri) {
-        const size_t row = (size_t)li * 6 * ns + (size_t)(3 * sl + c) * 2 + ri;
-        *reinterpret_cast<uint2*>(b_hi + row * kp + 4 * q) = pack4h(h[c][ri]);
-        *reinterpret_cast<uint2*>(b_lo + row * kp + 4 * q) = pack4h(l[c][ri]);
-      }
+    for (int c = 0; c < 3; ++c) {
+      const size_t row = (size_t)li * 6 * ns + (size_t)(3 * sl + c) * 2;
+      uint2 hr, lr, hm, lm;
+      split_pair16(v[c][0].x, v[c][1].x, hr.x, lr.x);
+      split_pair16(v[c][2].x, v[c][3].x, hr.y, lr.y);
+      split_pair16(v[c][0].y, v[c][1].y, hm.x, lm.x);
+      split_pair16(v[c][2].y, v[c][3].y, hm.y, lm.y);
+      *reinterpret_cast<uint2*>(b_hi + row * kp + 4 * q) = hr;
+      *reinterpret_cast<uint2*>(b_lo + row * kp + 4 * q) = lr;
+      *reinterpret_cast<uint2*>(b_hi + (row + 1) * kp + 4 * q) = hm;
+      *reinterpret_cast<uint2*>(b_lo + (row + 1) * kp + 4 * q) = lm;
+    }
   }
 }
 
@@ -800,7 +826,8 @@ void launch_harm_pupil(const HarmParams& p, ThetaTable t, EmitterTable e, const 
       p, t, e, zern, Zr, cs, Pm);
   k_harm_order<<<p.n_em, 256, 0, s>>>(p, Pm, ord);
   if (bh_max) cudaMemsetAsync(bh_max, 0, sizeof(unsigned), s);
-  k_harm_mix<<<dim3(p.n_em, p.n_theta), 128, 0, s>>>(p, t, e, Pm, ord, Bh, bh_max);
+  k_harm_mix<<<dim3(p.n_em, ceil_div(p.n_theta, HM_NODES)), 256, 0, s>>>(p, t, e, Pm, ord, Bh,
+                                                                         bh_max);
 }
 
 void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, const TcHarm* tc_ops,
@@ -819,13 +846,13 @@ void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, const TcHarm
 void launch_harm_operands(const HarmParams& p, ThetaTable t, const float2* Bh,
                           const int* slice_em, const int* valid, const int* ord,
                           const float2* zz, int s0, int ns, float2* D, const TcHarm& ops,
-                          float sA, int bf16, cudaStream_t s) {
+                          float sA, cudaStream_t s) {
   const long long nd = (long long)ns * p.n_theta;
   k_harm_defocus<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(p.n_theta, t, zz, s0, ns, D);
   const long long pairs = (long long)p.n_ord * ns;
   k_harm_bgen<<<(unsigned)((pairs + HB_TY - 1) / HB_TY), dim3(HB_TX, HB_TY), 0, s>>>(
-      p, Bh, D, slice_em, valid, ord, s0, ns, ops.kp, bf16, ops.bh_max, sA, ops.B_hi,
-      ops.B_lo, ops.out_scale);
+      p, Bh, D, slice_em, valid, ord, s0, ns, ops.kp, ops.bh_max, sA, ops.B_hi, ops.B_lo,
+      ops.out_scale);
   const int cpt = tc_harm_cols_per_tile();
   const int n_tiles = ceil_div(3 * ns, cpt);
   const long long nf = (long long)p.n_ord * n_tiles;

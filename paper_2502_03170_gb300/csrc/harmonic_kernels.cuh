@@ -60,7 +60,7 @@ void launch_harm_jtab(const HarmParams& p, ThetaTable t, float* Jt, const TcHarm
 void launch_harm_operands(const HarmParams& p, ThetaTable t, const float2* Bh,
                           const int* slice_em, const int* valid, const int* ord,
                           const float2* zz, int s0, int ns, float2* D, const TcHarm& ops,
-                          float sA, int bf16, cudaStream_t s);
+                          float sA, cudaStream_t s);
 
 // Profiles of the slices [s0, s0 + ns) (D: scratch [ns][n_theta] for the
 // defocus phasors e^{i k z_s cos theta_j}):

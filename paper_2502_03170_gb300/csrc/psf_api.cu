@@ -1563,7 +1563,7 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
       {
         TimingScope ts(kTimeSetup, s);
         launch_harm_operands(hp, R.tt, H.Bh, H.b.slice_em, H.b.et.valid, H.ord, H.b.zz, s0,
-                             ns, H.D, H.tc, sA, bf16, s);
+                             ns, H.D, H.tc, sA, s);
       }
       TimingScope ts(kTimeBesselRadial, s);
       if ((r = tc_harm_contract(H.tc, n_theta, n_r, m_max, 3 * ns, precision, H.prof,
