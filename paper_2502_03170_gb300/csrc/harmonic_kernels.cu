@@ -1,6 +1,8 @@
-// Azimuthal-harmonic (non-axisymmetric) Bessel strategy: pupil harmonics,
-// J_n table, batched radial contraction per order and the Cartesian
-// epilogue (FP32 arithmetic, FP64 tables).
+// Azimuthal-harmonic (non-axisymmetric) Bessel strategy: pupil harmonics by
+// FFT, the per-emitter adaptive order, the channel/order mixtures, the J_n
+// table, the FP32 per-order radial contraction (or the split operands of the
+// tensor-core contraction, mode 5 of the persistent GEMM) and the Cartesian
+// epilogues (FP32 arithmetic, FP64 tables).
 #include "harmonic_kernels.cuh"
 #include "tc_ptx.cuh"
 

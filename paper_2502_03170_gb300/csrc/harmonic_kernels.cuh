@@ -9,9 +9,10 @@
 //   Bh_{c,l} = sum over the five kinds of coef[c][kind] g_kind P_{l+shift},
 //   kinds (g_0, P_l), (g_2, P_{l-2}), (g_2, P_{l+2}), (g_1, P_{l-1}),
 //   (g_1, P_{l+1}); J_{-l} = (-1)^l J_l is folded into Bh.
-// P_m is a DFT over N_phi = 4 * pow2ceil(M + 1) azimuths of the
-// non-axisymmetric part, times the axisymmetric integrand of the emitter
-// table (A e^{i (W_GL + m = 0 Zernike)}).
+// P_m is a DFT (computed by FFT) over N_phi = 4 * pow2ceil(M + 1) azimuths
+// of the non-axisymmetric part, times the axisymmetric integrand of the
+// emitter table (A e^{i (W_GL + m = 0 Zernike)}); each emitter then keeps
+// the harmonics up to its adaptive order M_e.
 #pragma once
 
 #include "bessel_kernels.cuh"
