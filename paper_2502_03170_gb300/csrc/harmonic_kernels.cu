@@ -768,11 +768,13 @@ k_harm_intensity_oct(HarmParams p, const float2* __restrict__ prof,
       tn = cmul(tn, wc);
       pp += stride;
       pm -= stride;
-      ++nn;
-      const int ahead = min(kHarmPrefetch, Le - nn);
-      if (!staged && ahead > 0) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + (size_t)ahead * n_r));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(pm - (size_t)ahead * n_r));
+      if (!staged) {
+        ++nn;
+        const int ahead = min(kHarmPrefetch, Le - nn);
+        if (ahead > 0) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + (size_t)ahead * n_r));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pm - (size_t)ahead * n_r));
+        }
       }
     };
     for (int n0 = 0; n0 <= Le; n0 += 4) {
