@@ -33,6 +33,7 @@ itself: the Airy closed form (Eq. 18), the Fourier-Bessel equivalence theorem
 (Sec. 4.1), the continuum quadrature, axial / rotational symmetry, discrete
 Parseval energy, Zernike orthonormality, Gauss-Legendre exactness, the
 paraxial Gibson-Lanni expansion and finite differences for the gradient.
-The MLP oracle is pinned by finite differences only; its agreement with the
-paper is "parity unpinned" (the paper has no surrogate).
+The MLP oracle is pinned by finite differences, PyTorch's FP64 autograd and
+torch.optim.Adam; its agreement with the paper is "parity unpinned" (the
+paper has no surrogate).
 """

@@ -14,7 +14,8 @@ error of the output.  Losses (per batch of B samples):
 gradients), so GPU results can be compared element by element; with
 ``emulate=False`` everything stays in FP64 (the finite-difference pins use
 that form).  The surrogate is not part of the paper, so its agreement with
-the paper is "parity unpinned"; finite differences pin the gradients.
+the paper is "parity unpinned"; finite differences and PyTorch's FP64
+autograd pin the gradients, torch.optim.Adam the update.
 """
 import numpy as np
 
