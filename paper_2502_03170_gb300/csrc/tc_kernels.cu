@@ -1410,13 +1410,15 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
     p2.n_rows = ny;
     p2.mode = 1;
     p2.out_scale = scale / (sA * sU);
-    const int buf = (z0 / zc) & 1;
+    const int ci = z0 / zc, buf = ci & 1;
     const size_t plane = (size_t)nx * ny;
     if (cps) {
       // `intensity` is the two-chunk staging area; wait until the copy of
-      // chunk i - 2 has left this buffer
+      // chunk i - 2 of this call has left this buffer (only events recorded
+      // in this call are waited on, so the call holds no dependency on an
+      // earlier one)
       p2.I = intensity + (size_t)buf * zc * plane;
-      cudaStreamWaitEvent(s, cps->copied[buf], 0);
+      if (ci >= 2) cudaStreamWaitEvent(s, cps->copied[buf], 0);
     } else {
       p2.I = intensity + (size_t)z0 * plane;
     }
@@ -1443,8 +1445,9 @@ int tc_fourier_forward(const TcOperands& ops, NodeTable nodes, const float2* zz,
   }
   if (cps) {
     // the call completes on the caller's stream once the stack is on the host
-    cudaStreamWaitEvent(s, cps->copied[0], 0);
-    cudaStreamWaitEvent(s, cps->copied[1], 0);
+    const int n_chunks = (nz + zc - 1) / zc;
+    if (n_chunks >= 1) cudaStreamWaitEvent(s, cps->copied[0], 0);
+    if (n_chunks >= 2) cudaStreamWaitEvent(s, cps->copied[1], 0);
   }
   return PSF_OK;
 }
