@@ -72,26 +72,48 @@ def fourier_loss_grad(optics, n_pupil, grid, zernike, phase_map, target,
 
 
 class FourierPSF(torch.autograd.Function):
-    """I = psf(W_0, c) for one pupil; differentiable in W_0 and c."""
+    """I = psf(W_0, c) for a batch of pupils, differentiable in W_0 and c.
+
+    phase_map [B, N, N] (or [N, N]) in radians on the device, zernike
+    [B, n_zern] (or [n_zern]; n_zern may be 0).  Returns I [B, nz, nx, ny]
+    (or [nz, nx, ny] for unbatched inputs).  The backward runs the adjoint of
+    Eq. 8 in the forward's precision: the split modes recompute each plane's
+    fields with the tensor-core contractions of the forward and contract the
+    adjoint on the tensor cores as well; fp32 runs both in FP32."""
 
     @staticmethod
     def forward(ctx, phase_map, zernike, optics, n_pupil, grid, precision):
-        I = api.fourier(optics, n_pupil, grid,
-                        zernike=zernike.detach().cpu().numpy(),
-                        phase_map=phase_map.detach(), precision=precision)
-        ctx.save_for_backward(phase_map, zernike)
-        ctx.cfg = (optics, n_pupil, grid, precision)
-        return I
+        batched = phase_map.dim() == 3
+        pm = phase_map.detach() if batched else phase_map.detach()[None]
+        zc = zernike.detach() if zernike.dim() == 2 else zernike.detach()[None]
+        if zc.shape[0] != pm.shape[0]:
+            raise ValueError("zernike and phase_map batch sizes differ")
+        B = pm.shape[0]
+        g = grid if isinstance(grid, api.Grid) else api.Grid(grid)
+        zh = np.ascontiguousarray(zc.cpu().numpy(), dtype=np.float64)
+        I = torch.empty((B, g.c.nz, g.c.nx, g.c.ny), dtype=torch.float32, device=pm.device)
+        ws = api.Workspace(pm.device)
+        for b in range(B):
+            api.fourier(optics, n_pupil, g, zernike=zh[b] if zh.shape[1] else None,
+                        phase_map=pm[b], precision=precision, out=I[b], workspace=ws)
+        ctx.save_for_backward(pm, zc)
+        ctx.cfg = (optics, n_pupil, g, precision, batched, zernike.dim())
+        return I if batched else I[0]
 
     @staticmethod
     def backward(ctx, grad_I):
-        phase_map, zernike = ctx.saved_tensors
-        optics, n_pupil, grid, precision = ctx.cfg
-        _, gW, gc = _backward_call(optics, n_pupil, grid, zernike[None, :],
-                                   phase_map[None], grad_I=grad_I[None],
-                                   precision="fp32", want_loss=False)
-        gz = gc[0].to(dtype=zernike.dtype, device=zernike.device)
-        return gW[0].to(phase_map.dtype), gz, None, None, None, None
+        pm, zc = ctx.saved_tensors
+        optics, n_pupil, g, precision, batched, zdim = ctx.cfg
+        G = (grad_I if batched else grad_I[None]).to(torch.float32).contiguous()
+        _, gW, gc = _backward_call(optics, n_pupil, g, zc, pm, grad_I=G,
+                                   precision=precision, want_loss=False)
+        gz = torch.zeros_like(zc) if gc is None else gc.to(dtype=zc.dtype, device=zc.device)
+        gp = gW.to(pm.dtype)
+        if not batched:
+            gp = gp[0]
+        if zdim == 1:
+            gz = gz[0]
+        return gp, gz, None, None, None, None
 
 
 def fourier_psf(phase_map, zernike, optics, n_pupil, grid, precision="fp32"):

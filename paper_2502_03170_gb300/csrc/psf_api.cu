@@ -228,7 +228,9 @@ struct FourierLayout {
   float2* zz;
   float2 *Ax, *Ay;
   float2 *P, *U;       // FP32 path
-  TcOperands tc;       // split-precision path
+  TcOperands tc;       // split-precision path, unfolded contraction
+  TcFoldOperands fold; // split-precision path, symmetry-folded contraction
+  bool fold_path;
   float2* czt_words;   // chirp-Z path: x tables | y tables
   size_t czt_wx, czt_wy;
   float2* T;           // chirp-Z stage-1 output [zc][3][ny][N]
@@ -246,6 +248,14 @@ static int czt_zchunk(int N, int ny, int nz) {
   if (zc > 256) zc = 256;
   if (zc > nz) zc = nz;
   return zc;
+}
+
+// The split precisions run the symmetry-folded contractions (a quarter of the
+// multiply-adds of the unfolded 2x2-block form); PSF_TC_FOLD=0 in the
+// environment selects the unfolded form (same discrete sums, other rounding).
+static bool fold_enabled() {
+  const char* e = getenv("PSF_TC_FOLD");
+  return !(e && e[0] == '0');
 }
 
 // max_planes caps the z-chunk (the call shortens its chunks to fit a smaller
@@ -274,6 +284,10 @@ static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
     L.Ay = c.take<float2>((size_t)g->ny * N);
     L.P = c.take<float2>((size_t)L.zc * 3 * NN);
     L.U = c.take<float2>((size_t)L.zc * 3 * g->ny * N);
+  } else if (fold_enabled()) {
+    L.fold_path = true;
+    L.zc = capped(tc_fold_zchunk(N, g->nx, g->ny, g->nz));
+    tc_fold_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.fold);
   } else {
     L.zc = capped(tc_fourier_zchunk(N, g->nx, g->ny, g->nz));
     tc_fourier_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.tc);
@@ -518,6 +532,12 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
                           fz, N, grid->nx, grid->ny, nzc, scale, s);
       }
     }
+  } else if (L.fold_path) {
+    r = tc_fold_forward(L.fold, L.nodes, L.zz, N, grid->nx, grid->ny, grid->dx, grid->dy,
+                        grid->nz, L.zc, f, scale, tc_pupil_amplitude_bound(np), precision,
+                        host_out ? stage : intensity, (float2*)fields, host_out,
+                        (int*)workspace, s);
+    if (r) return fail(r, "split-precision (folded) launch failed");
   } else {
     r = tc_fourier_forward(L.tc, L.nodes, L.zz, N, grid->nx, grid->ny, grid->dx,
                            grid->dy, grid->nz, L.zc, f, scale,

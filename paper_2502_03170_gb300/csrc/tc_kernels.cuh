@@ -83,6 +83,32 @@ struct TcOperands {
   uint16_t *U_hi, *U_lo;     // [zc][3][ny][2 N] stage-1 output
 };
 
+// Operands of the symmetry-folded forward (fold_kernels.cu), 16-bit, split
+// hi + lo, row pitch Kp = H rounded up to 16 (H = N/2):
+//   Zx, Zy  zoom halves C = cos, S = sin over the first half p' < H of the
+//           pupil and the first half of the outputs: [4][ceil(n/2)][Kp] with
+//           the variants C hi, C lo, S hi, S lo;
+//   P       pupil parity classes of a z-chunk: [zc][3][parity][re/im] slabs
+//           of [4][H][Kp] with the variants X hi, X lo (q-even sum), Y hi,
+//           Y lo (q-odd difference);
+//   U       the p-folded stage-1 output: [zc][4][ny][3][re/im][Kp] with the
+//           variants T+ hi, T+ lo, T- hi, T- lo.
+struct TcFoldOperands {
+  int H, Kp;
+  uint16_t *Zx, *Zy, *P, *U;
+};
+int tc_fold_kp(int N);
+const char* tc_fold_supported(int N, int nx, int ny);
+int tc_fold_zchunk(int N, int nx, int ny, int nz);
+void tc_fold_carve(char* base, size_t* off, int N, int nx, int ny, int zc, TcFoldOperands* out);
+// The folded forward over z-chunks of zc planes; arguments as
+// tc_fourier_forward.  Returns PSF_ERR_CUDA when a launch is refused.
+int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz, int N,
+                    int nx, int ny, double dx, double dy, int nz, int zc,
+                    double na_over_lambda, float scale, double amp_bound, int precision,
+                    float* intensity, float2* fields, float* host_out, int* status,
+                    cudaStream_t s);
+
 // nullptr if (N, nx, ny) can run on the split-precision path, else a reason.
 const char* tc_fourier_supported(int N, int nx, int ny);
 

@@ -1,6 +1,6 @@
 """Small, self-contained invocations of single hot kernels for profiling.
 
-    python -m paper_2502_03170_gb300.profile_cases <case> [--precision P] [--nz NZ]
+    python profile_cases.py <case> [--precision P] [--nz NZ]
 
 Each case runs one warm-up call and one measured call of the library on
 cuda:0 with sizes small enough for a full ncu capture (well under a few GB on
@@ -21,12 +21,16 @@ the device), then exits.  Cases:
   split_fp16`` puts the radial contraction on the tensor cores.
 """
 import argparse
+import os
+import sys
 
 import numpy as np
 import torch
 
-from . import _lib, api
-from . import workloads as W
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+from paper_2502_03170_gb300 import _lib, api  # noqa: E402
+from paper_2502_03170_gb300 import workloads as W  # noqa: E402
 
 
 def main():
@@ -54,7 +58,7 @@ def main():
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
     elif args.case == "fourier_backward":
-        from . import autograd
+        from paper_2502_03170_gb300 import autograd
         c = W.adjoint(batch=args.batch)
         g = c["grid"]
         nz, nx, ny = len(g["z"]), g["nx"], g["ny"]

@@ -223,3 +223,56 @@ def test_backward_chunking_is_invisible(lib, use_target):
                                 ws_bytes=ws_bytes))
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16", "split_bf16"])
+def test_fourier_autograd_function(lib, prec):
+    """torch.autograd through fourier_psf for a batch of two pupils: the
+    gradient of sum (I - T)^2 with respect to the phase maps and the Zernike
+    rows against the FP64 oracle adjoint (pinned by finite differences on the
+    CPU), in the forward's precision; the forward stack against the oracle
+    forward."""
+    from paper_2502_03170_gb300 import autograd as ag
+
+    from .gpu_helpers import max_rel
+    rng = np.random.default_rng(3)
+    N, nx, ny, nz, B = 32, 16, 24, 3, 2
+    d = W.optics_gibson_lanni(1.0)
+    grid = dict(nx=nx, ny=ny, dx=0.04, dy=0.035, z=np.linspace(-0.5, 0.4, nz))
+    zern = np.zeros((B, 21))
+    zern[:, 3:15] = rng.normal(0, 0.2, (B, 12))
+    pm = np.where(pupil_mask(N), rng.normal(0, 0.3, (B, N, N)), 0.0)
+    T = rng.uniform(0, 2e-4, (B, nz, nx, ny))
+    pm_t = torch.tensor(pm, dtype=torch.float32, device="cuda", requires_grad=True)
+    zc_t = torch.tensor(zern, dtype=torch.float64, device="cuda", requires_grad=True)
+    I = ag.fourier_psf(pm_t, zc_t, d, N, grid, precision=prec)
+    L = ((I - torch.tensor(T, dtype=torch.float32, device="cuda")) ** 2).sum()
+    gW, gc = torch.autograd.grad(L, (pm_t, zc_t))
+    opt = oracle_optics(d)
+    tol_f = 1e-5
+    for b in range(B):
+        _, gWr, gcr, Ir = oa.loss_and_grad(opt, N, grid, zern[b], pm[b], T[b])
+        assert max_rel(I[b].detach().cpu().numpy(), Ir) <= tol_f
+        assert rel_l2(gW[b].cpu().numpy(), gWr) <= TOL_G
+        assert rel_l2(gc[b].cpu().numpy(), gcr) <= TOL_G
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16"])
+def test_fourier_autograd_without_zernike_terms(lib, prec):
+    """An unbatched pupil with an empty Zernike vector: the phase-map
+    gradient against the oracle adjoint, a zero-length Zernike gradient."""
+    from paper_2502_03170_gb300 import autograd as ag
+    rng = np.random.default_rng(9)
+    N, nx, ny, nz = 32, 16, 16, 2
+    d = W.optics_plain()
+    grid = dict(nx=nx, ny=ny, dx=0.04, dy=0.04, z=[-0.3, 0.25])
+    pm = np.where(pupil_mask(N), rng.normal(0, 0.3, (N, N)), 0.0)
+    T = rng.uniform(0, 2e-4, (nz, nx, ny))
+    pm_t = torch.tensor(pm, dtype=torch.float32, device="cuda", requires_grad=True)
+    zc_t = torch.zeros(0, dtype=torch.float64, device="cuda", requires_grad=True)
+    I = ag.fourier_psf(pm_t, zc_t, d, N, grid, precision=prec)
+    L = ((I - torch.tensor(T, dtype=torch.float32, device="cuda")) ** 2).sum()
+    gW, gc = torch.autograd.grad(L, (pm_t, zc_t))
+    assert gc.shape == (0,)
+    _, gWr, _, _ = oa.loss_and_grad(oracle_optics(d), N, grid, None, pm, T, n_zern=0)
+    assert rel_l2(gW.cpu().numpy(), gWr) <= TOL_G

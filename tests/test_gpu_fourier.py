@@ -105,11 +105,13 @@ def test_rejects_bad_arguments(lib):
 
 @pytest.mark.parametrize("nx,ny,N", [(150, 72, 48), (512, 512, 256)])
 def test_cta_pair_kernel_matches_single_cta(lib, nx, ny, N, monkeypatch):
-    """The CTA-pair contraction (default) and the single-CTA kernel compute
-    the same products in the same order: bitwise equal stacks, also with an
-    odd number of 64-row output tiles (the peer of the last pair has none)."""
+    """The unfolded contraction (PSF_TC_FOLD=0) on CTA pairs and on single
+    CTAs computes the same products in the same order: bitwise equal stacks,
+    also with an odd number of 64-row output tiles (the peer of the last
+    pair has none)."""
     c = W.fourier(n_pupil=N, nx=nx, nz=6)
     grid = dict(c["grid"], ny=ny)
+    monkeypatch.setenv("PSF_TC_FOLD", "0")
     out = {}
     for mode in ("1", "0"):
         monkeypatch.setenv("PSF_TC_PAIR", mode)
@@ -226,3 +228,28 @@ def test_forward_in_a_cuda_graph(lib, to_host):
     graph.replay()
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), I_dev.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["split_fp16", "split_bf16"])
+@pytest.mark.parametrize("N,nx,ny,nz", [(16, 5, 7, 2), (24, 3, 1, 2), (136, 37, 29, 3),
+                                        (40, 20, 33, 2), (64, 300, 258, 3), (256, 512, 512, 4)])
+def test_folded_matches_unfolded_and_oracle(lib, prec, N, nx, ny, nz, monkeypatch):
+    """The symmetry-folded contractions (default split path) against the
+    unfolded 2x2-block form and the FP64 oracle: odd output sizes (a pixel
+    on the axis, mirrored onto itself), a single row, K not a multiple of
+    the 64-wide stage (N = 136: 68 folded columns), several output tiles."""
+    g = np.random.default_rng(N + 7 * nx)
+    d = W.optics_gibson_lanni(1.0)
+    d["pol"] = (0.8, 0.36 + 0.48j)
+    zern = np.zeros(21)
+    zern[1:21] = g.normal(0, 0.12, 20)
+    pm = g.normal(0, 0.3, (N, N))
+    grid = dict(nx=nx, ny=ny, dx=0.019, dy=0.021, z=np.sort(g.uniform(-1.0, 1.0, nz)))
+    I_f, F_f = run_case(d, N, grid, zern, pm, precision=prec)
+    monkeypatch.setenv("PSF_TC_FOLD", "0")
+    I_u, _ = run_case(d, N, grid, zern, pm, precision=prec)
+    E = of.field_separable(oracle_optics(d), N, grid, zernike=zern, phase_map=pm)
+    Ir = of.intensity(E)
+    assert max_rel(I_f, Ir) <= TOL[prec]
+    assert max_rel(F_f, E) <= TOL[prec]
+    assert max_rel(I_f, I_u) <= 2 * TOL[prec]
