@@ -80,6 +80,30 @@ extern "C" {
                                    L = 2^k >= max(256, n_pupil + n_out - 1),
                                    L <= 4096 per direction; same discrete sum
                                    as PSF_PREC_FP32, O(L log L) per line      */
+#define PSF_PREC_AUTO        4  /* the fastest mode inside the accuracy
+                                   envelope below: Fourier forward split FP16
+                                   (n_pupil <= 512), else split BF16 (<= 1024),
+                                   else chirp-Z when its FFT length fits, else
+                                   FP32; spherical forwards split FP16 (n_theta
+                                   <= 448), else FP32; adjoints split FP16
+                                   where the tensor-core adjoint runs, else
+                                   FP32                                       */
+
+/* ---- accuracy envelope of the split modes ---------------------------------
+ * Every forward call is meant to stay within 1e-5 (max |I - I_ref| over max
+ * |I_ref| of the stack) of the FP64 oracle of the same discrete sums.  The
+ * split modes round each operand to hi + lo 16-bit parts and accumulate in
+ * FP32 on the tensor cores; their error grows with the length of each
+ * contraction.  A forward call in a split mode is refused with
+ * PSF_ERR_PRECISION (before any launch) outside the sizes where the error
+ * measured on the benchmark workloads (Gibson-Lanni + Noll 4..21, 512^2 px)
+ * stays within half the bound:
+ *   Fourier   split FP16  n_pupil <= 512   (4.3e-6 at 512; 8.7e-6 at 1024)
+ *             split BF16  n_pupil <= 1024  (4.2e-6 at 1024; 7.6e-6 at 2048)
+ *   Bessel /  split FP16  n_theta <= 448   (5.2e-6 at 448; 9.9e-6 at 880)
+ *   harmonic  split BF16  refused          (5.2e-5 on the Bessel workload)
+ * FP32 and chirp-Z stay below 2e-6 at every size.  The adjoints (gradient
+ * bound 1e-4 relative L2) take every mode they support.                      */
 
 /* ---- flags ---------------------------------------------------------------- */
 #define PSF_PROJECT_AXISYMMETRIC 1  /* Bessel path: drop m != 0 Zernike terms
@@ -177,7 +201,10 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
  *     PSF_ERR_WORKSPACE and a message giving both sizes; nothing is launched.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: a cudaDeviceReset() between calls is not supported (the
+ *     array's memory would be gone while the library still holds its
+ *     address).
  *   - All calls share the one array and it keeps the previous call's
  *     contents; every call rewrites what it reads.  Calls whose executions
  *     overlap on the GPU (other streams, other host threads) race on the

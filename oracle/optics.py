@@ -1,7 +1,7 @@
 """Optical model pieces shared by every oracle strategy (FP64, test-only).
 
-Conventions (each is a reading of the paper, listed with its reason in the
-design notes):
+Conventions (each is a reading of the paper where it is silent or
+ambiguous):
 
 * k = 2*pi*n_i/lambda: theta is defined in the immersion medium (Sec. 3.1).
 * The prefactor f*k of Eq. 1 is set to 1, so the Cartesian form carries

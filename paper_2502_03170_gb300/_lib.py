@@ -21,6 +21,7 @@ PSF_PREC_FP32 = 0
 PSF_PREC_SPLIT_FP16 = 1
 PSF_PREC_SPLIT_BF16 = 2
 PSF_PREC_FP32_CHIRPZ = 3
+PSF_PREC_AUTO = 4
 
 PSF_PROJECT_AXISYMMETRIC = 1
 PSF_SCALAR = 2

@@ -14,7 +14,7 @@ from ._lib import PsfGrid, PsfOptics, check
 
 PRECISIONS = {"fp32": _lib.PSF_PREC_FP32, "split_fp16": _lib.PSF_PREC_SPLIT_FP16,
               "split_bf16": _lib.PSF_PREC_SPLIT_BF16,
-              "chirpz_fp32": _lib.PSF_PREC_FP32_CHIRPZ}
+              "chirpz_fp32": _lib.PSF_PREC_FP32_CHIRPZ, "auto": _lib.PSF_PREC_AUTO}
 
 
 def make_optics(d, flags=0):
@@ -64,6 +64,11 @@ def _ptr(t):
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def _raise_code(lib, code):
+    """Raises the error of a call that was refused before any launch."""
+    raise _lib.PsfError(code if code else _lib.PSF_ERR_ARG, lib.psf_last_error().decode())
 
 
 def _zern_host(zernike):
@@ -172,15 +177,18 @@ def bessel_harmonic(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, 
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     need = lib.psf_bessel_harmonic_workspace_size(ctypes.byref(o), a.n_em, a.n_slices,
                                                   n_theta, n_r, nx, ny, int(m_max), prec)
+
+    def call(I, buf, nbytes):
+        return lib.psf_bessel_vectorial_harmonic(
+            ctypes.byref(o), a.n_em, _ptr(a.depth), _ptr(a.zern), a.n_zern, _ptr(a.offs),
+            _ptr(a.z), a.n_slices, n_theta, n_r, nx, ny, float(dx), float(dy), int(m_max),
+            float(tail_tol), prec, _ptr(I), _ptr(buf), nbytes, _stream(stream))
     if need == 0:
-        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+        _raise_code(lib, call(None, None, 0))
     buf = ws.get(need)
     I = out if out is not None else torch.empty((a.n_slices, nx, ny), dtype=torch.float32,
                                                 device=dev)
-    check(lib, lib.psf_bessel_vectorial_harmonic(
-        ctypes.byref(o), a.n_em, _ptr(a.depth), _ptr(a.zern), a.n_zern, _ptr(a.offs),
-        _ptr(a.z), a.n_slices, n_theta, n_r, nx, ny, float(dx), float(dy), int(m_max),
-        float(tail_tol), prec, _ptr(I), _ptr(buf), buf.numel(), _stream(stream)))
+    check(lib, call(I, buf, buf.numel()))
     return I
 
 
@@ -232,18 +240,23 @@ def bessel(optics, depth, zernike, z_offsets, z, n_theta, n_r, nx, ny, dx, dy,
     ws = workspace or Workspace(dev)
     need = lib.psf_bessel_workspace_size(ctypes.byref(o), n_em, n_slices,
                                          n_theta, n_r, nx, ny, prec)
+
+    def call(I, P, buf, nbytes):
+        return lib.psf_bessel_vectorial(
+            ctypes.byref(o), n_em, _ptr(depth_d), _ptr(zern_d), n_zern,
+            _ptr(a.phase), _ptr(offs_d), _ptr(z_d), n_slices, n_theta, n_r, nx, ny,
+            float(dx), float(dy), prec, _ptr(I), _ptr(P), _ptr(buf), nbytes,
+            _stream(stream))
     if need == 0:
-        raise _lib.PsfError(_lib.PSF_ERR_ARG, lib.psf_last_error().decode())
+        # invalid arguments: the call without a workspace returns their code
+        # (validated before anything is launched)
+        _raise_code(lib, call(None, None, None, 0))
     buf = ws.get(need)
     I = (out if out is not None else torch.empty((n_slices, nx, ny), dtype=torch.float32,
                                                  device=dev)) if intensity else None
     P = torch.empty((n_slices, 3, n_r), dtype=torch.complex64,
                     device=dev) if profiles else None
-    check(lib, lib.psf_bessel_vectorial(
-        ctypes.byref(o), n_em, _ptr(depth_d), _ptr(zern_d), n_zern,
-        _ptr(a.phase), _ptr(offs_d), _ptr(z_d), n_slices, n_theta, n_r, nx, ny,
-        float(dx), float(dy), prec, _ptr(I), _ptr(P), _ptr(buf), buf.numel(),
-        _stream(stream)))
+    check(lib, call(I, P, buf, buf.numel()))
     if not intensity:
         return P
     return (I, P) if profiles else I

@@ -46,6 +46,83 @@ static int cuda_check(const char* what) {
 
 static bool finite_pos(double v) { return isfinite(v) && v > 0; }
 
+// ---------------------------------------------------------------------------
+// Accuracy envelope of the split precisions.  A forward call in a split mode
+// is accepted only at sizes where its measured intensity error against the
+// FP64 oracle stays within half the 1e-5 bound on the benchmark workloads
+// (Gibson-Lanni + Noll 4..21, 512^2 px):
+//   Fourier, folded contractions: split FP16 4.3e-6 at n_pupil 512 (8.7e-6 at
+//     1024, 1.7e-5 at 2048); split BF16 4.2e-6 at 1024 (7.6e-6 at 2048);
+//   spherical (Bessel and harmonic) split FP16: 5.2e-6 at 448 Gauss-Legendre
+//     nodes (9.9e-6 at 880); split BF16 5.2e-5 on the Bessel workload.
+// The error grows with the contraction length (the K extent that each FP32
+// tensor-core accumulator sums).  PSF_PREC_AUTO picks the fastest mode that
+// stays inside.
+// ---------------------------------------------------------------------------
+constexpr int kSplitFp16MaxPupil = 512;
+constexpr int kSplitBf16MaxPupil = 1024;
+constexpr int kSplitMaxTheta = 448;
+
+static int fourier_envelope(int N, int precision) {
+  if (precision == PSF_PREC_SPLIT_FP16 && N > kSplitFp16MaxPupil)
+    return fail(PSF_ERR_PRECISION,
+                "split FP16 holds the 1e-5 bound up to n_pupil %d (measured 4.3e-6 at 512, "
+                "8.7e-6 at 1024); n_pupil %d: use PSF_PREC_SPLIT_BF16 (up to %d), "
+                "PSF_PREC_FP32_CHIRPZ, PSF_PREC_FP32 or PSF_PREC_AUTO",
+                kSplitFp16MaxPupil, N, kSplitBf16MaxPupil);
+  if (precision == PSF_PREC_SPLIT_BF16 && N > kSplitBf16MaxPupil)
+    return fail(PSF_ERR_PRECISION,
+                "split BF16 holds the 1e-5 bound up to n_pupil %d (measured 4.2e-6 at 1024, "
+                "7.6e-6 at 2048); n_pupil %d: use PSF_PREC_FP32_CHIRPZ, PSF_PREC_FP32 or "
+                "PSF_PREC_AUTO",
+                kSplitBf16MaxPupil, N);
+  return PSF_OK;
+}
+
+static int spherical_envelope(int n_theta, int precision) {
+  if (precision == PSF_PREC_SPLIT_BF16)
+    return fail(PSF_ERR_PRECISION,
+                "split BF16 keeps 16 significant bits per operand: 5.2e-5 from the FP64 "
+                "oracle on the Bessel workload, over the 1e-5 bound; use PSF_PREC_SPLIT_FP16, "
+                "PSF_PREC_FP32 or PSF_PREC_AUTO");
+  if (precision == PSF_PREC_SPLIT_FP16 && n_theta > kSplitMaxTheta)
+    return fail(PSF_ERR_PRECISION,
+                "split FP16 holds the 1e-5 bound up to %d theta nodes (measured 5.2e-6 at "
+                "448, 9.9e-6 at 880); n_theta %d: use PSF_PREC_FP32 or PSF_PREC_AUTO",
+                kSplitMaxTheta, n_theta);
+  return PSF_OK;
+}
+
+static int czt_fits(int N, int nx, int ny);   // defined with the Fourier strategy
+
+// PSF_PREC_AUTO of the Fourier forward: the dense split contraction inside
+// its envelope (FP16 up to n_pupil 512, BF16 up to 1024), else the chirp-Z
+// zoom when its FFT length fits, else FP32.
+static int resolve_fourier_precision(int N, int nx, int ny, int precision) {
+  if (precision != PSF_PREC_AUTO) return precision;
+  const bool tc = N % 8 == 0 && N >= 16;
+  if (tc && N <= kSplitFp16MaxPupil) return PSF_PREC_SPLIT_FP16;
+  if (tc && N <= kSplitBf16MaxPupil) return PSF_PREC_SPLIT_BF16;
+  if (czt_fits(N, nx, ny)) return PSF_PREC_FP32_CHIRPZ;
+  return PSF_PREC_FP32;
+}
+
+// PSF_PREC_AUTO of the spherical forwards: split FP16 inside its envelope.
+static int resolve_spherical_precision(int n_theta, int precision) {
+  if (precision != PSF_PREC_AUTO) return precision;
+  return n_theta <= kSplitMaxTheta ? PSF_PREC_SPLIT_FP16 : PSF_PREC_FP32;
+}
+
+// PSF_PREC_AUTO of the adjoints (gradient bound 1e-4): the tensor-core split
+// FP16 form wherever it runs.
+static int resolve_fourier_backward_precision(int N, int nx, int ny, int precision) {
+  if (precision != PSF_PREC_AUTO) return precision;
+  return tc_fourier_bwd_supported(N, nx, ny) ? PSF_PREC_FP32 : PSF_PREC_SPLIT_FP16;
+}
+static int resolve_bessel_backward_precision(int precision) {
+  return precision == PSF_PREC_AUTO ? PSF_PREC_SPLIT_FP16 : precision;
+}
+
 static int check_optics(const psf_optics* o) {
   if (!o) return fail(PSF_ERR_ARG, "optics is NULL");
   if (!finite_pos(o->NA) || !finite_pos(o->lambda) || !finite_pos(o->n_i))
@@ -238,6 +315,8 @@ struct FourierLayout {
   size_t bytes;
 };
 
+static int czt_fits(int N, int nx, int ny) { return czt_length(N, nx) && czt_length(N, ny); }
+
 static int czt_zchunk(int N, int ny, int nz) {
   // stage-1 output of a chunk up to 1 GB and 256 planes: longer launches
   // fill the GPU better than an L2-sized chunk (256^2 -> 512^2 x 128 planes:
@@ -407,7 +486,9 @@ int psf_workspace_status(const void* workspace, void* stream) {
 
 size_t psf_fourier_workspace_size(const psf_optics* opt, int n_pupil,
                                   const psf_grid* grid, int precision) {
+  if (grid) precision = resolve_fourier_precision(n_pupil, grid->nx, grid->ny, precision);
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
+  if (fourier_envelope(n_pupil, precision)) return 0;
   return fourier_layout(nullptr, n_pupil, grid, precision).bytes;
 }
 
@@ -417,8 +498,10 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
                           float* intensity, void* fields, void* workspace,
                           size_t ws_bytes, void* stream) {
   g_err[0] = 0;
+  if (grid) precision = resolve_fourier_precision(n_pupil, grid->nx, grid->ny, precision);
   int r = check_fourier_args(opt, n_pupil, grid, precision);
   if (r) return r;
+  if ((r = fourier_envelope(n_pupil, precision))) return r;
   if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
   if (n_zern > 0 && !zernike) return fail(PSF_ERR_ARG, "zernike is NULL");
   for (int j = 0; j < n_zern; ++j)
@@ -630,6 +713,8 @@ extern "C" size_t psf_fourier_backward_workspace_size(const psf_optics* opt,
                                                        int n_pupil,
                                                        const psf_grid* grid,
                                                        int precision) {
+  if (grid)
+    precision = resolve_fourier_backward_precision(n_pupil, grid->nx, grid->ny, precision);
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
   if (precision == PSF_PREC_FP32_CHIRPZ) return 0;
   if (precision != PSF_PREC_FP32 && tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
@@ -642,6 +727,7 @@ extern "C" size_t psf_fourier_backward_workspace_size_batch(const psf_optics* op
                                                              int precision, int batch) {
   const size_t base = psf_fourier_backward_workspace_size(opt, n_pupil, grid, precision);
   if (base == 0 || batch < 1) return 0;
+  precision = resolve_fourier_backward_precision(n_pupil, grid->nx, grid->ny, precision);
   const long long planes = (long long)batch * grid->nz;
   return backward_layout(nullptr, n_pupil, grid, precision, 66,
                          (int)(planes < 2048 ? planes : 2048)).bytes;
@@ -654,6 +740,8 @@ extern "C" int psf_fourier_vectorial_backward(
     float* grad_phase_map, float* grad_zernike, void* workspace,
     size_t ws_bytes, void* stream) {
   g_err[0] = 0;
+  if (grid)
+    precision = resolve_fourier_backward_precision(n_pupil, grid->nx, grid->ny, precision);
   int r = check_fourier_args(opt, n_pupil, grid, precision);
   if (r) return r;
   if (precision == PSF_PREC_FP32_CHIRPZ)
@@ -846,7 +934,9 @@ static int check_bessel_args(const psf_optics* base, int n_em, int n_slices,
 extern "C" size_t psf_bessel_workspace_size(const psf_optics* base, int n_em,
                                             int n_slices, int n_theta, int n_r,
                                             int nx, int ny, int precision) {
+  precision = resolve_spherical_precision(n_theta, precision);
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
+  if (spherical_envelope(n_theta, precision)) return 0;
   return bessel_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, true,
                        precision).bytes;
 }
@@ -1069,9 +1159,11 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
                                     void* profiles, void* workspace,
                                     size_t ws_bytes, void* stream) {
   g_err[0] = 0;
+  precision = resolve_spherical_precision(n_theta, precision);
   int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
                             n_theta, n_r, nx, ny, dx, dy, precision);
   if (r) return r;
+  if ((r = spherical_envelope(n_theta, precision))) return r;
   if (!intensity && !profiles && n_slices > 0)
     return fail(PSF_ERR_ARG, "intensity and profiles are both NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
@@ -1234,6 +1326,7 @@ static void build_pix_groups(int nx, int ny, double dx, double dy, int n_r, doub
 extern "C" size_t psf_bessel_backward_workspace_size(const psf_optics* base, int n_em,
                                                      int n_slices, int n_theta, int n_r,
                                                      int nx, int ny, int precision) {
+  precision = resolve_bessel_backward_precision(precision);
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
   if (nx > 4096 || ny > 4096 || n_r > 4096) return 0;
   return bessel_bwd_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, precision).bytes;
@@ -1247,6 +1340,7 @@ extern "C" int psf_bessel_vectorial_backward(
     float* grad_phase_theta, float* grad_zernike, float* grad_depth, void* workspace,
     size_t ws_bytes, void* stream) {
   g_err[0] = 0;
+  precision = resolve_bessel_backward_precision(precision);
   int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
                             n_theta, n_r, nx, ny, dx, dy, precision);
   if (r) return r;
@@ -1451,13 +1545,13 @@ extern "C" int psf_bessel_harmonic_order(const double* zernike, int n_em, int n_
   return best;
 }
 
-static int check_harm_args(int m_max, int precision) {
+static int check_harm_args(int m_max, int n_theta, int precision) {
   if (m_max < 0 || m_max > kHarmMaxM)
     return fail(PSF_ERR_ARG, "m_max %d outside [0, %d]", m_max, kHarmMaxM);
   if (precision != PSF_PREC_FP32 && !harm_split(precision))
     return fail(PSF_ERR_PRECISION, "harmonic path: precision %d is not FP32 or split FP16",
                 precision);
-  return PSF_OK;
+  return spherical_envelope(n_theta, precision);
 }
 
 extern "C" size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_em,
@@ -1465,7 +1559,8 @@ extern "C" size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int
                                                      int nx, int ny, int m_max,
                                                      int precision) {
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, PSF_PREC_FP32)) return 0;
-  if (check_harm_args(m_max, precision)) return 0;
+  precision = resolve_spherical_precision(n_theta, precision);
+  if (check_harm_args(m_max, n_theta, precision)) return 0;
   return harm_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, m_max, precision).bytes;
 }
 
@@ -1481,7 +1576,8 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
   int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
                             n_theta, n_r, nx, ny, dx, dy, PSF_PREC_FP32);
   if (r) return r;
-  if ((r = check_harm_args(m_max, precision))) return r;
+  precision = resolve_spherical_precision(n_theta, precision);
+  if ((r = check_harm_args(m_max, n_theta, precision))) return r;
   if (!(tail_tol >= 0.0 && tail_tol < 1.0))
     return fail(PSF_ERR_ARG, "tail_tol %g outside [0, 1)", tail_tol);
   if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");

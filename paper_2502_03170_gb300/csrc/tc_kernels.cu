@@ -36,7 +36,7 @@ constexpr int BN = 192;             // B rows per tile (3 channels x 64)
 constexpr int BOUT = 64;            // outputs per tile along m and per channel along n
 // Measured on GB300 (256^2 pupil, 512^2 px, 128 planes): BK 64 / 2 stages
 // 1.009 ms per stack, BK 32 / 4 stages 1.022 ms, BK 32 / 5 stages 1.031 ms:
-// the ring depth is not the limit (operand delivery is, see the design notes).
+// the ring depth is not the limit (operand delivery into the SM is).
 #ifndef PSF_TC_BK
 #define PSF_TC_BK 64
 #endif

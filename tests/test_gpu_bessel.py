@@ -1,8 +1,10 @@
 """Bessel strategy on the GPU (through the C ABI) against the FP64 oracle.
 
 Tolerance per stack: max |I - I_ref| / max |I_ref| <= 1e-5 for the FP32 and
-split-fp16 radial contractions, 1e-4 for split-bf16 (16 significant bits per
-operand); the complex profiles are held to the same bounds."""
+split-fp16 radial contractions; the complex profiles are held to the same
+bound.  Split BF16 (16 significant bits per operand) measured 5.2e-5 on the
+workload: the forward refuses it (PSF_ERR_PRECISION), as it refuses split
+FP16 beyond 448 theta nodes."""
 import numpy as np
 import pytest
 import torch
@@ -14,8 +16,8 @@ from paper_2502_03170_gb300 import workloads as W
 from .gpu_helpers import max_rel, oracle_optics
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp32": 1e-5, "split_fp16": 1e-5, "split_bf16": 1e-4}
-PRECS = ["fp32", "split_fp16", "split_bf16"]
+TOL = {"fp32": 1e-5, "split_fp16": 1e-5}
+PRECS = ["fp32", "split_fp16"]
 
 
 def small_batch(seed=7, nz=(3, 1, 4, 2, 5), with_m_nonzero=True):
@@ -139,3 +141,25 @@ def test_bessel_outputs_to_pinned_host_memory(lib):
     torch.cuda.synchronize()
     assert np.array_equal(I_pin.numpy(), I_dev.cpu().numpy())
     assert np.array_equal(H_pin.numpy(), H_dev.cpu().numpy())
+
+
+def test_split_modes_outside_the_envelope_are_refused(lib):
+    """Split BF16, and split FP16 beyond 448 theta nodes, are refused before
+    any launch; "auto" takes split FP16 inside the envelope (bitwise the
+    same stack) and FP32 beyond it."""
+    d = W.optics_gibson_lanni(0.0)
+    depth, zern, offs, z = small_batch(seed=5, nz=(2, 3))
+    geo = (200, 48, 12, 12, 0.03, 0.03)
+    with pytest.raises(_lib.PsfError) as e:
+        api.bessel(d, depth, zern, offs, z, *geo, project=True, precision="split_bf16")
+    assert e.value.code == _lib.PSF_ERR_PRECISION
+    with pytest.raises(_lib.PsfError) as e:
+        api.bessel(d, depth, zern, offs, z, 600, *geo[1:], project=True,
+                   precision="split_fp16")
+    assert e.value.code == _lib.PSF_ERR_PRECISION
+    a = api.bessel(d, depth, zern, offs, z, *geo, project=True, precision="auto")
+    f = api.bessel(d, depth, zern, offs, z, *geo, project=True, precision="split_fp16")
+    a6 = api.bessel(d, depth, zern, offs, z, 600, *geo[1:], project=True, precision="auto")
+    f6 = api.bessel(d, depth, zern, offs, z, 600, *geo[1:], project=True, precision="fp32")
+    torch.cuda.synchronize()
+    assert torch.equal(a, f) and torch.equal(a6, f6)

@@ -1,11 +1,13 @@
 """Fourier strategy on the GPU (through the C ABI) against the FP64 oracle.
 
 Tolerance: max |I - I_ref| / max |I_ref| <= 1e-5 per stack for intensity and
-the same for the complex fields (the forward target), for the FP32 and the
-split-fp16 contractions.  Split-bf16 keeps only 16 significant bits per
-operand (hi + lo of 8 bits each), so its bound is the one its representation
-error gives: 2^-16 per operand and product, i.e. a few 1e-5 on |E|^2; it is
-tested at 1e-4 and its measured error is reported by the benchmark."""
+the same for the complex fields (the forward target), for the FP32 and both
+split contractions (the symmetry-folded form sums half of K per accumulator
+and stays within the bound inside the library's accuracy envelope: split
+FP16 up to n_pupil 512, split BF16 up to 1024; larger pupils are refused).
+The unfolded 2x2-block form (PSF_TC_FOLD=0, a comparison path) is held to
+3e-5: it sums four times as many terms per accumulator and measured 1.07e-5
+in split BF16."""
 import ctypes
 
 import numpy as np
@@ -19,7 +21,8 @@ from paper_2502_03170_gb300 import workloads as W
 from .gpu_helpers import max_rel, oracle_optics
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp32": 1e-5, "split_fp16": 1e-5, "split_bf16": 1e-4}
+TOL = {"fp32": 1e-5, "split_fp16": 1e-5, "split_bf16": 1e-5}
+TOL_UNFOLDED = 3e-5
 PRECS = ["fp32", "split_fp16", "split_bf16"]
 
 
@@ -252,4 +255,30 @@ def test_folded_matches_unfolded_and_oracle(lib, prec, N, nx, ny, nz, monkeypatc
     Ir = of.intensity(E)
     assert max_rel(I_f, Ir) <= TOL[prec]
     assert max_rel(F_f, E) <= TOL[prec]
-    assert max_rel(I_f, I_u) <= 2 * TOL[prec]
+    assert max_rel(I_u, Ir) <= TOL_UNFOLDED
+
+
+def test_split_modes_outside_the_envelope_are_refused(lib):
+    """Split FP16 beyond n_pupil 512 and split BF16 beyond 1024 are refused
+    before any launch (their error grows with the pupil: 8.7e-6 and 1.7e-5
+    in split FP16 at 1024 and 2048)."""
+    c = W.fourier(n_pupil=1024, nx=32, nz=1)
+    for N, prec in ((1024, "split_fp16"), (2048, "split_bf16")):
+        with pytest.raises(_lib.PsfError) as e:
+            api.fourier(c["optics"], N, c["grid"], zernike=c["zernike"], precision=prec)
+        assert e.value.code == _lib.PSF_ERR_PRECISION, (N, prec)
+
+
+@pytest.mark.parametrize("N,mode", [(256, "split_fp16"), (1024, "split_bf16"),
+                                    (1536, "chirpz_fp32")])
+def test_auto_precision(lib, N, mode):
+    """"auto" runs the fastest mode inside the accuracy envelope (bitwise that
+    mode's stack) and stays within 1e-5 of the oracle."""
+    c = W.fourier(n_pupil=N, nx=48, nz=2)
+    a = api.fourier(c["optics"], N, c["grid"], zernike=c["zernike"], precision="auto")
+    m = api.fourier(c["optics"], N, c["grid"], zernike=c["zernike"], precision=mode)
+    torch.cuda.synchronize()
+    a = a.cpu().numpy()
+    assert np.array_equal(a, m.cpu().numpy())
+    Ir = of.psf_fourier(oracle_optics(c["optics"]), N, c["grid"], zernike=c["zernike"])
+    assert max_rel(a, Ir) <= 1e-5

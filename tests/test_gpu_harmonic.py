@@ -157,19 +157,30 @@ def test_square_geometry_octant_epilogue(lib, n, n_r):
     assert max_rel(I, I4.cpu().numpy()) <= 2e-6
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split_fp16"])
 @pytest.mark.parametrize("px", [(9, 11, 0.05, 0.04), (12, 12, 0.045, 0.045)])
-def test_maximum_order_and_nodes(lib, precision, px):
+def test_maximum_order_and_nodes(lib, px):
     """The largest sizes the call takes: m_max = 64 (133 orders, a 512-point
     azimuthal FFT) with every order kept, and 880 Gauss-Legendre nodes; the
-    quarter-pixel and the octant epilogue.  The split form keeps about 21
-    bits per product; with 880 strongly oscillating terms per integral
-    (aberrations of 0.15 rad per term) it measured 1.2e-5, so it is held to
-    2e-5 here (the FP32 contraction to the 1e-5 bound)."""
+    quarter-pixel and the octant epilogue, FP32 contraction.  The split form
+    sums 880 strongly oscillating terms per integral (aberrations of 0.15 rad
+    per term) in each FP32 tensor-core accumulator and measured up to 1.2e-5
+    there: it is refused beyond 448 nodes."""
     d = W.optics_gibson_lanni(0.0)
     depth, zern, offs, z = batch(3, 91, scale=0.15)
-    check(d, depth, zern, offs, z, (880, 40) + px, 64, tail_tol=0.0, precision=precision,
-          tol=TOL if precision == "fp32" else 2e-5)
+    check(d, depth, zern, offs, z, (880, 40) + px, 64, tail_tol=0.0, precision="fp32")
+    with pytest.raises(_lib.PsfError) as e:
+        check(d, depth, zern, offs, z, (880, 40) + px, 64, tail_tol=0.0,
+              precision="split_fp16")
+    assert e.value.code == _lib.PSF_ERR_PRECISION
+
+
+@pytest.mark.parametrize("px", [(9, 11, 0.05, 0.04), (12, 12, 0.045, 0.045)])
+def test_split_at_the_envelope_edge(lib, px):
+    """Split FP16 at the largest node count it accepts (448) with every
+    order up to 64 and the same strong aberrations: within 1e-5."""
+    d = W.optics_gibson_lanni(0.0)
+    depth, zern, offs, z = batch(3, 91, scale=0.15)
+    check(d, depth, zern, offs, z, (448, 40) + px, 64, tail_tol=0.0, precision="split_fp16")
 
 
 @pytest.mark.parametrize("kind", ["bessel_split", "harmonic_fp32", "harmonic_split"])

@@ -197,3 +197,46 @@ def test_backward_batch_workspace(cpu_lib):
     assert sizes[1] < sizes[2] < sizes[3] == sizes[4]     # capped at 2048 planes
     assert cpu_lib.psf_fourier_backward_workspace_size_batch(ctypes.byref(o), 256,
                                                              ctypes.byref(g.c), 1, 0) == 0
+
+
+def test_split_precision_envelope(cpu_lib):
+    """Forward calls in a split mode are refused (PSF_ERR_PRECISION, before
+    any launch) outside the sizes where the split contractions stay within
+    the 1e-5 bound; PSF_PREC_AUTO then takes a mode that does, and the
+    adjoints (gradient bound 1e-4) keep every mode."""
+    o = api.make_optics(W.optics_gibson_lanni(2.0))
+    g = api.Grid(dict(nx=64, ny=64, dx=0.01, dy=0.01, z=[0.0, 0.5]))
+    size = lambda N, p: cpu_lib.psf_fourier_workspace_size(ctypes.byref(o), N,
+                                                           ctypes.byref(g.c), p)
+    F16, B16 = _lib.PSF_PREC_SPLIT_FP16, _lib.PSF_PREC_SPLIT_BF16
+    assert size(512, F16) > 0 and size(1024, B16) > 0
+    assert size(1024, F16) == 0
+    assert b"split FP16" in cpu_lib.psf_last_error() and b"512" in cpu_lib.psf_last_error()
+    assert size(2048, B16) == 0 and b"split BF16" in cpu_lib.psf_last_error()
+    # AUTO: the split form's own size where it is inside, another mode beyond
+    for N, mode in ((256, F16), (1024, B16), (1536, _lib.PSF_PREC_FP32_CHIRPZ),
+                    (4096, _lib.PSF_PREC_FP32)):
+        assert size(N, _lib.PSF_PREC_AUTO) == size(N, mode), N
+    r = cpu_lib.psf_fourier_vectorial(ctypes.byref(o), 1024, ctypes.byref(g.c), None, 0,
+                                      None, F16, ctypes.c_void_p(16), None,
+                                      ctypes.c_void_p(256), 1 << 40, None)
+    assert r == _lib.PSF_ERR_PRECISION
+    # the adjoint takes split FP16 at any pupil its tensor-core form runs
+    assert cpu_lib.psf_fourier_backward_workspace_size(ctypes.byref(o), 1024,
+                                                       ctypes.byref(g.c), F16) > 0
+    # spherical forwards: no split BF16; split FP16 up to 448 theta nodes
+    ob_ = api.make_optics(W.optics_gibson_lanni(0.0), _lib.PSF_PROJECT_AXISYMMETRIC)
+    bsize = lambda nt, p: cpu_lib.psf_bessel_workspace_size(ctypes.byref(ob_), 4, 16, nt, 64,
+                                                            16, 16, p)
+    assert bsize(448, F16) > 0 and bsize(200, _lib.PSF_PREC_FP32) > 0
+    assert bsize(200, B16) == 0 and b"BF16" in cpu_lib.psf_last_error()
+    assert bsize(600, F16) == 0 and b"448" in cpu_lib.psf_last_error()
+    assert bsize(200, _lib.PSF_PREC_AUTO) == bsize(200, F16)
+    assert bsize(600, _lib.PSF_PREC_AUTO) == bsize(600, _lib.PSF_PREC_FP32)
+    hsize = lambda nt, p: cpu_lib.psf_bessel_harmonic_workspace_size(
+        ctypes.byref(ob_), 4, 16, nt, 64, 16, 16, 12, p)
+    assert hsize(448, F16) > 0 and hsize(600, F16) == 0
+    assert hsize(600, _lib.PSF_PREC_AUTO) == hsize(600, _lib.PSF_PREC_FP32)
+    # the Bessel adjoint keeps split BF16
+    assert cpu_lib.psf_bessel_backward_workspace_size(ctypes.byref(ob_), 4, 16, 200, 64, 16,
+                                                      16, B16) > 0

@@ -14,7 +14,6 @@ from paper_2502_03170_gb300 import _lib, api
 from paper_2502_03170_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-5
 
 
 def _noalloc(lib, d, N, grid, zern, pm):
@@ -51,8 +50,10 @@ def test_noalloc_matches_workspace_entry_point(lib):
             I_ref, F_ref = I_ref.cpu().numpy(), F_ref.cpu().numpy()
             I, F = _noalloc(lib, d, N, grid, zern, pm)
             assert np.all(np.isfinite(I)), rep
-            assert np.max(np.abs(I - I_ref)) <= TOL * np.max(np.abs(I_ref)), rep
-            assert np.max(np.abs(F - F_ref)) <= TOL * np.max(np.abs(F_ref)), rep
+            # the same kernels and per-plane arithmetic (only the z-chunk
+            # length differs, which no plane's result depends on): bitwise
+            assert np.array_equal(I, I_ref), rep
+            assert np.array_equal(F, F_ref), rep
 
 
 def test_noalloc_runs_large_stacks_in_short_chunks(lib):
@@ -69,8 +70,8 @@ def test_noalloc_runs_large_stacks_in_short_chunks(lib):
     I_ref, F_ref = api.fourier(c["optics"], c["n_pupil"], c["grid"], zernike=c["zernike"],
                                fields=True)
     I_ref, F_ref = I_ref.cpu().numpy(), F_ref.cpu().numpy()
-    assert np.max(np.abs(I - I_ref)) <= TOL * np.max(np.abs(I_ref))
-    assert np.max(np.abs(F - F_ref)) <= TOL * np.max(np.abs(F_ref))
+    assert np.array_equal(I, I_ref)
+    assert np.array_equal(F, F_ref)
 
 
 def test_noalloc_rejects_sizes_beyond_the_array(lib):
