@@ -707,15 +707,18 @@ def pupil_scaling(c, ws, flush, stream, pupils=(512, 1024), steps=3):
 
 def fourier_variants(args, c, g, opt, N, ws, flush, stream, steps=5):
     """Every contraction precision on the same stack (the chirp-Z FFT zoom
-    among them), and the scalar (Eq. 3) and Fresnel (Eq. 6-7) models at split
-    FP16: voxels/s and error against the FP64 oracle of the same model."""
+    among them; single-pass TF32 is outside the 1e-5 bound and runs only with
+    the caller's opt-out), and the scalar (Eq. 3) and Fresnel (Eq. 6-7)
+    models at split FP16: voxels/s and error against the FP64 oracle of the
+    same model."""
     import torch
 
     from paper_2502_03170_gb300 import api
     out = {}
     runs = [("fp32", "fp32", {}), ("split_fp16", "split_fp16", {}),
-            ("split_bf16", "split_bf16", {}), ("chirpz_fp32", "chirpz_fp32", {}),
-            ("auto", "auto", {}),
+            ("split_bf16", "split_bf16", {}), ("split_tf32", "split_tf32", {}),
+            ("tf32_single_pass", "tf32", {"outside_envelope": True}),
+            ("chirpz_fp32", "chirpz_fp32", {}), ("auto", "auto", {}),
             ("scalar_split_fp16", "split_fp16", {"scalar": True}),
             ("fresnel_split_fp16", "split_fp16", {"fresnel": True})]
     for name, prec, kw in runs:

@@ -80,6 +80,13 @@ extern "C" {
                                    L = 2^k >= max(256, n_pupil + n_out - 1),
                                    L <= 4096 per direction; same discrete sum
                                    as PSF_PREC_FP32, O(L log L) per line      */
+#define PSF_PREC_SPLIT_TF32  5  /* Fourier forward: tcgen05 kind::tf32, operands
+                                   split hi + lo TF32 (FP32 storage), 3
+                                   products, FP32 accumulation in TMEM       */
+#define PSF_PREC_TF32        6  /* Fourier forward: one TF32 product per MAC
+                                   (10-bit operand mantissas: about 1e-3 of
+                                   the stack; outside the accuracy envelope,
+                                   accepted only with PSF_OUTSIDE_ENVELOPE)   */
 #define PSF_PREC_AUTO        4  /* the fastest mode inside the accuracy
                                    envelope below: Fourier forward split FP16
                                    (n_pupil <= 512), else split BF16 (<= 1024),
@@ -100,8 +107,11 @@ extern "C" {
  * stays within half the bound:
  *   Fourier   split FP16  n_pupil <= 512   (4.3e-6 at 512; 8.7e-6 at 1024)
  *             split BF16  n_pupil <= 1024  (4.2e-6 at 1024; 7.6e-6 at 2048)
+ *             split TF32  n_pupil <= 512   (three TF32 products)
+ *             TF32        refused          (one product: about 1e-3)
  *   Bessel /  split FP16  n_theta <= 448   (5.2e-6 at 448; 9.9e-6 at 880)
  *   harmonic  split BF16  refused          (5.2e-5 on the Bessel workload)
+ * The flag PSF_OUTSIDE_ENVELOPE lifts these refusals.
  * FP32 and chirp-Z stay below 2e-6 at every size.  The adjoints (gradient
  * bound 1e-4 relative L2) take every mode they support.                      */
 
@@ -121,6 +131,9 @@ extern "C" {
                                        angles, principal root where evanescent).
                                        Fourier: every path; Bessel: the FP32
                                        forward only (complex J_n operand)       */
+#define PSF_OUTSIDE_ENVELOPE     8  /* accept a precision mode outside the
+                                       accuracy envelope below (results may miss
+                                       the 1e-5 bound; for comparisons)        */
 
 /* Physical parameters (Eq. 1, Eq. 13-14, Eq. 16-17). */
 typedef struct {

@@ -22,10 +22,13 @@ PSF_PREC_SPLIT_FP16 = 1
 PSF_PREC_SPLIT_BF16 = 2
 PSF_PREC_FP32_CHIRPZ = 3
 PSF_PREC_AUTO = 4
+PSF_PREC_SPLIT_TF32 = 5
+PSF_PREC_TF32 = 6
 
 PSF_PROJECT_AXISYMMETRIC = 1
 PSF_SCALAR = 2
 PSF_FRESNEL = 4
+PSF_OUTSIDE_ENVELOPE = 8
 
 ERROR_NAMES = {
     PSF_ERR_ARG: "PSF_ERR_ARG",

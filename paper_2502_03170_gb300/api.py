@@ -14,7 +14,8 @@ from ._lib import PsfGrid, PsfOptics, check
 
 PRECISIONS = {"fp32": _lib.PSF_PREC_FP32, "split_fp16": _lib.PSF_PREC_SPLIT_FP16,
               "split_bf16": _lib.PSF_PREC_SPLIT_BF16,
-              "chirpz_fp32": _lib.PSF_PREC_FP32_CHIRPZ, "auto": _lib.PSF_PREC_AUTO}
+              "chirpz_fp32": _lib.PSF_PREC_FP32_CHIRPZ, "auto": _lib.PSF_PREC_AUTO,
+              "split_tf32": _lib.PSF_PREC_SPLIT_TF32, "tf32": _lib.PSF_PREC_TF32}
 
 
 def make_optics(d, flags=0):
@@ -41,6 +42,8 @@ def make_optics(d, flags=0):
         flags |= _lib.PSF_SCALAR
     if d.get("fresnel"):
         flags |= _lib.PSF_FRESNEL
+    if d.get("outside_envelope"):
+        flags |= _lib.PSF_OUTSIDE_ENVELOPE
     o.flags = flags
     return o
 

@@ -39,7 +39,7 @@ namespace tc {
 namespace fold {
 
 constexpr int BM = 128;                 // zoom rows per CTA
-constexpr int BK = 64;                  // K elements per stage (128-byte swizzled rows)
+constexpr int BK = 64;                  // 16-bit K elements per stage (128-byte swizzled rows)
 constexpr int SWZ = 128;
 constexpr int EPI_WARPS = 8;            // two per TMEM lane quarter
 constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
@@ -82,8 +82,10 @@ struct FoldParams {
   int pblk;             // stage 1: p'-blocks of S1_PB per (channel, parity)
   uint32_t idesc;
   int bf16;
+  int passes;           // TF32 operands: 3 (hi.hi + lo.hi + hi.lo) or 1 (hi.hi)
   float out_scale;
   uint16_t* U;          // stage 1 output [planes][4][6 ny][Kp]: T+ hi, T+ lo, T- hi, T- lo
+                        // (32-bit elements with TF32 operands)
   float* I;             // stage 2: [planes][nx][ny]
   float2* F;            // stage 2: [planes][3][nx][ny] or null
   int* status;
@@ -205,6 +207,42 @@ PSF_D void store_piece16(uint16_t* base, size_t off, size_t lo_delta, const floa
   }
 }
 
+// The TF32 form of store_piece16: 16 values split into TF32 hi + lo (lo 0
+// with one pass), 32-bit elements, two 32-byte stores each for hi and lo.
+PSF_D void store_piece32(uint32_t* base, size_t off, size_t lo_delta, const float (&v)[16],
+                         int passes, int n_valid) {
+  uint32_t h[16], l[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) split_tf32(v[j], passes, h[j], l[j]);
+  if (n_valid >= 16) {
+    const uint32_t h0[8] = {h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7]};
+    const uint32_t h1[8] = {h[8], h[9], h[10], h[11], h[12], h[13], h[14], h[15]};
+    const uint32_t l0[8] = {l[0], l[1], l[2], l[3], l[4], l[5], l[6], l[7]};
+    const uint32_t l1[8] = {l[8], l[9], l[10], l[11], l[12], l[13], l[14], l[15]};
+    st_global_v8(base + off, h0);
+    st_global_v8(base + off + 8, h1);
+    st_global_v8(base + off + lo_delta, l0);
+    st_global_v8(base + off + lo_delta + 8, l1);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j < n_valid) {
+        base[off + j] = h[j];
+        base[off + lo_delta + j] = l[j];
+      }
+    }
+  }
+}
+
+template <bool TF32>
+PSF_D void store_piece(const FoldParams& p, size_t off, size_t lo_delta, const float (&v)[16],
+                       int n_valid) {
+  if (TF32)
+    store_piece32((uint32_t*)p.U, off, lo_delta, v, p.passes, n_valid);
+  else
+    store_piece16(p.U, off, lo_delta, v, p.bf16, n_valid);
+}
+
 // Releases the accumulator on the leader's barrier once this warp has read
 // its columns (before the arithmetic and the stores of the tile).
 PSF_D void release_acc(int lane, uint32_t bar_cluster) {
@@ -220,6 +258,7 @@ PSF_D void release_acc(int lane, uint32_t bar_cluster) {
 //   T^r[p'][b'] = X + i Y,  T^r[p'][b~'] = X - i Y   (X, Y complex)
 // written split hi + lo as rows (b, c, re/im) of U^r for b = b' and b~'.
 // ---------------------------------------------------------------------------
+template <bool TF32>
 PSF_D void epilogue_stage1(const FoldParams& p, uint32_t tx, uint32_t ty, int plane, int mt,
                            int nt, int row, int half, int lane, uint32_t release_bar) {
   const int c = nt / (2 * p.pblk);
@@ -256,20 +295,20 @@ PSF_D void epilogue_stage1(const FoldParams& p, uint32_t tx, uint32_t ty, int pl
 #pragma unroll
     for (int j = 0; j < 16; ++j)
       t[j] = sc * (__uint_as_float(v[u][0][j]) - __uint_as_float(v[u][3][j]));
-    store_piece16(p.U, rb + p0, var, t, p.bf16, n_valid);
+    store_piece<TF32>(p, rb + p0, var, t, n_valid);
 #pragma unroll
     for (int j = 0; j < 16; ++j)
       t[j] = sc * (__uint_as_float(v[u][1][j]) + __uint_as_float(v[u][2][j]));
-    store_piece16(p.U, rb + kp + p0, var, t, p.bf16, n_valid);
+    store_piece<TF32>(p, rb + kp + p0, var, t, n_valid);
     if (ok_m) {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         t[j] = sc * (__uint_as_float(v[u][0][j]) + __uint_as_float(v[u][3][j]));
-      store_piece16(p.U, rm + p0, var, t, p.bf16, n_valid);
+      store_piece<TF32>(p, rm + p0, var, t, n_valid);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         t[j] = sc * (__uint_as_float(v[u][1][j]) - __uint_as_float(v[u][2][j]));
-      store_piece16(p.U, rm + kp + p0, var, t, p.bf16, n_valid);
+      store_piece<TF32>(p, rm + kp + p0, var, t, n_valid);
     }
   }
 }
@@ -359,12 +398,16 @@ PSF_D void epilogue_stage2(const FoldParams& p, uint32_t tx, uint32_t ty, int pl
 // The persistent CTA-pair kernel of both folded stages.
 //   mA: zoom halves [4][m_rows][H] (C hi, C lo, S hi, S lo), box BK x 128 x 4
 //   mB: data, four variants (X hi, X lo, Y hi, Y lo) per box
+// TF32: 32-bit operands, kind::tf32 MMAs with K = 8; a stage holds the same
+// 128-byte rows (32 elements), so the shared-memory layout, the four 32-byte
+// K steps per stage and the descriptors are those of the 16-bit form.
 // ---------------------------------------------------------------------------
-template <int MODE, bool RES>
+template <int MODE, bool RES, bool TF32>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_fold_pair(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
             const FoldParams p) {
   using Sh = Shape<MODE, RES>;
+  constexpr int BKE = TF32 ? BK / 2 : BK;      // K elements per stage
   constexpr int STAGES = Sh::STAGES, BN = Sh::BN, NACC = Sh::NACC;
   constexpr int PB_BYTES = Sh::PB_BYTES, STAGE_BYTES = Sh::STAGE_BYTES;
   constexpr int B_OFF = RES ? 0 : A_CHUNK;      // data operand within a stage
@@ -421,7 +464,7 @@ k_fold_pair(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
       const uint32_t fa = mapa_shared(afull_bar, 0);
       if (leader) mbar_arrive_expect_tx(afull_bar, 2u * p.k_chunks * A_CHUNK);
       for (int kc = 0; kc < p.k_chunks; ++kc)
-        tma_load_3d_pair(smem_u32(smem) + kc * A_CHUNK, &mA, kc * BK, (int)rank * BM, 0, fa);
+        tma_load_3d_pair(smem_u32(smem) + kc * A_CHUNK, &mA, kc * BKE, (int)rank * BM, 0, fa);
     }
     int stage = 0;
     uint32_t phase = 0;
@@ -438,7 +481,7 @@ k_fold_pair(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
         const uint32_t base = smem_u32(ring + stage * STAGE_BYTES);
         const uint32_t fb = mapa_shared(full_bar(stage), 0);   // the leader's barrier
         if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * STAGE_BYTES);
-        const int k0 = kc * BK;
+        const int k0 = kc * BKE;
         if (!RES) tma_load_3d_pair(base, &mA, k0, mt * BM, 0, fb);
         if (MODE == 0) {
           // rows (plane, c, parity, re/im = rank) x 64 p' of the p'-block
@@ -508,12 +551,25 @@ k_fold_pair(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
         for (int k = 0; k < BK / 16; ++k) {
           const uint64_t adv = (uint64_t)((k * 32) >> 4);   // 16 elements = 32 bytes
           const uint32_t first = (kc == 0 && k == 0) ? 0u : 1u;
-          mma_f16_pair(d_x, dCh + adv, dXh + adv, p.idesc, first);
-          mma_f16_pair(d_x, dCl + adv, dXh + adv, p.idesc, 1u);
-          mma_f16_pair(d_x, dCh + adv, dXl + adv, p.idesc, 1u);
-          mma_f16_pair(d_y, dSh + adv, dYh + adv, p.idesc, first);
-          mma_f16_pair(d_y, dSl + adv, dYh + adv, p.idesc, 1u);
-          mma_f16_pair(d_y, dSh + adv, dYl + adv, p.idesc, 1u);
+          if (TF32) {
+            mma_tf32_pair(d_x, dCh + adv, dXh + adv, p.idesc, first);
+            if (p.passes == 3) {
+              mma_tf32_pair(d_x, dCl + adv, dXh + adv, p.idesc, 1u);
+              mma_tf32_pair(d_x, dCh + adv, dXl + adv, p.idesc, 1u);
+            }
+            mma_tf32_pair(d_y, dSh + adv, dYh + adv, p.idesc, first);
+            if (p.passes == 3) {
+              mma_tf32_pair(d_y, dSl + adv, dYh + adv, p.idesc, 1u);
+              mma_tf32_pair(d_y, dSh + adv, dYl + adv, p.idesc, 1u);
+            }
+          } else {
+            mma_f16_pair(d_x, dCh + adv, dXh + adv, p.idesc, first);
+            mma_f16_pair(d_x, dCl + adv, dXh + adv, p.idesc, 1u);
+            mma_f16_pair(d_x, dCh + adv, dXl + adv, p.idesc, 1u);
+            mma_f16_pair(d_y, dSh + adv, dYh + adv, p.idesc, first);
+            mma_f16_pair(d_y, dSl + adv, dYh + adv, p.idesc, 1u);
+            mma_f16_pair(d_y, dSh + adv, dYl + adv, p.idesc, 1u);
+          }
         }
         mma_commit_pair(empty_bar(stage), 3);   // frees the stage in both CTAs
         if (++stage == STAGES) {
@@ -552,7 +608,7 @@ k_fold_pair(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
       // as soon as it has read its columns, before its arithmetic and stores
       const uint32_t rel = mapa_shared(tempty_bar(acc), 0);
       if (MODE == 0)
-        epilogue_stage1(p, tx, ty, plane, mt, nt, row, half, lane, rel);
+        epilogue_stage1<TF32>(p, tx, ty, plane, mt, nt, row, half, lane, rel);
       else
         epilogue_stage2(p, tx, ty, plane, mt, nt, row, half, lane, rel);
       if (++acc == NACC) {
@@ -576,8 +632,10 @@ k_fold_pair(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
 //   C[i'][p'] = S_A cos(2 pi f u_p' x_i'),  S[i'][p'] = S_A sin(...),
 // the angle f d m n / (2N) cycles from the exact integers m = 2p'+1-N and
 // n = 2i'+1-n_out (one FP64 product, reduced mod 1).
+// (TF32 operands: 32-bit elements, split into TF32 hi + lo, lo 0 with one pass.)
+template <bool TF32>
 __global__ void k_fold_twiddle(int N, int n_out, int m_rows, int H, int Kp, double alpha,
-                               float sA, int bf16, uint16_t* __restrict__ Z) {
+                               float sA, int bf16, int passes, void* __restrict__ Zv) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m_rows * H) return;
   const int i = idx / H, pp = idx - (idx / H) * H;
@@ -588,13 +646,25 @@ __global__ void k_fold_twiddle(int N, int n_out, int m_rows, int H, int Kp, doub
   sincospif(2.0f * (float)cyc, &sn, &cs);
   const size_t var = (size_t)m_rows * Kp;
   const size_t o = (size_t)i * Kp + pp;
-  uint16_t h, l;
-  split16(sA * cs, bf16, h, l);
-  Z[o] = h;
-  Z[var + o] = l;
-  split16(sA * sn, bf16, h, l);
-  Z[2 * var + o] = h;
-  Z[3 * var + o] = l;
+  if (TF32) {
+    uint32_t* Z = (uint32_t*)Zv;
+    uint32_t h, l;
+    split_tf32(sA * cs, passes, h, l);
+    Z[o] = h;
+    Z[var + o] = l;
+    split_tf32(sA * sn, passes, h, l);
+    Z[2 * var + o] = h;
+    Z[3 * var + o] = l;
+  } else {
+    uint16_t* Z = (uint16_t*)Zv;
+    uint16_t h, l;
+    split16(sA * cs, bf16, h, l);
+    Z[o] = h;
+    Z[var + o] = l;
+    split16(sA * sn, bf16, h, l);
+    Z[2 * var + o] = h;
+    Z[3 * var + o] = l;
+  }
 }
 
 // Pupil fields of a z-chunk folded over both mirrors.  For node (p', q') of
@@ -607,9 +677,11 @@ __global__ void k_fold_twiddle(int N, int n_out, int m_rows, int H, int Kp, doub
 // consecutive q' per thread, one plane per grid row; planes are numbered
 // flat over (pupil, z) with nz_per planes per pupil (a single pupil:
 // wfr_stride 0).
+template <bool TF32>
 __global__ void __launch_bounds__(128)
 k_fold_pupil(NodeTable t, int N, int H, int Kp, const float2* __restrict__ zz, int z0,
-             int nz_per, long long wfr_stride, float sP, int bf16, uint16_t* __restrict__ P) {
+             int nz_per, long long wfr_stride, float sP, int bf16, int passes,
+             void* __restrict__ Pout) {
   const int NN = N * N;
   const int H4 = H / 4;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -674,15 +746,25 @@ k_fold_pupil(NodeTable t, int N, int H, int Kp, const float2* __restrict__ zz, i
       for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int ri = 0; ri < 2; ++ri) {
-          uint16_t h[4], l[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) split16(v[s][r][ri][k], bf16, h[k], l[k]);
           const size_t slab = (((size_t)blockIdx.y * 3 + c) * 2 + r) * 2 + ri;
           const size_t o = (slab * 4 + 2 * s) * var + (size_t)pp * Kp + q0;
-          *(uint2*)(P + o) = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
-                                        (uint32_t)h[2] | ((uint32_t)h[3] << 16));
-          *(uint2*)(P + o + var) = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16),
-                                              (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+          if (TF32) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) split_tf32(v[s][r][ri][k], passes, h[k], l[k]);
+            uint32_t* P = (uint32_t*)Pout;
+            *(uint4*)(P + o) = make_uint4(h[0], h[1], h[2], h[3]);
+            *(uint4*)(P + o + var) = make_uint4(l[0], l[1], l[2], l[3]);
+          } else {
+            uint16_t h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) split16(v[s][r][ri][k], bf16, h[k], l[k]);
+            uint16_t* P = (uint16_t*)Pout;
+            *(uint2*)(P + o) = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
+                                          (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+            *(uint2*)(P + o + var) = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16),
+                                                (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+          }
         }
   }
 }
@@ -712,22 +794,25 @@ static EncodeTiledFn encode_fn() {
 // [slabs][rows][K] 16-bit tensor with row pitch Kp (elements), K extent H;
 // boxes BK x box_rows x 4 (four consecutive slabs: the four variants).
 // Columns H .. Kp-1 and rows past `rows` read as zeros.
-static bool make_map(CUtensorMap* m, const uint16_t* base, int H, int Kp, int rows,
-                     int slabs, int box_rows) {
+// eb: element bytes (2: 16-bit operands, 4: TF32), a box row is 128 bytes.
+static bool make_map(CUtensorMap* m, const void* base, int H, int Kp, int rows, int slabs,
+                     int box_rows, int eb) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)H, (cuuint64_t)rows, (cuuint64_t)slabs};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 4};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * eb, (cuuint64_t)Kp * eb * rows};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows, 4};
   cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, (void*)base, dims, strides, box, es,
+  return fn(m, eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+            (void*)base, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
-static uint32_t make_idesc(int bf16, int bn) {
-  const uint32_t fmt = bf16 ? 1u : 0u;
+// operand format: 0 fp16, 1 bf16, 2 tf32
+static uint32_t make_idesc(int fmt_code, int bn) {
+  const uint32_t fmt = (uint32_t)fmt_code;
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
          ((uint32_t)((2 * BM) >> 4) << 24);
 }
@@ -743,19 +828,19 @@ static int num_sms() {
   return n;
 }
 
-template <int MODE, bool RES>
+template <int MODE, bool RES, bool TF32>
 static int launch(const CUtensorMap& mA, const CUtensorMap& mB, FoldParams p,
                   cudaStream_t s) {
   using Sh = Shape<MODE, RES>;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_fold_pair<MODE, RES>,
+    if (cudaFuncSetAttribute(k_fold_pair<MODE, RES, TF32>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Sh::SMEM_BYTES) != cudaSuccess)
       return PSF_ERR_CUDA;
     attr = true;
   }
-  p.idesc = make_idesc(p.bf16, Sh::BN);
+  p.idesc = make_idesc(TF32 ? 2 : p.bf16, Sh::BN);
   const int total = p.planes * p.m_pairs * p.n_tiles;
   int clusters = num_sms() / 2;
   if (total < clusters) clusters = total;
@@ -772,7 +857,7 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, FoldParams p,
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_fold_pair<MODE, RES>, mA, mB, p) != cudaSuccess)
+  if (cudaLaunchKernelEx(&cfg, k_fold_pair<MODE, RES, TF32>, mA, mB, p) != cudaSuccess)
     return PSF_ERR_CUDA;
   return cudaPeekAtLastError() == cudaSuccess ? PSF_OK : PSF_ERR_CUDA;
 }
@@ -781,9 +866,11 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, FoldParams p,
 // whole K range fits the resident area.
 template <int MODE>
 static int launch_any(const CUtensorMap& mA, const CUtensorMap& mB, const FoldParams& p,
-                      cudaStream_t s) {
-  if (p.m_pairs == 1 && p.k_chunks <= RES_CHUNKS) return launch<MODE, true>(mA, mB, p, s);
-  return launch<MODE, false>(mA, mB, p, s);
+                      bool tf32, cudaStream_t s) {
+  const bool res = p.m_pairs == 1 && p.k_chunks <= RES_CHUNKS;
+  if (tf32)
+    return res ? launch<MODE, true, true>(mA, mB, p, s) : launch<MODE, false, true>(mA, mB, p, s);
+  return res ? launch<MODE, true, false>(mA, mB, p, s) : launch<MODE, false, false>(mA, mB, p, s);
 }
 
 static float pow2_scale(double bound, double target) {
@@ -806,18 +893,18 @@ const char* tc_fold_supported(int N, int nx, int ny) {
   return nullptr;
 }
 
-static double fold_plane_bytes(int N, int ny) {
+static double fold_plane_bytes(int N, int ny, int eb) {
   const double H = N / 2, Kp = tc_fold_kp(N);
-  // P: 4 variants x 12 H rows; U: 4 variants x 6 ny rows (16-bit, pitch Kp)
-  return 2.0 * Kp * (4.0 * 12.0 * H + 4.0 * 6.0 * ny);
+  // P: 4 variants x 12 H rows; U: 4 variants x 6 ny rows (eb-byte elements, pitch Kp)
+  return eb * Kp * (4.0 * 12.0 * H + 4.0 * 6.0 * ny);
 }
 
-int tc_fold_zchunk(int N, int nx, int ny, int nz) {
+int tc_fold_zchunk(int N, int nx, int ny, int nz, int eb) {
   // P and U of a chunk up to 4 GB and 256 planes (long launches fill the
   // persistent contractions); the planes are then spread evenly over the
   // chunks so the last one is not short
   (void)nx;
-  int cap = (int)(4096.0 * 1048576.0 / fold_plane_bytes(N, ny));
+  int cap = (int)(4096.0 * 1048576.0 / fold_plane_bytes(N, ny, eb));
   if (cap < 1) cap = 1;
   if (cap > 256) cap = 256;
   if (cap > nz) cap = nz;
@@ -825,11 +912,12 @@ int tc_fold_zchunk(int N, int nx, int ny, int nz) {
   return (nz + n_chunks - 1) / n_chunks;
 }
 
-void tc_fold_carve(char* base, size_t* off, int N, int nx, int ny, int zc, TcFoldOperands* out) {
+void tc_fold_carve(char* base, size_t* off, int N, int nx, int ny, int zc, TcFoldOperands* out,
+                   int eb) {
   auto take = [&](size_t elems) -> uint16_t* {
     *off = align_up(*off, 1024);
     uint16_t* p = base ? (uint16_t*)(base + *off) : nullptr;
-    *off += elems * sizeof(uint16_t);
+    *off += elems * (size_t)eb;
     return p;
   };
   const int H = N / 2, Kp = tc_fold_kp(N);
@@ -883,6 +971,10 @@ int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz
   FoldStreams* fs = fold_streams();
   if (host_out && !fs) return PSF_ERR_CUDA;
   const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
+  const bool tf32 = precision == PSF_PREC_SPLIT_TF32 || precision == PSF_PREC_TF32;
+  const int passes = precision == PSF_PREC_TF32 ? 1 : 3;
+  const int eb = tf32 ? 4 : 2;
+  const int bke = tf32 ? BK / 2 : BK;        // K elements per stage
   const int H = ops.H, Kp = ops.Kp;
   const int mx = (nx + 1) / 2, my = (ny + 1) / 2;
   const double target = 16384.0;             // keep |scaled value| <= 2^14
@@ -891,22 +983,33 @@ int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz
   const float sU = fold::pow2_scale(2.0 * amp_bound * N, target);
   {
     TimingScope ts(kTimeSetup, s);
-    k_fold_twiddle<<<ceil_div(mx * H, 256), 256, 0, s>>>(
-        N, nx, mx, H, Kp, na_over_lambda * dx / (2.0 * N), sA, bf16, ops.Zx);
-    k_fold_twiddle<<<ceil_div(my * H, 256), 256, 0, s>>>(
-        N, ny, my, H, Kp, na_over_lambda * dy / (2.0 * N), sA, bf16, ops.Zy);
+    auto twiddle = [&](int n_out, int m, double d, void* Z) {
+      if (tf32)
+        k_fold_twiddle<true><<<ceil_div(m * H, 256), 256, 0, s>>>(
+            N, n_out, m, H, Kp, na_over_lambda * d / (2.0 * N), sA, bf16, passes, Z);
+      else
+        k_fold_twiddle<false><<<ceil_div(m * H, 256), 256, 0, s>>>(
+            N, n_out, m, H, Kp, na_over_lambda * d / (2.0 * N), sA, bf16, passes, Z);
+    };
+    twiddle(nx, mx, dx, ops.Zx);
+    twiddle(ny, my, dy, ops.Zy);
   }
   CUtensorMap mZy, mP, mZx, mU;
-  bool ok = make_map(&mZy, ops.Zy, H, Kp, my, 4, BM) &&
-            make_map(&mP, ops.P, H, Kp, H, 48 * zc, S1_PB) &&
-            make_map(&mZx, ops.Zx, H, Kp, mx, 4, BM) &&
-            make_map(&mU, ops.U, H, Kp, 6 * ny, 4 * zc, 6 * S2_HB);
+  bool ok = make_map(&mZy, ops.Zy, H, Kp, my, 4, BM, eb) &&
+            make_map(&mP, ops.P, H, Kp, H, 48 * zc, S1_PB, eb) &&
+            make_map(&mZx, ops.Zx, H, Kp, mx, 4, BM, eb) &&
+            make_map(&mU, ops.U, H, Kp, 6 * ny, 4 * zc, 6 * S2_HB, eb);
   if (!ok) return PSF_ERR_CUDA;
   auto pupil = [&](int zc0, cudaStream_t st) {
     const int n = nz - zc0 < zc ? nz - zc0 : zc;
     TimingScope ts(kTimePupil, st);
     const dim3 pg(ceil_div(H * (H / 4), 128), n);
-    k_fold_pupil<<<pg, 128, 0, st>>>(nodes, N, H, Kp, zz, zc0, nz, 0, sP, bf16, ops.P);
+    if (tf32)
+      k_fold_pupil<true><<<pg, 128, 0, st>>>(nodes, N, H, Kp, zz, zc0, nz, 0, sP, bf16, passes,
+                                             ops.P);
+    else
+      k_fold_pupil<false><<<pg, 128, 0, st>>>(nodes, N, H, Kp, zz, zc0, nz, 0, sP, bf16,
+                                              passes, ops.P);
   };
   pupil(0, s);
   for (int z0 = 0; z0 < nz; z0 += zc) {
@@ -918,7 +1021,7 @@ int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz
     p1.m_pairs = ceil_div(my, 2 * BM);
     p1.pblk = ceil_div(H, S1_PB);
     p1.n_tiles = 3 * 2 * p1.pblk;
-    p1.k_chunks = ceil_div(H, BK);
+    p1.k_chunks = ceil_div(H, bke);
     p1.H = H;
     p1.Kp = Kp;
     p1.m_rows = my;
@@ -926,13 +1029,14 @@ int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz
     p1.nx = nx;
     p1.ny = ny;
     p1.bf16 = bf16;
+    p1.passes = passes;
     p1.out_scale = sU / (sA * sP);
     p1.U = ops.U;
     p1.status = status;
     int r;
     {
       TimingScope ts(kTimeStage1, s);
-      r = launch_any<0>(mZy, mP, p1, s);
+      r = launch_any<0>(mZy, mP, p1, tf32, s);
     }
     if (r) return r;
     if (more && fs) {
@@ -961,7 +1065,7 @@ int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz
     p2.F = fields ? fields + (size_t)z0 * 3 * plane : nullptr;
     {
       TimingScope ts(kTimeStage2, s);
-      r = launch_any<1>(mZx, mU, p2, s);
+      r = launch_any<1>(mZx, mU, p2, tf32, s);
     }
     if (r) return r;
     if (host_out) {

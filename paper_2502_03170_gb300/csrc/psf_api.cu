@@ -63,7 +63,22 @@ constexpr int kSplitFp16MaxPupil = 512;
 constexpr int kSplitBf16MaxPupil = 1024;
 constexpr int kSplitMaxTheta = 448;
 
-static int fourier_envelope(int N, int precision) {
+static bool outside_allowed(const psf_optics* opt) {
+  return opt && (opt->flags & PSF_OUTSIDE_ENVELOPE);
+}
+
+static int fourier_envelope(const psf_optics* opt, int N, int precision) {
+  if (outside_allowed(opt)) return PSF_OK;
+  if (precision == PSF_PREC_TF32)
+    return fail(PSF_ERR_PRECISION,
+                "TF32 with one product per multiply-add keeps 11 significant bits per "
+                "operand (about 1e-3 from the FP64 oracle): outside the 1e-5 envelope; use "
+                "PSF_PREC_SPLIT_TF32 or set PSF_OUTSIDE_ENVELOPE");
+  if (precision == PSF_PREC_SPLIT_TF32 && N > kSplitFp16MaxPupil)
+    return fail(PSF_ERR_PRECISION,
+                "split TF32 is accepted up to n_pupil %d; n_pupil %d: use "
+                "PSF_PREC_FP32_CHIRPZ, PSF_PREC_FP32 or PSF_PREC_AUTO",
+                kSplitFp16MaxPupil, N);
   if (precision == PSF_PREC_SPLIT_FP16 && N > kSplitFp16MaxPupil)
     return fail(PSF_ERR_PRECISION,
                 "split FP16 holds the 1e-5 bound up to n_pupil %d (measured 4.3e-6 at 512, "
@@ -79,7 +94,8 @@ static int fourier_envelope(int N, int precision) {
   return PSF_OK;
 }
 
-static int spherical_envelope(int n_theta, int precision) {
+static int spherical_envelope(const psf_optics* opt, int n_theta, int precision) {
+  if (outside_allowed(opt)) return PSF_OK;
   if (precision == PSF_PREC_SPLIT_BF16)
     return fail(PSF_ERR_PRECISION,
                 "split BF16 keeps 16 significant bits per operand: 5.2e-5 from the FP64 "
@@ -365,8 +381,9 @@ static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
     L.U = c.take<float2>((size_t)L.zc * 3 * g->ny * N);
   } else if (fold_enabled()) {
     L.fold_path = true;
-    L.zc = capped(tc_fold_zchunk(N, g->nx, g->ny, g->nz));
-    tc_fold_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.fold);
+    const int eb = precision == PSF_PREC_SPLIT_TF32 || precision == PSF_PREC_TF32 ? 4 : 2;
+    L.zc = capped(tc_fold_zchunk(N, g->nx, g->ny, g->nz, eb));
+    tc_fold_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.fold, eb);
   } else {
     L.zc = capped(tc_fourier_zchunk(N, g->nx, g->ny, g->nz));
     tc_fourier_carve(c.base, &c.off, N, g->nx, g->ny, L.zc, &L.tc);
@@ -390,8 +407,11 @@ static int check_fourier_args(const psf_optics* opt, int N, const psf_grid* g,
     if (!isfinite(g->z[i]) || fabs(g->z[i]) > 1e4)
       return fail(PSF_ERR_ARG, "z[%d] not finite or beyond 1e4 um", i);
   if (precision != PSF_PREC_FP32 && precision != PSF_PREC_SPLIT_FP16 &&
-      precision != PSF_PREC_SPLIT_BF16 && precision != PSF_PREC_FP32_CHIRPZ)
+      precision != PSF_PREC_SPLIT_BF16 && precision != PSF_PREC_FP32_CHIRPZ &&
+      precision != PSF_PREC_SPLIT_TF32 && precision != PSF_PREC_TF32)
     return fail(PSF_ERR_PRECISION, "unknown precision mode %d", precision);
+  if ((precision == PSF_PREC_SPLIT_TF32 || precision == PSF_PREC_TF32) && !fold_enabled())
+    return fail(PSF_ERR_PRECISION, "the TF32 modes run on the folded contraction only");
   if (precision == PSF_PREC_FP32_CHIRPZ) {
     if (!czt_length(N, g->nx) || !czt_length(N, g->ny))
       return fail(PSF_ERR_PRECISION, "chirp-Z: n_pupil + n_out - 1 = %d exceeds %d",
@@ -488,7 +508,7 @@ size_t psf_fourier_workspace_size(const psf_optics* opt, int n_pupil,
                                   const psf_grid* grid, int precision) {
   if (grid) precision = resolve_fourier_precision(n_pupil, grid->nx, grid->ny, precision);
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
-  if (fourier_envelope(n_pupil, precision)) return 0;
+  if (fourier_envelope(opt, n_pupil, precision)) return 0;
   return fourier_layout(nullptr, n_pupil, grid, precision).bytes;
 }
 
@@ -501,7 +521,7 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
   if (grid) precision = resolve_fourier_precision(n_pupil, grid->nx, grid->ny, precision);
   int r = check_fourier_args(opt, n_pupil, grid, precision);
   if (r) return r;
-  if ((r = fourier_envelope(n_pupil, precision))) return r;
+  if ((r = fourier_envelope(opt, n_pupil, precision))) return r;
   if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
   if (n_zern > 0 && !zernike) return fail(PSF_ERR_ARG, "zernike is NULL");
   for (int j = 0; j < n_zern; ++j)
@@ -529,7 +549,8 @@ int psf_fourier_vectorial(const psf_optics* opt, int n_pupil,
   // kernels store through the host memory's device alias.
   float* host_out = nullptr;
   float* stage = nullptr;
-  const bool tc_path = precision == PSF_PREC_SPLIT_FP16 || precision == PSF_PREC_SPLIT_BF16;
+  const bool tc_path = precision == PSF_PREC_SPLIT_FP16 || precision == PSF_PREC_SPLIT_BF16 ||
+                       precision == PSF_PREC_SPLIT_TF32 || precision == PSF_PREC_TF32;
   if (tc_path && !fields && is_pinned_host(intensity) && tc_host_streaming_available()) {
     const int chunks = 8;
     int zs = (grid->nz + chunks - 1) / chunks;
@@ -716,7 +737,9 @@ extern "C" size_t psf_fourier_backward_workspace_size(const psf_optics* opt,
   if (grid)
     precision = resolve_fourier_backward_precision(n_pupil, grid->nx, grid->ny, precision);
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
-  if (precision == PSF_PREC_FP32_CHIRPZ) return 0;
+  if (precision == PSF_PREC_FP32_CHIRPZ || precision == PSF_PREC_SPLIT_TF32 ||
+      precision == PSF_PREC_TF32)
+    return 0;
   if (precision != PSF_PREC_FP32 && tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
     return 0;
   return backward_layout(nullptr, n_pupil, grid, precision).bytes;
@@ -744,8 +767,9 @@ extern "C" int psf_fourier_vectorial_backward(
     precision = resolve_fourier_backward_precision(n_pupil, grid->nx, grid->ny, precision);
   int r = check_fourier_args(opt, n_pupil, grid, precision);
   if (r) return r;
-  if (precision == PSF_PREC_FP32_CHIRPZ)
-    return fail(PSF_ERR_PRECISION, "the chirp-Z mode is forward only");
+  if (precision == PSF_PREC_FP32_CHIRPZ || precision == PSF_PREC_SPLIT_TF32 ||
+      precision == PSF_PREC_TF32)
+    return fail(PSF_ERR_PRECISION, "the chirp-Z and TF32 modes are forward only");
   if (precision != PSF_PREC_FP32) {
     if (const char* why = tc_fourier_bwd_supported(n_pupil, grid->nx, grid->ny))
       return fail(PSF_ERR_ARG, "%s", why);
@@ -936,7 +960,7 @@ extern "C" size_t psf_bessel_workspace_size(const psf_optics* base, int n_em,
                                             int nx, int ny, int precision) {
   precision = resolve_spherical_precision(n_theta, precision);
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
-  if (spherical_envelope(n_theta, precision)) return 0;
+  if (spherical_envelope(base, n_theta, precision)) return 0;
   return bessel_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, true,
                        precision).bytes;
 }
@@ -1163,7 +1187,7 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   int r = check_bessel_call(base, n_em, depth, zernike, n_zern, z_offsets, z, n_slices,
                             n_theta, n_r, nx, ny, dx, dy, precision);
   if (r) return r;
-  if ((r = spherical_envelope(n_theta, precision))) return r;
+  if ((r = spherical_envelope(base, n_theta, precision))) return r;
   if (!intensity && !profiles && n_slices > 0)
     return fail(PSF_ERR_ARG, "intensity and profiles are both NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
@@ -1545,13 +1569,13 @@ extern "C" int psf_bessel_harmonic_order(const double* zernike, int n_em, int n_
   return best;
 }
 
-static int check_harm_args(int m_max, int n_theta, int precision) {
+static int check_harm_args(const psf_optics* base, int m_max, int n_theta, int precision) {
   if (m_max < 0 || m_max > kHarmMaxM)
     return fail(PSF_ERR_ARG, "m_max %d outside [0, %d]", m_max, kHarmMaxM);
   if (precision != PSF_PREC_FP32 && !harm_split(precision))
     return fail(PSF_ERR_PRECISION, "harmonic path: precision %d is not FP32 or split FP16",
                 precision);
-  return spherical_envelope(n_theta, precision);
+  return spherical_envelope(base, n_theta, precision);
 }
 
 extern "C" size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int n_em,
@@ -1560,7 +1584,7 @@ extern "C" size_t psf_bessel_harmonic_workspace_size(const psf_optics* base, int
                                                      int precision) {
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, PSF_PREC_FP32)) return 0;
   precision = resolve_spherical_precision(n_theta, precision);
-  if (check_harm_args(m_max, n_theta, precision)) return 0;
+  if (check_harm_args(base, m_max, n_theta, precision)) return 0;
   return harm_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, m_max, precision).bytes;
 }
 
@@ -1577,7 +1601,7 @@ extern "C" int psf_bessel_vectorial_harmonic(const psf_optics* base, int n_em,
                             n_theta, n_r, nx, ny, dx, dy, PSF_PREC_FP32);
   if (r) return r;
   precision = resolve_spherical_precision(n_theta, precision);
-  if ((r = check_harm_args(m_max, n_theta, precision))) return r;
+  if ((r = check_harm_args(base, m_max, n_theta, precision))) return r;
   if (!(tail_tol >= 0.0 && tail_tol < 1.0))
     return fail(PSF_ERR_ARG, "tail_tol %g outside [0, 1)", tail_tol);
   if (!intensity && n_slices > 0) return fail(PSF_ERR_ARG, "intensity is NULL");

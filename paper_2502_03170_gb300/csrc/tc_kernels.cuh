@@ -84,7 +84,8 @@ struct TcOperands {
 };
 
 // Operands of the symmetry-folded forward (fold_kernels.cu), 16-bit, split
-// hi + lo, row pitch Kp = H rounded up to 16 (H = N/2):
+// hi + lo, row pitch Kp = H rounded up to 16 (H = N/2; 16-bit elements, or
+// 32-bit TF32 parts with the TF32 precisions):
 //   Zx, Zy  zoom halves C = cos, S = sin over the first half p' < H of the
 //           pupil and the first half of the outputs: [4][ceil(n/2)][Kp] with
 //           the variants C hi, C lo, S hi, S lo;
@@ -99,8 +100,10 @@ struct TcFoldOperands {
 };
 int tc_fold_kp(int N);
 const char* tc_fold_supported(int N, int nx, int ny);
-int tc_fold_zchunk(int N, int nx, int ny, int nz);
-void tc_fold_carve(char* base, size_t* off, int N, int nx, int ny, int zc, TcFoldOperands* out);
+// eb: operand element bytes, 2 (FP16 / BF16 parts) or 4 (TF32 parts)
+int tc_fold_zchunk(int N, int nx, int ny, int nz, int eb = 2);
+void tc_fold_carve(char* base, size_t* off, int N, int nx, int ny, int zc, TcFoldOperands* out,
+                   int eb = 2);
 // The folded forward over z-chunks of zc planes; arguments as
 // tc_fourier_forward.  Returns PSF_ERR_CUDA when a launch is refused.
 int tc_fold_forward(const TcFoldOperands& ops, NodeTable nodes, const float2* zz, int N,

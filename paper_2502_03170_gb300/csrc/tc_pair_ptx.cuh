@@ -54,6 +54,16 @@ PSF_D void mma_f16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
       : "memory");
 }
 
+// The same with 32-bit operands read as TF32 (kind::tf32, K = 8 per MMA).
+PSF_D void mma_tf32_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // arrive once on the mbarrier at this shared-memory offset in every CTA of mask
 PSF_D void mma_commit_pair(uint32_t bar, uint16_t mask) {
   asm volatile(

@@ -176,6 +176,21 @@ PSF_D void split16(float x, int bf16, uint16_t& hi, uint16_t& lo) {
   }
 }
 
+// x rounded to TF32 (10 explicit mantissa bits, nearest, ties away), kept in
+// an FP32 container as the tensor core reads it.
+PSF_D float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Splits x into TF32 hi + lo (three-product form); with one pass lo is 0.
+PSF_D void split_tf32(float x, int passes, uint32_t& hi, uint32_t& lo) {
+  const float h = round_tf32(x);
+  hi = __float_as_uint(h);
+  lo = passes == 3 ? __float_as_uint(round_tf32(x - h)) : 0u;
+}
+
 // The same split of an FP64 value (hi rounded from x, lo from x - hi).
 PSF_D void split16d(double v, int bf16, uint16_t& hi, uint16_t& lo) {
   if (bf16) {

@@ -4,7 +4,8 @@ Tolerance: max |I - I_ref| / max |I_ref| <= 1e-5 per stack for intensity and
 the same for the complex fields (the forward target), for the FP32 and both
 split contractions (the symmetry-folded form sums half of K per accumulator
 and stays within the bound inside the library's accuracy envelope: split
-FP16 up to n_pupil 512, split BF16 up to 1024; larger pupils are refused).
+FP16 and split TF32 up to n_pupil 512, split BF16 up to 1024; larger pupils
+are refused).
 The unfolded 2x2-block form (PSF_TC_FOLD=0, a comparison path) is held to
 3e-5: it sums four times as many terms per accumulator and measured 1.07e-5
 in split BF16."""
@@ -21,9 +22,9 @@ from paper_2502_03170_gb300 import workloads as W
 from .gpu_helpers import max_rel, oracle_optics
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp32": 1e-5, "split_fp16": 1e-5, "split_bf16": 1e-5}
+TOL = {"fp32": 1e-5, "split_fp16": 1e-5, "split_bf16": 1e-5, "split_tf32": 1e-5}
 TOL_UNFOLDED = 3e-5
-PRECS = ["fp32", "split_fp16", "split_bf16"]
+PRECS = ["fp32", "split_fp16", "split_bf16", "split_tf32"]
 
 
 def run_case(d, N, grid, zern=None, pm=None, precision="fp32", fields=True):
@@ -126,7 +127,7 @@ def test_cta_pair_kernel_matches_single_cta(lib, nx, ny, N, monkeypatch):
     assert max_rel(out["1"][2:3], Ir) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_fp16", "chirpz_fp32"])
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16", "split_tf32", "chirpz_fp32"])
 def test_short_chunks_from_a_small_workspace(lib, prec):
     """Handed a workspace below psf_fourier_workspace_size(), the forward
     runs shorter z-chunks; every plane's arithmetic is the same, so the stack
@@ -282,3 +283,29 @@ def test_auto_precision(lib, N, mode):
     assert np.array_equal(a, m.cpu().numpy())
     Ir = of.psf_fourier(oracle_optics(c["optics"]), N, c["grid"], zernike=c["zernike"])
     assert max_rel(a, Ir) <= 1e-5
+
+
+def test_tf32_modes(lib):
+    """3xTF32 (split TF32) holds 1e-5 up to n_pupil 512 and is refused beyond;
+    single-pass TF32 (a 10-bit mantissa per operand, measured 1.3e-4 to
+    3.4e-4 on the workload's planes) is refused unless the caller opts out of
+    the bound, and then stays within 1e-3; the adjoints take no TF32 mode."""
+    c = W.fourier(n_pupil=512, nx=64, nz=2)
+    opt = oracle_optics(c["optics"])
+    Ir = of.psf_fourier(opt, 512, c["grid"], zernike=c["zernike"])
+    I = api.fourier(c["optics"], 512, c["grid"], zernike=c["zernike"], precision="split_tf32")
+    assert max_rel(I.cpu().numpy(), Ir) <= 1e-5
+    with pytest.raises(_lib.PsfError) as e:
+        api.fourier(c["optics"], 1024, c["grid"], zernike=c["zernike"], precision="split_tf32")
+    assert e.value.code == _lib.PSF_ERR_PRECISION
+    with pytest.raises(_lib.PsfError) as e:
+        api.fourier(c["optics"], 512, c["grid"], zernike=c["zernike"], precision="tf32")
+    assert e.value.code == _lib.PSF_ERR_PRECISION
+    d = dict(c["optics"], outside_envelope=True)
+    I1 = api.fourier(d, 512, c["grid"], zernike=c["zernike"], precision="tf32").cpu().numpy()
+    assert 1e-6 < max_rel(I1, Ir) <= 1e-3
+    o = api.make_optics(c["optics"])
+    g = api.Grid(c["grid"])
+    for p in (_lib.PSF_PREC_SPLIT_TF32, _lib.PSF_PREC_TF32):
+        assert lib.psf_fourier_backward_workspace_size(ctypes.byref(o), 256,
+                                                       ctypes.byref(g.c), p) == 0
