@@ -129,8 +129,10 @@ extern "C" {
                                        Eq. 7 in Eq. 6, over the interfaces
                                        sample -> coverslip -> immersion (Snell
                                        angles, principal root where evanescent).
-                                       Fourier: every path; Bessel: the FP32
-                                       forward only (complex J_n operand)       */
+                                       Every path and adjoint; the split Bessel
+                                       contraction then runs per order n with
+                                       the complex g_n on the F operand, and
+                                       the Bessel adjoint contracts with B^H    */
 #define PSF_OUTSIDE_ENVELOPE     8  /* accept a precision mode outside the
                                        accuracy envelope below (results may miss
                                        the 1e-5 bound; for comparisons)        */
@@ -373,7 +375,8 @@ size_t psf_bessel_backward_workspace_size(const psf_optics* base, int n_emitters
  * dL/dI = grad_intensity.  The adjoint, with G = dL/dI and the complex
  * gradient g_X = dL/dRe X + i dL/dIm X:
  *   g_E_c = 2 G E_c;  g_I_n through the conjugate of Eq. 10 and the transposed
- *   radial interpolation;  g_F = sum_n B_n^T g_I_n (B_n the J_n operand);
+ *   radial interpolation;  g_F = sum_n B_n^H g_I_n (B_n the J_n operand,
+ *   complex with PSF_FRESNEL);
  *   Q_j = sum_{z of e} conj(g_F(theta_j, z)) F(theta_j, z);
  *   dL/dW_0(theta_j) = -Im Q_j,
  *   dL/dc_q  = sum_j Z_q(sin theta_j / s_max) dL/dW_0(theta_j)  (m = 0 Noll q;

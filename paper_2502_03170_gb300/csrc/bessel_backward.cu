@@ -799,19 +799,32 @@ void launch_bessel_adj_epilogue_staged(const BesselParams& p, float2* prof,
 }
 
 // ---------------------------------------------------------------------------
-// Kernel B: transposed radial contraction, g_F[s][j] = sum_row Bt[j][row]
-// g_P[s][row] (B real, rows = 3 N_r), FP32.  CTA tile 64 slices x 32 theta
-// nodes, 128 threads with 4 x 4 complex accumulators, 32-row K chunks staged
-// through shared memory.
+// Kernel B: transposed radial contraction, g_F[s][j] = sum_row
+// conj(Bt[j][row]) g_P[s][row] (rows = 3 N_r; Bt real, or complex with the
+// Fresnel weights), FP32.  CTA tile 64 slices x 32 theta nodes, 128 threads
+// with 4 x 4 complex accumulators, 32-row K chunks staged through shared
+// memory.
 // ---------------------------------------------------------------------------
 constexpr int AT_S = 64, AT_J = 32, AT_K = 32;
 
+PSF_D void adj_fma(float b, float2 p, float2& acc) {
+  acc.x = fmaf(b, p.x, acc.x);
+  acc.y = fmaf(b, p.y, acc.y);
+}
+PSF_D void adj_fma(float2 b, float2 p, float2& acc) {   // acc += conj(b) p
+  acc.x = fmaf(b.x, p.x, fmaf(b.y, p.y, acc.x));
+  acc.y = fmaf(b.x, p.y, fmaf(-b.y, p.x, acc.y));
+}
+PSF_D float adj_zero(float) { return 0.f; }
+PSF_D float2 adj_zero(float2) { return make_float2(0.f, 0.f); }
+
+template <typename TB>
 __global__ void __launch_bounds__(128)
-k_bessel_adj_contract(const float* __restrict__ Bt, const float2* __restrict__ gP,
+k_bessel_adj_contract(const TB* __restrict__ Bt, const float2* __restrict__ gP,
                       float2* __restrict__ gF, int n_slices, int n_theta, int rows) {
   // +1 padding: the transposing stores below hit distinct banks
   __shared__ float2 Ps[AT_K][AT_S + 1];
-  __shared__ float Bs[AT_K][AT_J + 1];
+  __shared__ TB Bs[AT_K][AT_J + 1];
   const int tid = threadIdx.x;
   const int s0 = blockIdx.x * AT_S, j0 = blockIdx.y * AT_J;
   const int ts = tid & 15, tj = tid >> 4;       // 16 slice quads x 8 theta quads
@@ -831,13 +844,14 @@ k_bessel_adj_contract(const float* __restrict__ Bt, const float2* __restrict__ g
     for (int q = tid; q < AT_J * AT_K; q += 128) {
       const int jj = q / AT_K, rr = q - jj * AT_K;
       const int jg = j0 + jj, rg = r0 + rr;
-      Bs[rr][jj] = (jg < n_theta && rg < rows) ? __ldg(&Bt[(size_t)jg * rows + rg]) : 0.f;
+      Bs[rr][jj] = (jg < n_theta && rg < rows) ? __ldg(&Bt[(size_t)jg * rows + rg])
+                                               : adj_zero(TB());
     }
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < AT_K; ++k) {
       float2 pv[4];
-      float bv[4];
+      TB bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         pv[a] = Ps[k][ts * 4 + a];
@@ -846,10 +860,7 @@ k_bessel_adj_contract(const float* __restrict__ Bt, const float2* __restrict__ g
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          acc[a][b].x = fmaf(bv[b], pv[a].x, acc[a][b].x);
-          acc[a][b].y = fmaf(bv[b], pv[a].y, acc[a][b].y);
-        }
+        for (int b = 0; b < 4; ++b) adj_fma(bv[b], pv[a], acc[a][b]);
     }
     __syncthreads();
   }
@@ -865,11 +876,15 @@ k_bessel_adj_contract(const float* __restrict__ Bt, const float2* __restrict__ g
   }
 }
 
-void launch_bessel_adj_contract(const BesselParams& p, const float* Bt, const float2* gP,
-                                float2* gF, cudaStream_t s) {
+void launch_bessel_adj_contract(const BesselParams& p, const float* Bt, const float2* BtC,
+                                const float2* gP, float2* gF, cudaStream_t s) {
   dim3 grid(ceil_div(p.n_slices, AT_S), ceil_div(p.n_theta, AT_J));
-  k_bessel_adj_contract<<<grid, 128, 0, s>>>(Bt, gP, gF, p.n_slices, p.n_theta,
-                                             3 * p.n_r);
+  if (BtC)
+    k_bessel_adj_contract<float2><<<grid, 128, 0, s>>>(BtC, gP, gF, p.n_slices, p.n_theta,
+                                                       3 * p.n_r);
+  else
+    k_bessel_adj_contract<float><<<grid, 128, 0, s>>>(Bt, gP, gF, p.n_slices, p.n_theta,
+                                                      3 * p.n_r);
 }
 
 // ---------------------------------------------------------------------------

@@ -49,9 +49,10 @@ void launch_bessel_adj_epilogue_staged(const BesselParams& p, float2* prof,
                                        const float* target, const float* grad_intensity,
                                        float* loss_slice, uint16_t* g_hi, uint16_t* g_lo,
                                        int kp, int* status, cudaStream_t s);
-// g_F[s][j] = sum_row Bt[j][row] g_P[s][row]
-void launch_bessel_adj_contract(const BesselParams& p, const float* Bt, const float2* gP,
-                                float2* gF, cudaStream_t s);
+// g_F[s][j] = sum_row conj(B[j][row]) g_P[s][row], B = Bt (real) or, when
+// BtC is non-null, the complex operand of the Fresnel weights
+void launch_bessel_adj_contract(const BesselParams& p, const float* Bt, const float2* BtC,
+                                const float2* gP, float2* gF, cudaStream_t s);
 // per-emitter gradients and loss
 void launch_bessel_adj_reduce(const BesselParams& p, ThetaTable t, EmitterTable et,
                               const int* z_offsets, const float2* zz, const float2* gF,

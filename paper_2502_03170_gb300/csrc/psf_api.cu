@@ -912,19 +912,25 @@ struct BesselLayout {
   size_t bytes;
 };
 
+// complex_g: the model's angular weights are complex (Fresnel coefficients)
+static bool bessel_complex_g(const psf_optics* base) {
+  return (base->flags & PSF_FRESNEL) && !(base->flags & PSF_SCALAR);
+}
+
 static BesselLayout bessel_layout(void* ws, int n_em, int n_slices, int n_theta,
                                   int n_r, int nx, int ny, bool own_profiles,
-                                  int precision, bool fp32_bt = false) {
+                                  int precision, bool complex_g, bool fp32_bt = false) {
   BesselLayout L;
   memset(&L, 0, sizeof(L));
   Carver c(ws);
   L.theta_tab = c.take<double>((size_t)(10 + kMaxM0 + 6) * n_theta);
   L.kappa = c.take<float>(2 * (size_t)n_theta);
-  if (precision == PSF_PREC_FP32 || fp32_bt)
+  if (precision == PSF_PREC_FP32 || (fp32_bt && !complex_g))
     L.Bt = c.take<float>((size_t)3 * n_r * n_theta);
-  if (precision == PSF_PREC_FP32) L.BtC = c.take<float2>((size_t)3 * n_r * n_theta);
+  if (precision == PSF_PREC_FP32 || (fp32_bt && complex_g))
+    L.BtC = c.take<float2>((size_t)3 * n_r * n_theta);
   if (precision != PSF_PREC_FP32)
-    tc_bessel_carve(c.base, &c.off, n_theta, n_r, n_slices, &L.tc);
+    tc_bessel_carve(c.base, &c.off, n_theta, n_r, n_slices, complex_g, &L.tc);
   L.et.amp = c.take<float>((size_t)n_em * n_theta);
   L.et.wfr = c.take<float>((size_t)n_em * n_theta);
   L.et.valid = c.take<int>(n_em);
@@ -962,7 +968,7 @@ extern "C" size_t psf_bessel_workspace_size(const psf_optics* base, int n_em,
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
   if (spherical_envelope(base, n_theta, precision)) return 0;
   return bessel_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, true,
-                       precision).bytes;
+                       precision, bessel_complex_g(base)).bytes;
 }
 
 // Host-side tables of one Bessel call and the setup launches shared by the
@@ -972,6 +978,7 @@ struct BesselRun {
   BesselParams bp;
   ThetaTable tt;
   double max_w;
+  double g_max;          // max |g_n(theta_j)| over orders and nodes
   bool split;
 };
 
@@ -1124,9 +1131,14 @@ static int bessel_prepare(const psf_optics* base, int n_em, const double* depth,
 
   R->split = !fp32_operand && precision != PSF_PREC_FP32;
   const bool split = R->split;
-  double max_w = 0.0;
+  double max_w = 0.0, g_max = 0.0;
   for (int j = 0; j < n_theta; ++j) max_w = fmax(max_w, T_w[j]);
+  for (int n = 0; n < 3; ++n)
+    for (int j = 0; j < n_theta; ++j)
+      g_max = fmax(g_max, hypot(T_g[(size_t)(2 * n) * n_theta + j],
+                                T_g[(size_t)(2 * n + 1) * n_theta + j]));
   R->max_w = max_w;
+  R->g_max = g_max;
   {
     TimingScope ts(kTimeSetup, s);
     if (split)
@@ -1163,10 +1175,6 @@ static int check_bessel_call(const psf_optics* base, int n_em, const double* dep
                              int ny, double dx, double dy, int precision) {
   int r = check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision);
   if (r) return r;
-  if ((base->flags & PSF_FRESNEL) && !(base->flags & PSF_SCALAR) &&
-      precision != PSF_PREC_FP32)
-    return fail(PSF_ERR_PRECISION,
-                "Fresnel weights on the Bessel path need PSF_PREC_FP32 (complex J_n operand)");
   if (!finite_pos(dx) || !finite_pos(dy)) return fail(PSF_ERR_ARG, "pixel pitch must be > 0");
   if (n_zern < 0 || n_zern > 66) return fail(PSF_ERR_ARG, "n_zern %d outside [0, 66]", n_zern);
   if (!depth || !z_offsets || (n_slices > 0 && !z) || (n_zern > 0 && !zernike))
@@ -1192,7 +1200,7 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
     return fail(PSF_ERR_ARG, "intensity and profiles are both NULL");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   BesselLayout L = bessel_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
-                                 profiles == nullptr, precision);
+                                 profiles == nullptr, precision, bessel_complex_g(base));
   if (ws_bytes < L.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.bytes);
   if ((r = resolve_output((void**)&intensity, "intensity")) ||
@@ -1208,8 +1216,8 @@ extern "C" int psf_bessel_vectorial(const psf_optics* base, int n_em,
   const BesselParams& bp = R.bp;
   if (n_slices > 0) {
     if (R.split) {
-      r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, precision, L.tc,
-                             L.prof, (int*)workspace, s);
+      r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, R.g_max, precision,
+                             L.tc, L.prof, (int*)workspace, s);
       if (r) return fail(r, "split-precision Bessel contraction launch failed");
     } else if (bp.complex_g) {
       TimingScope ts(kTimeBesselRadial, s);
@@ -1259,10 +1267,12 @@ static size_t n_pix_groups(int nx, int ny) {
 }
 
 static BesselBwdLayout bessel_bwd_layout(void* ws, int n_em, int n_slices, int n_theta,
-                                         int n_r, int nx, int ny, int precision) {
+                                         int n_r, int nx, int ny, int precision,
+                                         bool complex_g) {
   BesselBwdLayout B;
   memset(&B, 0, sizeof(B));
-  B.fwd = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, true, precision, true);
+  B.fwd = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, true, precision, complex_g,
+                        true);
   Carver c(ws);
   c.off = B.fwd.bytes;
   B.gF = c.take<float2>((size_t)n_slices * n_theta);
@@ -1279,7 +1289,7 @@ static BesselBwdLayout bessel_bwd_layout(void* ws, int n_em, int n_slices, int n
   q.n_r = n_r;
   B.sorted_form = bessel_adj_sorted_fits(q);
   if (B.sorted_form && precision != PSF_PREC_FP32)
-    tc_bessel_adj_carve(c.base, &c.off, n_theta, n_r, n_slices, &B.tc);
+    tc_bessel_adj_carve(c.base, &c.off, n_theta, n_r, n_slices, complex_g, &B.tc);
   B.bytes = align_up(c.off, 256);
   return B;
 }
@@ -1353,7 +1363,8 @@ extern "C" size_t psf_bessel_backward_workspace_size(const psf_optics* base, int
   precision = resolve_bessel_backward_precision(precision);
   if (check_bessel_args(base, n_em, n_slices, n_theta, n_r, nx, ny, precision)) return 0;
   if (nx > 4096 || ny > 4096 || n_r > 4096) return 0;
-  return bessel_bwd_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, precision).bytes;
+  return bessel_bwd_layout(nullptr, n_em, n_slices, n_theta, n_r, nx, ny, precision,
+                           bessel_complex_g(base)).bytes;
 }
 
 extern "C" int psf_bessel_vectorial_backward(
@@ -1370,14 +1381,12 @@ extern "C" int psf_bessel_vectorial_backward(
   if (r) return r;
   if (nx > 4096 || ny > 4096)
     return fail(PSF_ERR_ARG, "the Bessel adjoint takes nx, ny <= 4096");
-  if ((base->flags & PSF_FRESNEL) && !(base->flags & PSF_SCALAR))
-    return fail(PSF_ERR_ARG, "the Bessel adjoint does not take Fresnel weights");
   if (n_slices > 0 && !target && !grad_intensity)
     return fail(PSF_ERR_ARG, "target and grad_intensity are both NULL");
   if (loss && !target) return fail(PSF_ERR_ARG, "loss needs a target");
   if (!workspace) return fail(PSF_ERR_WORKSPACE, "workspace is NULL");
   BesselBwdLayout B = bessel_bwd_layout(workspace, n_em, n_slices, n_theta, n_r, nx, ny,
-                                        precision);
+                                        precision, bessel_complex_g(base));
   if (ws_bytes < B.bytes)
     return fail(PSF_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, B.bytes);
   BesselLayout& L = B.fwd;
@@ -1392,8 +1401,14 @@ extern "C" int psf_bessel_vectorial_backward(
   if (split) {
     // the adjoint contraction takes the J_n operand unscaled in FP32 as well
     TimingScope ts(kTimeSetup, s);
-    launch_bessel_jmat(bp, R.tt, L.Bt, s);
+    if (bp.complex_g)
+      launch_bessel_jmat_complex(bp, R.tt, L.BtC, s);
+    else
+      launch_bessel_jmat(bp, R.tt, L.Bt, s);
   }
+  // the adjoint contraction's operand: B^H with complex weights
+  const float* adj_Bt = bp.complex_g ? nullptr : L.Bt;
+  const float2* adj_BtC = bp.complex_g ? L.BtC : nullptr;
   if (n_slices > 0) {
     PixTables pt;
     build_pix_groups(nx, ny, dx, dy, n_r, bp.dr, bp.pol, pt);
@@ -1410,9 +1425,12 @@ extern "C" int psf_bessel_vectorial_backward(
     upload_async(B.cell_start, pt.start.data(), pt.start.size() * sizeof(int), s);
     // recompute the profiles (per-z recomputation: nothing of the forward is stored)
     if (split) {
-      r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, precision, L.tc,
-                             L.prof, (int*)workspace, s);
+      r = tc_bessel_contract(bp, R.tt, L.et, L.slice_em, L.zz, R.max_w, R.g_max, precision,
+                             L.tc, L.prof, (int*)workspace, s);
       if (r) return fail(r, "split-precision Bessel contraction launch failed");
+    } else if (bp.complex_g) {
+      TimingScope ts(kTimeBesselRadial, s);
+      launch_bessel_profiles_f32c(bp, R.tt, L.BtC, L.et, L.slice_em, L.zz, L.prof, s);
     } else {
       TimingScope ts(kTimeBesselRadial, s);
       launch_bessel_profiles_f32(bp, R.tt, L.Bt, L.et, L.slice_em, L.zz, L.prof, s);
@@ -1433,7 +1451,7 @@ extern "C" int psf_bessel_vectorial_backward(
                                             B.gfg, B.sorted_f, B.cell_start, target,
                                             target ? nullptr : grad_intensity, B.loss_slice,
                                             B.tc.G_hi, B.tc.G_lo, B.tc.kp, s);
-        r = tc_bessel_adj_contract(bp, L.Bt, B.tc, B.gF, (int*)workspace, s);
+        r = tc_bessel_adj_contract(bp, adj_Bt, adj_BtC, B.tc, B.gF, (int*)workspace, s);
         if (r) return fail(r, "tensor-core adjoint contraction launch failed");
       } else if (sorted_form) {
         if (staged)
@@ -1446,12 +1464,12 @@ extern "C" int psf_bessel_vectorial_backward(
                                             B.gfg, B.sorted_f, B.cell_start, target,
                                             target ? nullptr : grad_intensity, B.loss_slice,
                                             nullptr, nullptr, 0, s);
-        launch_bessel_adj_contract(bp, L.Bt, L.prof, B.gF, s);
+        launch_bessel_adj_contract(bp, adj_Bt, adj_BtC, L.prof, B.gF, s);
       } else {
         launch_bessel_adj_epilogue(bp, L.prof, L.slice_em, L.et.valid, B.groups,
                                    B.cell_start, target, target ? nullptr : grad_intensity,
                                    B.loss_slice, s);
-        launch_bessel_adj_contract(bp, L.Bt, L.prof, B.gF, s);
+        launch_bessel_adj_contract(bp, adj_Bt, adj_BtC, L.prof, B.gF, s);
       }
     }
   }
@@ -1501,7 +1519,7 @@ static HarmLayout harm_layout(void* ws, int n_em, int n_slices, int n_theta, int
   const bool split = harm_split(precision);
   HarmLayout H;
   memset(&H, 0, sizeof(H));
-  H.b = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, false, PSF_PREC_FP32);
+  H.b = bessel_layout(ws, n_em, n_slices, n_theta, n_r, nx, ny, false, PSF_PREC_FP32, false);
   Carver c(ws);
   c.off = H.b.bytes;
   const int n_ord = 2 * m_max + 5;

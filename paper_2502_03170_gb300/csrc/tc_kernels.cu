@@ -76,6 +76,9 @@ struct Params {
   float2* prof;
   int rows_total;       // 3 N_r
   int n_slices;
+  // mode 2 with conj_pairs: A rows (r, Re / Im of a complex operand b_r),
+  // prof[s][r] = conj(b_r) . x_s from the two rows' accumulators
+  int conj_pairs;
   const float* scale_ptr;   // device scalar: 1 / (S_B S_F)
   int m_fastest;        // tile order: consecutive tiles share the B tile
   // mode 3 (adjoint source, stage-2 recomputation): g = 2 (I - T) or dL/dI,
@@ -172,6 +175,27 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
         // Bessel: prof[s][row] = scale * (D[row][2k], D[row][2k+1]), s = nt*96 + k
         const int grow = mt * BM + row;
         const float sc = *p.scale_ptr;
+        if (p.conj_pairs) {
+          // rows 2r (Re b) and 2r + 1 (Im b) sit in adjacent lanes:
+          // conj(b) x = (Re b Re x + Im b Im x) + i (Re b Im x - Im b Re x)
+          const int orow = grow >> 1;
+          const bool odd = (lane & 1) != 0;
+          for (int h = 0; h < BN / 32; ++h) {
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(h * 32), r);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const float xr = __uint_as_float(r[2 * k]), xi = __uint_as_float(r[2 * k + 1]);
+              const float pr = __shfl_xor_sync(0xffffffffu, xr, 1);
+              const float pi = __shfl_xor_sync(0xffffffffu, xi, 1);
+              const int s = nt * (BN / 2) + h * 16 + k;
+              if (!odd && orow < p.rows_total && s < p.n_slices)
+                p.prof[(size_t)s * p.rows_total + orow] =
+                    make_float2(sc * (xr + pi), sc * (xi - pr));
+            }
+          }
+          return;
+        }
         for (int h = 0; h < BN / 32; ++h) {
           uint32_t r[32];
           tmem_ld32(tbase + (uint32_t)(h * 32), r);
@@ -1707,16 +1731,19 @@ int tc_fourier_backward(const TcBwdOperands& ops, NodeTable nodes, const float2*
 namespace tc {
 
 // B[(n, i)][j] = S_B w_j g_n(theta_j) J_n(k r_i sin theta_j) (Eq. 11), FP64,
-// columns j >= n_theta zero.
+// columns j >= n_theta zero.  row_pitch rows per order (rows i >= N_r zero);
+// with complex weights (Fresnel) g_n stays out of this operand (with_g 0)
+// and rides on the per-order F operand instead.
 __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
-                                    int bf16, int Kp, uint16_t* hi, uint16_t* lo) {
+                                    int bf16, int Kp, int row_pitch, int with_g,
+                                    uint16_t* hi, uint16_t* lo) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int rows = 3 * p.n_r;
+  const int rows = 3 * row_pitch;
   if (idx >= (long long)rows * Kp) return;
   const int row = (int)(idx / Kp), j = (int)(idx - (long long)row * Kp);
   double v = 0.0;
-  if (j < p.n_theta) {
-    const int n = row / p.n_r, i = row - n * p.n_r;
+  const int n = row / row_pitch, i = row - n * row_pitch;
+  if (j < p.n_theta && i < p.n_r) {
     const double st = t.sin_t[j];
     const double x = p.k * (i * p.dr) * st;
     double jn_v;
@@ -1727,7 +1754,7 @@ __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
     } else {
       jn_v = x > 0.0 ? jn(2, x) : 0.0;   // J_2(0) = 0
     }
-    v = sB * t.w[j] * t.g[(2 * n) * p.n_theta + j] * jn_v;   // real weights only
+    v = sB * t.w[j] * (with_g ? t.g[(2 * n) * p.n_theta + j] : 1.0) * jn_v;
   }
   uint16_t h, l;
   split16d(v, bf16, h, l);
@@ -1736,10 +1763,11 @@ __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
 }
 
 // F rows (s, re) and (s, im): S_F amp e^{2 pi i (wfr + n_i z_s cos / lambda)};
-// S_F is the power of two that keeps the largest |F0| below 2^14.  Block
-// (64, 4): one slice per threadIdx.y, each thread four consecutive theta
-// nodes (Kp is a multiple of 8), stored as 8-byte packs of four 16-bit
-// values per row.
+// S_F is the power of two that keeps the largest |F0| (times g_max) below
+// 2^14.  With complex weights (n_ord 3) the operand holds one plane of rows
+// per order, g_n(theta_j) F: rows (n, s, re/im).  Block (64, 4): one slice
+// per threadIdx.y, each thread four consecutive theta nodes (Kp is a
+// multiple of 8), stored as 8-byte packs of four 16-bit values per row.
 constexpr int FG_TX = 64, FG_TY = 4;
 
 PSF_D uint2 pack4(const uint16_t (&v)[4]) {
@@ -1751,49 +1779,74 @@ __global__ void __launch_bounds__(FG_TX * FG_TY)
 k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable et,
                     const int* __restrict__ slice_em, const float2* __restrict__ zz,
                     const unsigned* __restrict__ amp_max, int Kp, int bf16, float sB,
-                    uint16_t* hi, uint16_t* lo, float* out_scale) {
-  const float am = __uint_as_float(*amp_max);
+                    int n_ord, float g_max, uint16_t* hi, uint16_t* lo, float* out_scale) {
+  const float am = __uint_as_float(*amp_max) * g_max;
   const float sF = am > 0.f ? exp2f(floorf(log2f(16384.f / am))) : 1.f;
   if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *out_scale = 1.f / (sB * sF);
   const int s = blockIdx.x * FG_TY + threadIdx.y;
   if (s >= p.n_slices) return;
   const int e = slice_em[s];
   const float2 z = zz[s];
-  const size_t row0 = (size_t)(2 * s) * Kp;
+  const size_t plane_rows = 2 * (size_t)p.n_slices;
   for (int q = threadIdx.x; q < (Kp >> 2); q += FG_TX) {
-    uint16_t hr[4], lr[4], hm[4], lm[4];
+    float2 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = 4 * q + u;
-      float2 v = make_float2(0.f, 0.f);
+      v[u] = make_float2(0.f, 0.f);
       if (j < p.n_theta && e >= 0) {
         const size_t ej = (size_t)e * p.n_theta + j;
         const float2 c =
             cis_cycles(frac_mul_add(f2x{t.kh[j], t.kl[j]}, f2x{z.x, z.y}, et.wfr[ej]));
         const float a = sF * et.amp[ej];
-        v = make_float2(a * c.x, a * c.y);
+        v[u] = make_float2(a * c.x, a * c.y);
       }
-      split16(v.x, bf16, hr[u], lr[u]);
-      split16(v.y, bf16, hm[u], lm[u]);
     }
-    const size_t r0 = row0 + 4 * q, r1 = r0 + Kp;
-    *reinterpret_cast<uint2*>(hi + r0) = pack4(hr);
-    *reinterpret_cast<uint2*>(lo + r0) = pack4(lr);
-    *reinterpret_cast<uint2*>(hi + r1) = pack4(hm);
-    *reinterpret_cast<uint2*>(lo + r1) = pack4(lm);
+    for (int n = 0; n < n_ord; ++n) {
+      uint16_t hr[4], lr[4], hm[4], lm[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = 4 * q + u;
+        float2 w = v[u];
+        if (n_ord > 1 && j < p.n_theta) {
+          const float2 g = make_float2((float)t.g[(2 * n) * p.n_theta + j],
+                                       (float)t.g[(2 * n + 1) * p.n_theta + j]);
+          w = cmul(g, w);
+        }
+        split16(w.x, bf16, hr[u], lr[u]);
+        split16(w.y, bf16, hm[u], lm[u]);
+      }
+      const size_t r0 = ((size_t)n * plane_rows + 2 * (size_t)s) * Kp + 4 * q, r1 = r0 + Kp;
+      *reinterpret_cast<uint2*>(hi + r0) = pack4(hr);
+      *reinterpret_cast<uint2*>(lo + r0) = pack4(lr);
+      *reinterpret_cast<uint2*>(hi + r1) = pack4(hm);
+      *reinterpret_cast<uint2*>(lo + r1) = pack4(lm);
+    }
   }
 }
 
 // Adjoint operand: A[j][row] = Bt[j][row] (FP32 J_n operand, theta-major)
 // split into BF16 hi + lo with row pitch kp (columns >= rows zero); thread 0
-// also stores the unit output scale of the contraction.
-__global__ void k_bessel_adj_bt_split(const float* __restrict__ Bt, int n_theta, int rows,
+// also stores the unit output scale of the contraction.  With the complex
+// operand BtC (Fresnel weights) the rows interleave A[2j] = Re BtC[j] and
+// A[2j + 1] = Im BtC[j].
+__global__ void k_bessel_adj_bt_split(const float* __restrict__ Bt,
+                                      const float2* __restrict__ BtC, int n_theta, int rows,
                                       int kp, uint16_t* hi, uint16_t* lo, float* scale) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx == 0) *scale = 1.f;
-  if (idx >= (long long)n_theta * kp) return;
-  const int j = (int)(idx / kp), q = (int)(idx - (long long)j * kp);
-  const float v = q < rows ? Bt[(size_t)j * rows + q] : 0.f;
+  const int a_rows = BtC ? 2 * n_theta : n_theta;
+  if (idx >= (long long)a_rows * kp) return;
+  const int ar = (int)(idx / kp), q = (int)(idx - (long long)ar * kp);
+  float v = 0.f;
+  if (q < rows) {
+    if (BtC) {
+      const float2 b = BtC[(size_t)(ar >> 1) * rows + q];
+      v = (ar & 1) ? b.y : b.x;
+    } else {
+      v = Bt[(size_t)ar * rows + q];
+    }
+  }
   uint16_t h, l;
   split16(v, 1, h, l);
   hi[idx] = h;
@@ -1805,7 +1858,7 @@ __global__ void k_bessel_adj_bt_split(const float* __restrict__ Bt, int n_theta,
 int tc_bessel_kp(int n_theta) { return (n_theta + 7) / 8 * 8; }
 
 void tc_bessel_adj_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
-                         TcBesselAdj* out) {
+                         bool complex_g, TcBesselAdj* out) {
   auto take = [&](size_t bytes) -> char* {
     *off = align_up(*off, 1024);
     char* p = base ? base + *off : nullptr;
@@ -1814,21 +1867,23 @@ void tc_bessel_adj_carve(char* base, size_t* off, int n_theta, int n_r, int n_sl
   };
   out->kp = tc_bessel_kp(3 * n_r);
   const size_t kp = out->kp;
-  out->A_hi = (uint16_t*)take((size_t)n_theta * kp * 2);
-  out->A_lo = (uint16_t*)take((size_t)n_theta * kp * 2);
+  const size_t a_rows = (complex_g ? 2 : 1) * (size_t)n_theta;
+  out->A_hi = (uint16_t*)take(a_rows * kp * 2);
+  out->A_lo = (uint16_t*)take(a_rows * kp * 2);
   out->G_hi = (uint16_t*)take(2 * (size_t)n_slices * kp * 2 + 2);
   out->G_lo = (uint16_t*)take(2 * (size_t)n_slices * kp * 2 + 2);
   out->scale = (float*)take(sizeof(float));
 }
 
-int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesselAdj& ops,
-                           float2* gF, int* status, cudaStream_t s) {
+int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const float2* BtC,
+                           const TcBesselAdj& ops, float2* gF, int* status, cudaStream_t s) {
   using namespace tc;
   const int rows = 3 * p.n_r, kp = ops.kp;
+  const int a_rows = BtC ? 2 * p.n_theta : p.n_theta;
   {
-    const long long n = (long long)p.n_theta * kp;
+    const long long n = (long long)a_rows * kp;
     k_bessel_adj_bt_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        Bt, p.n_theta, rows, kp, ops.A_hi, ops.A_lo, ops.scale);
+        Bt, BtC, p.n_theta, rows, kp, ops.A_hi, ops.A_lo, ops.scale);
   }
   // K extent = 3 N_r (columns past it read as zero), row pitch kp
   auto map2 = [&](CUtensorMap* m, const uint16_t* base, int nrows, int box_rows) {
@@ -1845,13 +1900,13 @@ int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesse
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
   CUtensorMap mAh, mAl, mGh, mGl;
-  if (!(map2(&mAh, ops.A_hi, p.n_theta, BM) && map2(&mAl, ops.A_lo, p.n_theta, BM) &&
+  if (!(map2(&mAh, ops.A_hi, a_rows, BM) && map2(&mAl, ops.A_lo, a_rows, BM) &&
         map2(&mGh, ops.G_hi, 2 * p.n_slices, BN) && map2(&mGl, ops.G_lo, 2 * p.n_slices, BN)))
     return PSF_ERR_CUDA;
   Params q;
   memset(&q, 0, sizeof(q));
   q.planes = 1;
-  q.m_tiles = ceil_div(p.n_theta, BM);
+  q.m_tiles = ceil_div(a_rows, BM);
   q.n_tiles = ceil_div(2 * p.n_slices, BN);
   q.k_chunks = ceil_div(rows, BK);
   q.idesc = make_idesc(1);
@@ -1859,6 +1914,7 @@ int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesse
   q.bf16 = 1;
   q.prof = gF;                 // gF[s][j]: "rows" of this contraction are theta nodes
   q.rows_total = p.n_theta;
+  q.conj_pairs = BtC ? 1 : 0;  // rows (j, Re / Im of the complex operand)
   q.n_slices = p.n_slices;
   q.scale_ptr = ops.scale;
   q.m_fastest = 1;
@@ -1867,7 +1923,7 @@ int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesse
 }
 
 void tc_bessel_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
-                     TcBessel* out) {
+                     bool complex_g, TcBessel* out) {
   auto take = [&](size_t bytes) -> char* {
     *off = align_up(*off, 1024);
     char* p = base ? base + *off : nullptr;
@@ -1875,42 +1931,50 @@ void tc_bessel_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices
     return p;
   };
   const size_t Kp = tc_bessel_kp(n_theta);
-  out->B_hi = (uint16_t*)take(3 * (size_t)n_r * Kp * 2);
-  out->B_lo = (uint16_t*)take(3 * (size_t)n_r * Kp * 2);
-  out->F_hi = (uint16_t*)take(2 * (size_t)n_slices * Kp * 2 + 2);
-  out->F_lo = (uint16_t*)take(2 * (size_t)n_slices * Kp * 2 + 2);
+  // complex weights: J_n planes of n_r_pad rows, F planes per order
+  const size_t b_rows = 3 * (size_t)(complex_g ? tc_harm_n_r_pad(n_r) : n_r);
+  const size_t f_rows = (complex_g ? 3 : 1) * 2 * (size_t)n_slices;
+  out->B_hi = (uint16_t*)take(b_rows * Kp * 2);
+  out->B_lo = (uint16_t*)take(b_rows * Kp * 2);
+  out->F_hi = (uint16_t*)take(f_rows * Kp * 2 + 2);
+  out->F_lo = (uint16_t*)take(f_rows * Kp * 2 + 2);
+  out->need = complex_g ? (unsigned char*)take(3 * (size_t)ceil_div(2 * n_slices, tc::BN) + 1)
+                        : nullptr;
   out->amp_max = (unsigned*)take(sizeof(unsigned));
   out->out_scale = (float*)take(sizeof(float));
 }
 
-static float bessel_sB(double max_w) {
-  // |B| <= max_j w_j * |g_n| (<= 2) * |J_n| (<= 1)
-  return pow2_scale(2.0 * max_w, 16384.0);
+static float bessel_sB(const BesselParams& p, double max_w) {
+  // |B| <= max_j w_j * |g_n| (<= 2 for the real weights) * |J_n| (<= 1);
+  // complex weights leave B = w_j J_n
+  return pow2_scale((p.complex_g ? 1.0 : 2.0) * max_w, 16384.0);
 }
 
 void tc_bessel_jmat(const BesselParams& p, ThetaTable t, double max_w,
                     int precision, const TcBessel& ops, cudaStream_t s) {
   const int Kp = tc_bessel_kp(p.n_theta);
-  const long long n = 3LL * p.n_r * Kp;
+  const int pitch = p.complex_g ? tc_harm_n_r_pad(p.n_r) : p.n_r;
+  const long long n = 3LL * pitch * Kp;
   tc::k_bessel_jmat_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-      p, t, (double)bessel_sB(max_w), precision == PSF_PREC_SPLIT_BF16 ? 1 : 0, Kp,
-      ops.B_hi, ops.B_lo);
+      p, t, (double)bessel_sB(p, max_w), precision == PSF_PREC_SPLIT_BF16 ? 1 : 0, Kp,
+      pitch, p.complex_g ? 0 : 1, ops.B_hi, ops.B_lo);
 }
 
 int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
-                       const int* slice_em, const float2* zz, double max_w,
+                       const int* slice_em, const float2* zz, double max_w, double g_max,
                        int precision, const TcBessel& ops, float2* prof,
                        int* status, cudaStream_t s) {
   using namespace tc;
   const int bf16 = precision == PSF_PREC_SPLIT_BF16 ? 1 : 0;
   const int Kp = tc_bessel_kp(p.n_theta);
-  const float sB = bessel_sB(max_w);
+  const float sB = bessel_sB(p, max_w);
+  const int n_ord = p.complex_g ? 3 : 1;
   {
     TimingScope ts(kTimeSetup, s);
     const unsigned nb = (unsigned)(p.n_slices > 0 ? ceil_div(p.n_slices, FG_TY) : 1);
     k_bessel_fgen_split<<<nb, dim3(FG_TX, FG_TY), 0, s>>>(
-        p, t, et, slice_em, zz, ops.amp_max, Kp, bf16, sB, ops.F_hi, ops.F_lo,
-        ops.out_scale);
+        p, t, et, slice_em, zz, ops.amp_max, Kp, bf16, sB, n_ord,
+        p.complex_g ? (float)g_max : 1.f, ops.F_hi, ops.F_lo, ops.out_scale);
   }
   // K extent = n_theta (columns past it read as zero), row pitch Kp
   auto map2 = [&](CUtensorMap* m, const uint16_t* base, int rows, int box_rows) {
@@ -1928,6 +1992,40 @@ int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
   };
   CUtensorMap mBh, mBl, mFh, mFl;
   const int rows = 3 * p.n_r;
+  if (p.complex_g) {
+    // complex weights: per order n a tile grid over (radius, slice column)
+    // with A = S_B w_j J_n (plane n of n_r_pad rows) and B = S_F g_n F
+    // (plane n of 2 n_slices rows) -- the per-order contraction of the
+    // harmonic path with orders 0..2
+    const int n_r_pad = tc_harm_n_r_pad(p.n_r);
+    const int n_tiles = ceil_div(2 * p.n_slices, BN);
+    if (!(map2(&mBh, ops.B_hi, 3 * n_r_pad, BM) && map2(&mBl, ops.B_lo, 3 * n_r_pad, BM) &&
+          map2(&mFh, ops.F_hi, 6 * p.n_slices, BN) && map2(&mFl, ops.F_lo, 6 * p.n_slices, BN)))
+      return PSF_ERR_CUDA;
+    cudaMemsetAsync(ops.need, 1, 3 * (size_t)n_tiles, s);
+    Params q;
+    memset(&q, 0, sizeof(q));
+    q.planes = 3;
+    q.m_tiles = n_r_pad / BM;
+    q.n_tiles = n_tiles;
+    q.k_chunks = ceil_div(p.n_theta, BK);
+    q.idesc = make_idesc(bf16);
+    q.mode = 5;
+    q.bf16 = bf16;
+    q.prof = prof;
+    q.rows_total = p.n_r;
+    q.n_slices = p.n_slices;
+    q.scale_ptr = ops.out_scale;
+    q.m_fastest = 1;
+    q.status = status;
+    q.need = ops.need;
+    q.n_ord = 3;
+    q.hL = 0;
+    q.n_r_pad = n_r_pad;
+    q.b_rows_per_plane = 2 * p.n_slices;
+    TimingScope ts(kTimeBesselRadial, s);
+    return launch_gemm(mBh, mBl, mFh, mFl, q, s);
+  }
   if (!(map2(&mBh, ops.B_hi, rows, BM) && map2(&mBl, ops.B_lo, rows, BM) &&
         map2(&mFh, ops.F_hi, 2 * p.n_slices, BN) && map2(&mFl, ops.F_lo, 2 * p.n_slices, BN)))
     return PSF_ERR_CUDA;

@@ -19,29 +19,34 @@ namespace psf {
 // Split-precision operands of the Bessel radial contraction
 //   prof[s][(n, i)] = sum_j B[(n, i)][j] F[j][s]  (real B, complex F):
 // B rows (n, i) x K columns (theta nodes, padded to Kp = 8k), F rows
-// (s, re/im) interleaved, both split hi + lo.
+// (s, re/im) interleaved, both split hi + lo.  With complex weights g_n
+// (Fresnel coefficients) B = w_j J_n holds three planes of n_r_pad rows and
+// F one plane per order, g_n F; the contraction runs per order.
 struct TcBessel {
-  uint16_t *B_hi, *B_lo;     // [3 N_r][Kp]
-  uint16_t *F_hi, *F_lo;     // [2 n_slices][Kp]
+  uint16_t *B_hi, *B_lo;     // [3 N_r][Kp]  (complex weights: [3][n_r_pad][Kp])
+  uint16_t *F_hi, *F_lo;     // [2 n_slices][Kp]  (complex weights: [3][2 n_slices][Kp])
+  unsigned char* need;       // complex weights: per-order tile flags (all set)
   unsigned* amp_max;         // device max of |F0| (float bits), zeroed per call
   float* out_scale;          // device 1 / (S_B S_F)
 };
 
 int tc_bessel_kp(int n_theta);
 void tc_bessel_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
-                     TcBessel* out);
-// J_n operand in split form (per call).
+                     bool complex_g, TcBessel* out);
+// J_n operand in split form (per call; layout from p.complex_g).
 void tc_bessel_jmat(const BesselParams& p, ThetaTable t, double max_w,
                     int precision, const TcBessel& ops, cudaStream_t s);
-// F operand from the per-emitter table and the contraction into prof.
+// F operand from the per-emitter table and the contraction into prof;
+// g_max bounds |g_n| over the nodes (used with complex weights).
 int tc_bessel_contract(const BesselParams& p, ThetaTable t, EmitterTable et,
-                       const int* slice_em, const float2* zz, double max_w,
+                       const int* slice_em, const float2* zz, double max_w, double g_max,
                        int precision, const TcBessel& ops, float2* prof,
                        int* status, cudaStream_t s);
 
 // Split-precision operands of the Bessel adjoint contraction
-//   g_F[s][j] = sum_row Bt[j][row] g_P[s][row]   (real Bt, complex g_P):
-// A rows j x K columns (3 N_r, pitch kp), g_P rows (s, re/im), BF16 hi + lo.
+//   g_F[s][j] = sum_row conj(Bt[j][row]) g_P[s][row]   (complex g_P):
+// A rows j x K columns (3 N_r, pitch kp), g_P rows (s, re/im), BF16 hi + lo;
+// a complex Bt (Fresnel weights) gives A rows (j, Re / Im).
 // Harmonic radial contraction on the tensor cores (split hi + lo operands):
 // per order l' = l + m_max + 2, prof[col][l'][i] = sum_j A[|l|][i][j] B[l'][col][j]
 // over the columns col = 3 s + c of a slice chunk.
@@ -66,15 +71,16 @@ int tc_harm_contract(const TcHarm& ops, int n_theta, int n_r, int m_max, int n_c
 
 struct TcBesselAdj {
   int kp;
-  uint16_t *A_hi, *A_lo;     // [n_theta][kp]
+  uint16_t *A_hi, *A_lo;     // [n_theta][kp] (complex weights: [2 n_theta][kp])
   uint16_t *G_hi, *G_lo;     // [2 n_slices][kp]
   float* scale;              // device 1.0 (BF16 needs no pre-scaling)
 };
 void tc_bessel_adj_carve(char* base, size_t* off, int n_theta, int n_r, int n_slices,
-                         TcBesselAdj* out);
-// A operand from the FP32 J_n operand, then the contraction into gF.
-int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const TcBesselAdj& ops,
-                           float2* gF, int* status, cudaStream_t s);
+                         bool complex_g, TcBesselAdj* out);
+// A operand from the FP32 J_n operand (Bt real, or BtC complex when
+// non-null), then the contraction into gF.
+int tc_bessel_adj_contract(const BesselParams& p, const float* Bt, const float2* BtC,
+                           const TcBesselAdj& ops, float2* gF, int* status, cudaStream_t s);
 
 struct TcOperands {
   uint16_t *Ax_hi, *Ax_lo;   // [2 nx][2 N] zoom-matrix blocks

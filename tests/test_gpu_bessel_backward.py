@@ -84,6 +84,25 @@ def test_target_loss_parity(lib, pol, nx, ny, prec):
     assert torch.all(res["grad_zernike"][:, 5] == 0)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nx,ny,n_r", [(16, 16, 40), (13, 21, 40), (180, 177, 256)])
+def test_fresnel_weights(lib, prec, nx, ny, n_r):
+    """Complex g_n (Fresnel coefficients, Eq. 7 in Eq. 11): the adjoint
+    contracts with B^H.  16 x 16 and 13 x 21 take the sorted epilogue and
+    (split modes) the tensor-core contraction with the (Re, Im) row pairs;
+    180 x 177 the one-pass epilogue and the FP32 contraction."""
+    geo = dict(n_theta=24, n_r=n_r, nx=nx, ny=ny, dx=0.05 * 16 / nx, dy=0.045 * 16 / ny)
+    d = dict(W.optics_gibson_lanni(0.0), pol=(0.6, 0.48 + 0.64j), fresnel=True)
+    opt = oracle_optics(d)
+    depth, zern, offs, z, w0 = batch(seed=21)
+    T = target_for(opt, depth, zern, offs, z, geo)
+    res = api.bessel_backward(d, depth, zern, offs, z, target=T, project=True,
+                              phase_theta=w0, precision=prec, **geo)
+    ref = oa.loss_and_grads_batch(opt, depth, zern, offs, z, phase_theta=w0,
+                                  project=True, target=T, **geo)
+    compare(res, ref)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "split_fp16"])
 def test_grad_intensity_mode_and_determinism(lib, prec):
     geo = dict(n_theta=48, n_r=96, nx=40, ny=34, dx=0.03, dy=0.03)

@@ -73,19 +73,29 @@ def test_bessel_scalar(lib, prec):
         assert max_rel(I[a:b], Ir) <= TOL[prec], e
 
 
-def test_bessel_fresnel_fp32_and_split_rejected(lib):
+@pytest.mark.parametrize("prec", ["fp32", "split_fp16"])
+@pytest.mark.parametrize("geo,nz", [((80, 48, 17, 20, 0.03, 0.03), (3, 2)),
+                                    ((200, 300, 64, 61, 0.02, 0.02), (40, 1, 57, 9))])
+def test_bessel_fresnel(lib, prec, geo, nz):
+    """Complex angular weights (Eq. 7 in Eq. 11).  Split FP16 runs the radial
+    contraction per order n with g_n on the F operand; the second case spans
+    several radius tiles (300 radii), slice tiles straddling the order planes
+    and a ragged theta tail (200 nodes)."""
     d = model(W.optics_gibson_lanni(0.0), fresnel=True, pol=W.CIRCULAR)
-    depth = np.array([1.0, 4.0])
-    zern = np.zeros((2, 11))
-    zern[:, 10] = [0.1, -0.2]
-    offs = np.array([0, 3, 5], dtype=np.int32)
-    z = np.array([-0.5, 0.0, 0.4, -0.2, 0.6])
-    geo = (80, 48, 17, 20, 0.03, 0.03)
-    I = api.bessel(d, depth, zern, offs, z, *geo).cpu().numpy()
-    Ir = ob.psf_bessel_batch(oracle_optics(d), depth, zern, offs, z, *geo)
-    assert max_rel(I, Ir) <= 1e-5
-    with pytest.raises(_lib.PsfError):
-        api.bessel(d, depth, zern, offs, z, *geo, precision="split_fp16")
+    g = np.random.default_rng(len(nz))
+    n_em = len(nz)
+    depth = g.uniform(0.5, 5.0, n_em)
+    zern = np.zeros((n_em, 11))
+    zern[:, 10] = g.normal(0, 0.15, n_em)
+    zern[:, 3] = g.normal(0, 0.2, n_em)
+    offs = np.concatenate([[0], np.cumsum(nz)]).astype(np.int32)
+    z = g.uniform(-0.8, 0.8, int(offs[-1]))
+    I = api.bessel(d, depth, zern, offs, z, *geo, precision=prec).cpu().numpy()
+    opt = oracle_optics(d)
+    for e in range(n_em):
+        a, b = offs[e], offs[e + 1]
+        Ir = ob.psf_bessel_batch(opt, depth, zern, offs, z, *geo, emitters=[e])
+        assert max_rel(I[a:b], Ir) <= 1e-5, e
 
 
 @pytest.mark.parametrize("kw", [dict(fresnel=True), dict(scalar=True)])

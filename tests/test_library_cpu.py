@@ -252,3 +252,26 @@ def test_split_precision_envelope(cpu_lib):
     # the Bessel adjoint keeps split BF16
     assert cpu_lib.psf_bessel_backward_workspace_size(ctypes.byref(ob_), 4, 16, 200, 64, 16,
                                                       16, B16) > 0
+
+
+def test_fresnel_bessel_workspaces(cpu_lib):
+    """Complex angular weights (Fresnel) are accepted by every Bessel mode and
+    the adjoint; the split forward then holds one F plane per order (three
+    times the operand rows) and the adjoint the complex J_n operand."""
+    plain = W.optics_gibson_lanni(0.0)
+    fr = dict(plain, fresnel=True)
+    args = (4, 500, 200, 256, 64, 64)
+    ws = {}
+    for name, d in (("plain", plain), ("fresnel", fr)):
+        o = api.make_optics(d, _lib.PSF_PROJECT_AXISYMMETRIC)
+        for p in (_lib.PSF_PREC_FP32, _lib.PSF_PREC_SPLIT_FP16):
+            ws[name, p, "fwd"] = cpu_lib.psf_bessel_workspace_size(ctypes.byref(o), *args, p)
+        for p in (_lib.PSF_PREC_FP32, _lib.PSF_PREC_SPLIT_FP16, _lib.PSF_PREC_SPLIT_BF16):
+            ws[name, p, "bwd"] = cpu_lib.psf_bessel_backward_workspace_size(
+                ctypes.byref(o), *args, p)
+    assert all(v > 0 for v in ws.values()), ws
+    F16 = _lib.PSF_PREC_SPLIT_FP16
+    # F: 2 x (2 n_slices Kp) 16-bit parts more per extra order
+    extra = 2 * 2 * (2 * 500 * 200 * 2)
+    assert ws["fresnel", F16, "fwd"] - ws["plain", F16, "fwd"] >= extra
+    assert ws["fresnel", _lib.PSF_PREC_FP32, "fwd"] == ws["plain", _lib.PSF_PREC_FP32, "fwd"]
