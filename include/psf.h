@@ -84,8 +84,8 @@ extern "C" {
                                    split hi + lo TF32 (FP32 storage), 3
                                    products, FP32 accumulation in TMEM       */
 #define PSF_PREC_TF32        6  /* Fourier forward: one TF32 product per MAC
-                                   (10-bit operand mantissas: about 1e-3 of
-                                   the stack; outside the accuracy envelope,
+                                   (10-bit operand mantissas: 1.3e-4 to
+                                   3.4e-4; outside the accuracy envelope,
                                    accepted only with PSF_OUTSIDE_ENVELOPE)   */
 #define PSF_PREC_AUTO        4  /* the fastest mode inside the accuracy
                                    envelope below: Fourier forward split FP16
@@ -107,8 +107,8 @@ extern "C" {
  * stays within half the bound:
  *   Fourier   split FP16  n_pupil <= 512   (4.3e-6 at 512; 8.7e-6 at 1024)
  *             split BF16  n_pupil <= 1024  (4.2e-6 at 1024; 7.6e-6 at 2048)
- *             split TF32  n_pupil <= 512   (three TF32 products)
- *             TF32        refused          (one product: about 1e-3)
+ *             split TF32  n_pupil <= 256   (3.0e-6 at 256; 6.1e-6 at 512)
+ *             TF32        refused          (one product: 1.3e-4 to 3.4e-4)
  *   Bessel /  split FP16  n_theta <= 448   (5.2e-6 at 448; 9.9e-6 at 880)
  *   harmonic  split BF16  refused          (5.2e-5 on the Bessel workload)
  * The flag PSF_OUTSIDE_ENVELOPE lifts these refusals.

@@ -24,6 +24,13 @@
 // leader issues six MMAs (three split products into each of the X and Y
 // accumulators, FP32 in TMEM).  Warp roles, bounded waits and the drain on
 // time-out are those of the unfolded pair kernel.
+//
+// TF32 (template flag): the operand parts are 32-bit TF32 values (x = hi + lo
+// rounded with cvt.rna.tf32, or hi alone for single-pass TF32), a 128-byte
+// stage row holds 32 K elements, and the leader issues kind::tf32 MMAs of
+// K = 8 (three split products, or one product per accumulator in the single
+// pass).  Everything else -- layout of the variants, the tiles, the
+// epilogues -- is shared with the 16-bit form.
 #include <cuda.h>
 #include <math.h>
 #include <stdlib.h>

@@ -53,6 +53,8 @@ static bool finite_pos(double v) { return isfinite(v) && v > 0; }
 // (Gibson-Lanni + Noll 4..21, 512^2 px):
 //   Fourier, folded contractions: split FP16 4.3e-6 at n_pupil 512 (8.7e-6 at
 //     1024, 1.7e-5 at 2048); split BF16 4.2e-6 at 1024 (7.6e-6 at 2048);
+//   split TF32 (three TF32 products) 3.0e-6 at 256 (6.1e-6 at 512, 1.2e-5
+//     at 1024); single-pass TF32 1.3e-4 to 3.4e-4 at every pupil;
 //   spherical (Bessel and harmonic) split FP16: 5.2e-6 at 448 Gauss-Legendre
 //     nodes (9.9e-6 at 880); split BF16 5.2e-5 on the Bessel workload.
 // The error grows with the contraction length (the K extent that each FP32
@@ -61,6 +63,7 @@ static bool finite_pos(double v) { return isfinite(v) && v > 0; }
 // ---------------------------------------------------------------------------
 constexpr int kSplitFp16MaxPupil = 512;
 constexpr int kSplitBf16MaxPupil = 1024;
+constexpr int kSplitTf32MaxPupil = 256;
 constexpr int kSplitMaxTheta = 448;
 
 static bool outside_allowed(const psf_optics* opt) {
@@ -72,13 +75,13 @@ static int fourier_envelope(const psf_optics* opt, int N, int precision) {
   if (precision == PSF_PREC_TF32)
     return fail(PSF_ERR_PRECISION,
                 "TF32 with one product per multiply-add keeps 11 significant bits per "
-                "operand (about 1e-3 from the FP64 oracle): outside the 1e-5 envelope; use "
-                "PSF_PREC_SPLIT_TF32 or set PSF_OUTSIDE_ENVELOPE");
-  if (precision == PSF_PREC_SPLIT_TF32 && N > kSplitFp16MaxPupil)
+                "operand (measured 1.3e-4 to 3.4e-4 from the FP64 oracle): outside the "
+                "1e-5 envelope; use PSF_PREC_SPLIT_TF32 or set PSF_OUTSIDE_ENVELOPE");
+  if (precision == PSF_PREC_SPLIT_TF32 && N > kSplitTf32MaxPupil)
     return fail(PSF_ERR_PRECISION,
-                "split TF32 is accepted up to n_pupil %d; n_pupil %d: use "
-                "PSF_PREC_FP32_CHIRPZ, PSF_PREC_FP32 or PSF_PREC_AUTO",
-                kSplitFp16MaxPupil, N);
+                "split TF32 is accepted up to n_pupil %d (measured 3.0e-6 at 256, 6.1e-6 "
+                "at 512); n_pupil %d: use PSF_PREC_SPLIT_FP16, PSF_PREC_FP32_CHIRPZ or "
+                "PSF_PREC_AUTO", kSplitTf32MaxPupil, N);
   if (precision == PSF_PREC_SPLIT_FP16 && N > kSplitFp16MaxPupil)
     return fail(PSF_ERR_PRECISION,
                 "split FP16 holds the 1e-5 bound up to n_pupil %d (measured 4.3e-6 at 512, "

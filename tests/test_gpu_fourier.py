@@ -4,8 +4,8 @@ Tolerance: max |I - I_ref| / max |I_ref| <= 1e-5 per stack for intensity and
 the same for the complex fields (the forward target), for the FP32 and both
 split contractions (the symmetry-folded form sums half of K per accumulator
 and stays within the bound inside the library's accuracy envelope: split
-FP16 and split TF32 up to n_pupil 512, split BF16 up to 1024; larger pupils
-are refused).
+FP16 up to n_pupil 512, split TF32 up to 256, split BF16 up to 1024; larger
+pupils are refused).
 The unfolded 2x2-block form (PSF_TC_FOLD=0, a comparison path) is held to
 3e-5: it sums four times as many terms per accumulator and measured 1.07e-5
 in split BF16."""
@@ -286,22 +286,22 @@ def test_auto_precision(lib, N, mode):
 
 
 def test_tf32_modes(lib):
-    """3xTF32 (split TF32) holds 1e-5 up to n_pupil 512 and is refused beyond;
-    single-pass TF32 (a 10-bit mantissa per operand, measured 1.3e-4 to
-    3.4e-4 on the workload's planes) is refused unless the caller opts out of
-    the bound, and then stays within 1e-3; the adjoints take no TF32 mode."""
+    """3xTF32 (split TF32) holds half the 1e-5 bound up to n_pupil 256 and is
+    refused beyond (6.1e-6 measured at 512, which it still returns with the
+    caller's opt-out); single-pass TF32 (a 10-bit mantissa per operand,
+    measured 1.3e-4 to 3.4e-4 on the workload's planes) is refused unless the
+    caller opts out of the bound, and then stays within 1e-3; the adjoints
+    take no TF32 mode."""
     c = W.fourier(n_pupil=512, nx=64, nz=2)
     opt = oracle_optics(c["optics"])
-    Ir = of.psf_fourier(opt, 512, c["grid"], zernike=c["zernike"])
-    I = api.fourier(c["optics"], 512, c["grid"], zernike=c["zernike"], precision="split_tf32")
-    assert max_rel(I.cpu().numpy(), Ir) <= 1e-5
-    with pytest.raises(_lib.PsfError) as e:
-        api.fourier(c["optics"], 1024, c["grid"], zernike=c["zernike"], precision="split_tf32")
-    assert e.value.code == _lib.PSF_ERR_PRECISION
-    with pytest.raises(_lib.PsfError) as e:
-        api.fourier(c["optics"], 512, c["grid"], zernike=c["zernike"], precision="tf32")
-    assert e.value.code == _lib.PSF_ERR_PRECISION
     d = dict(c["optics"], outside_envelope=True)
+    Ir = of.psf_fourier(opt, 512, c["grid"], zernike=c["zernike"])
+    I = api.fourier(d, 512, c["grid"], zernike=c["zernike"], precision="split_tf32")
+    assert max_rel(I.cpu().numpy(), Ir) <= 1e-5
+    for N, prec in ((512, "split_tf32"), (512, "tf32")):
+        with pytest.raises(_lib.PsfError) as e:
+            api.fourier(c["optics"], N, c["grid"], zernike=c["zernike"], precision=prec)
+        assert e.value.code == _lib.PSF_ERR_PRECISION
     I1 = api.fourier(d, 512, c["grid"], zernike=c["zernike"], precision="tf32").cpu().numpy()
     assert 1e-6 < max_rel(I1, Ir) <= 1e-3
     o = api.make_optics(c["optics"])

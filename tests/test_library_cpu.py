@@ -217,9 +217,9 @@ def test_split_precision_envelope(cpu_lib):
     for N, mode in ((256, F16), (1024, B16), (1536, _lib.PSF_PREC_FP32_CHIRPZ),
                     (4096, _lib.PSF_PREC_FP32)):
         assert size(N, _lib.PSF_PREC_AUTO) == size(N, mode), N
-    # 3xTF32 up to 512; single-pass TF32 only with PSF_OUTSIDE_ENVELOPE
+    # 3xTF32 up to 256; single-pass TF32 only with PSF_OUTSIDE_ENVELOPE
     T3, T1 = _lib.PSF_PREC_SPLIT_TF32, _lib.PSF_PREC_TF32
-    assert size(512, T3) > 0 and size(1024, T3) == 0
+    assert size(256, T3) > 0 and size(512, T3) == 0
     assert size(256, T1) == 0 and b"TF32" in cpu_lib.psf_last_error()
     oo = api.make_optics(dict(W.optics_gibson_lanni(2.0), outside_envelope=True))
     assert cpu_lib.psf_fourier_workspace_size(ctypes.byref(oo), 256, ctypes.byref(g.c), T1) > 0
