@@ -9,33 +9,46 @@ namespace psf {
 // ---------------------------------------------------------------------------
 // Node table: geometry of the cell-centred pupil grid (Sec. 3.4 footnote),
 // Gibson-Lanni path (Eq. 13-14), Zernike + free phase (Eq. 15), apodization
-// (Eq. 16), envelope (Eq. 17), far-field basis change (Eq. 6, q_s = q_p = 1)
-// and the 1/s_z of dOmega = ds_x ds_y / s_z (Eq. 8).  One thread per node,
-// FP64 throughout, once per call.
+// (Eq. 16), envelope (Eq. 17), far-field basis change (Eq. 6, q_s = q_p = 1
+// unless Fresnel) and the 1/s_z of dOmega = ds_x ds_y / s_z (Eq. 8).  FP64
+// throughout, once per call, in two passes:
+//   radial pass: everything that depends on the node's radius only, once per
+//     octant pair (|m_p|, |m_q|) with |m_p| <= |m_q| (m = 2p + 1 - N), an
+//     eighth of the nodes: optical path in cycles (reduced mod 1), amplitude
+//     (1/cos, apodization, envelope, evanescent decay), cos, sin, q_s, q_p,
+//     |m| / r of both coordinates and the Zernike radial sums per azimuthal
+//     order (FP64);
+//   node pass: the azimuthal factors cos(m phi), sin(m phi) of the Zernike
+//     sum and the free phase (FP64), the basis change of Eq. 6 (FP32: the
+//     amplitudes are stored in FP32) and the double-float n_i cos / lambda.
 // ---------------------------------------------------------------------------
-__global__ void k_node_table(NodeParams p, NodeTable t) {
+__device__ __forceinline__ size_t node_tri(int k1, int k2) {
+  return (size_t)k2 * (k2 + 1) / 2 + k1;
+}
+
+__global__ void k_node_radial(NodeParams p, double* __restrict__ rad) {
   const int N = p.N;
-  const int NN = N * N;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= NN) return;
-  const int ip = idx / N, iq = idx - (idx / N) * N;
-  const long long mp = 2 * ip + 1 - N, mq = 2 * iq + 1 - N;
-  const bool inside = mp * mp + mq * mq <= (long long)N * N;
-  if (!inside) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) t.amp[c * NN + idx] = 0.f;
-    t.wfr[idx] = 0.f;
-    t.kh[idx] = 0.f;
-    t.kl[idx] = 0.f;
+  const int K = (N + 1) / 2;
+  // flat index over the triangle k1 <= k2 (FP64 issues at about 2 FMA per
+  // clock per SM here: spread the pairs evenly over small blocks)
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)K * (K + 1) / 2) return;
+  int k2 = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+  while ((long long)k2 * (k2 + 1) / 2 > idx) --k2;
+  while ((long long)(k2 + 1) * (k2 + 2) / 2 <= idx) ++k2;
+  const int k1 = (int)(idx - (long long)k2 * (k2 + 1) / 2);
+  const int r0 = (N & 1) ? 0 : 1;          // |m| = 2k + r0
+  const long long m1 = 2 * k1 + r0, m2 = 2 * k2 + r0;
+  double* rec = rad + kNodeRad * node_tri(k1, k2);
+  if (m1 * m1 + m2 * m2 > (long long)N * N) {
+    for (int k = 0; k < kNodeRad; ++k) rec[k] = 0.0;
+    rec[1] = -1.0;
     return;
   }
-  const double u = (double)mp / N, v = (double)mq / N;
-  const double rn = sqrt(u * u + v * v);
+  const double rr = sqrt((double)(m1 * m1 + m2 * m2));
+  const double rn = rr / N;
   const double sin_t = p.s_max * rn;
   const double cos_t = sqrt(fmax(0.0, 1.0 - sin_t * sin_t));
-  const double cp = rn > 0 ? u / rn : 1.0;
-  const double sp = rn > 0 ? v / rn : 0.0;
-
   // Eq. 13: optical path in cycles; evanescent layers add decay.
   double w_cyc = 0.0, decay_cyc = 0.0;
   const double nis = p.n_i * sin_t;
@@ -46,56 +59,113 @@ __global__ void k_node_table(NodeParams p, NodeTable t) {
     else
       decay_cyc += p.gl.t[l] * sqrt(-arg) * p.inv_lambda;
   }
-  // Eq. 15: Zernike sum by azimuthal order, radians.
-  double wz = 0.0;
-  if (p.zp.max_m >= 0) {
-    double cm = 1.0, sm = 0.0;
-    for (int m = 0; m <= p.zp.max_m; ++m) {
-      double pc = 0.0, ps = 0.0;
+  w_cyc -= rint(w_cyc);
+  double a = 1.0 / cos_t;
+  if (p.apodize) a *= sqrt(cos_t);
+  if (p.s_env > 0) a *= exp(-(sin_t * sin_t) / (p.s_env * p.s_env));
+  if (decay_cyc != 0.0) a *= exp(-2.0 * kPi * decay_cyc);
+  dcplx qs{1.0, 0.0}, qp{1.0, 0.0};
+  if (p.model == 2) fresnel_q(p.n_s, p.n_g, p.n_i, sin_t, qs, qp);
+  rec[0] = w_cyc;
+  rec[1] = a;
+  rec[2] = cos_t;
+  rec[3] = sin_t;
+  rec[4] = qs.re;
+  rec[5] = qs.im;
+  rec[6] = qp.re;
+  rec[7] = qp.im;
+  rec[8] = rr > 0 ? (double)m1 / rr : 1.0;
+  rec[9] = rr > 0 ? (double)m2 / rr : 0.0;
+  // Eq. 15: radial sums of the Zernike terms by azimuthal order (radians)
+  for (int m = 0; m <= kZernMaxOrder; ++m) {
+    double pc = 0.0, ps = 0.0;
+    if (m <= p.zp.max_m) {
       for (int k = p.zp.deg; k >= 0; --k) {
         pc = pc * rn + p.zp.c[m][k];
         ps = ps * rn + p.zp.s[m][k];
       }
-      wz += pc * cm + ps * sm;
+    }
+    rec[10 + 2 * m] = pc;
+    rec[11 + 2 * m] = ps;
+  }
+}
+
+__global__ void k_node_table(NodeParams p, const double* __restrict__ rad, NodeTable t) {
+  const int N = p.N;
+  const int NN = N * N;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NN) return;
+  const int ip = idx / N, iq = idx - (idx / N) * N;
+  const int mp = 2 * ip + 1 - N, mq = 2 * iq + 1 - N;
+  const int r0 = (N & 1) ? 0 : 1;
+  const int ap = abs(mp), aq = abs(mq);
+  const int ka = (ap - r0) >> 1, kb = (aq - r0) >> 1;
+  const double* rec = rad + kNodeRad * node_tri(min(ka, kb), max(ka, kb));
+  const double a = rec[1];
+  if (a < 0.0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t.amp[c * NN + idx] = 0.f;
+    t.wfr[idx] = 0.f;
+    t.kh[idx] = 0.f;
+    t.kl[idx] = 0.f;
+    return;
+  }
+  const double cos_t = rec[2], sin_t = rec[3];
+  // cos phi = m_p / r, sin phi = m_q / r from the octant's |m| / r
+  double cp = ap <= aq ? rec[8] : rec[9];
+  double sp = ap <= aq ? rec[9] : rec[8];
+  if (mp < 0) cp = -cp;
+  if (mq < 0) sp = -sp;
+  // Eq. 15: sum over azimuthal orders of the radial sums times cos / sin(m phi)
+  double wz = 0.0;
+  if (p.zp.max_m >= 0) {
+    double cm = 1.0, sm = 0.0;
+    for (int m = 0; m <= p.zp.max_m; ++m) {
+      wz += rec[10 + 2 * m] * cm + rec[11 + 2 * m] * sm;
       const double cn = cm * cp - sm * sp;
       sm = sm * cp + cm * sp;
       cm = cn;
     }
   }
   if (p.phase_map) wz += (double)p.phase_map[idx];
-  double w_total = w_cyc + wz * (0.5 / kPi);
+  double w_total = rec[0] + wz * (0.5 / kPi);
   w_total -= rint(w_total);
 
-  double a = 1.0 / cos_t;
-  if (p.apodize) a *= sqrt(cos_t);
-  if (p.s_env > 0) a *= exp(-(sin_t * sin_t) / (p.s_env * p.s_env));
-  if (decay_cyc != 0.0) a *= exp(-2.0 * kPi * decay_cyc);
-
-  double e[6];
+  float e[6];
+  const float af = (float)a;
   if (p.model == 1) {
     // scalar model (Eq. 3): e_far = e_inc, carried in channel 0
-    e[0] = a;
-    e[1] = e[2] = e[3] = e[4] = e[5] = 0.0;
+    e[0] = af;
+    e[1] = e[2] = e[3] = e[4] = e[5] = 0.f;
   } else {
     // Eq. 6, columns for e_inc^x and e_inc^y (each / 2); q_s = q_p = 1 unless
     // the Fresnel coefficients of Eq. 7 are requested (complex past the
     // critical angle of a layer)
-    dcplx qs{1.0, 0.0}, qp{1.0, 0.0};
-    if (p.model == 2) fresnel_q(p.n_s, p.n_g, p.n_i, sin_t, qs, qp);
-    const double c2 = cp * cp - sp * sp, s2 = 2.0 * sp * cp;
+    const float2 qs = make_float2((float)rec[4], (float)rec[5]);
+    const float2 qp = make_float2((float)rec[6], (float)rec[7]);
+    const float ct = (float)cos_t, st = (float)sin_t, cpf = (float)cp, spf = (float)sp;
+    const float c2 = cpf * cpf - spf * spf, s2 = 2.f * spf * cpf;
+    auto lin = [](float a1, float2 x, float a2, float2 y) {
+      return make_float2(a1 * x.x + a2 * y.x, a1 * x.y + a2 * y.y);
+    };
     // xx = [qs (1 - c2) + qp (1 + c2) cos] / 2, xy = (qp cos - qs) s2 / 2,
     // yy = [qs (1 + c2) + qp (1 - c2) cos] / 2, z = -qp (cos phi, sin phi) sin
-    const dcplx xx = 0.5 * ((1.0 - c2) * qs + ((1.0 + c2) * cos_t) * qp);
-    const dcplx xy = (0.5 * s2) * (cos_t * qp - qs);
-    const dcplx yy = 0.5 * ((1.0 + c2) * qs + ((1.0 - c2) * cos_t) * qp);
-    const dcplx zx = (-cp * sin_t) * qp, zy = (-sp * sin_t) * qp;
-    const dcplx px{p.pol[0], p.pol[1]}, py{p.pol[2], p.pol[3]};
-    const dcplx ex = a * (xx * px + xy * py), ey = a * (xy * px + yy * py),
-                ez = a * (zx * px + zy * py);
-    e[0] = ex.re; e[1] = ex.im; e[2] = ey.re; e[3] = ey.im; e[4] = ez.re; e[5] = ez.im;
+    const float2 xx = lin(0.5f * (1.f - c2), qs, 0.5f * (1.f + c2) * ct, qp);
+    const float2 xy = lin(-0.5f * s2, qs, 0.5f * s2 * ct, qp);
+    const float2 yy = lin(0.5f * (1.f + c2), qs, 0.5f * (1.f - c2) * ct, qp);
+    const float2 zx = make_float2(-cpf * st * qp.x, -cpf * st * qp.y);
+    const float2 zy = make_float2(-spf * st * qp.x, -spf * st * qp.y);
+    const float2 px = make_float2((float)p.pol[0], (float)p.pol[1]);
+    const float2 py = make_float2((float)p.pol[2], (float)p.pol[3]);
+    auto mac = [&](float2 m1, float2 v1, float2 m2, float2 v2) {
+      const float2 u = cmul(m1, v1), w = cmul(m2, v2);
+      return make_float2(af * (u.x + w.x), af * (u.y + w.y));
+    };
+    const float2 ex = mac(xx, px, xy, py), ey = mac(xy, px, yy, py), ez = mac(zx, px, zy, py);
+    e[0] = ex.x; e[1] = ex.y; e[2] = ey.x; e[3] = ey.y; e[4] = ez.x; e[5] = ez.y;
   }
 #pragma unroll
-  for (int c = 0; c < 6; ++c) t.amp[c * NN + idx] = (float)e[c];
+  for (int c = 0; c < 6; ++c) t.amp[c * NN + idx] = e[c];
   t.wfr[idx] = (float)w_total;
   const f2x kap = split_double(p.n_i * cos_t * p.inv_lambda);
   t.kh[idx] = kap.hi;
@@ -103,8 +173,10 @@ __global__ void k_node_table(NodeParams p, NodeTable t) {
 }
 
 void launch_node_table(const NodeParams& p, NodeTable t, cudaStream_t s) {
+  const int pairs = (int)node_rad_count(p.N);
+  k_node_radial<<<ceil_div(pairs, 32), 32, 0, s>>>(p, t.rad);
   const int NN = p.N * p.N;
-  k_node_table<<<ceil_div(NN, 128), 128, 0, s>>>(p, t);
+  k_node_table<<<ceil_div(NN, 128), 128, 0, s>>>(p, t.rad, t);
 }
 
 // ---------------------------------------------------------------------------

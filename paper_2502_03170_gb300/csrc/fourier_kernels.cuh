@@ -45,12 +45,26 @@ struct NodeParams {
 //   amp[6][N*N]  A e^{-Im W} e_inf,c / cos(theta) (c = x, y, z; re, im)
 //   wfr[N*N]     frac(Re W / 2 pi) in cycles
 //   kh, kl[N*N]  n_i cos(theta) / lambda as a double-float (cycles per um)
+//   rad          scratch of the build: the radial quantities (everything but
+//                the Zernike / free phase and the azimuthal basis change) of
+//                the node_rad_count(N) octant pairs, kNodeRad doubles each
 struct NodeTable {
   float* amp;
   float* wfr;
   float* kh;
   float* kl;
+  double* rad;
 };
+// radial record: [0] Re W / 2 pi mod 1, [1] amplitude (-1 outside the disk),
+// [2] cos theta, [3] sin theta, [4, 5] q_s, [6, 7] q_p, [8, 9] min(|m_p|,
+// |m_q|) / r and max / r (1, 0 at r = 0), [10 + 2m, 11 + 2m] the cos / sin
+// Zernike radial sums of azimuthal order m (m <= kZernMaxOrder), radians
+constexpr int kNodeRad = 10 + 2 * (kZernMaxOrder + 1);
+// Octant pairs (k1 <= k2 < K, K = (N + 1) / 2) of |2p + 1 - N| values.
+inline size_t node_rad_count(int N) {
+  const size_t K = (size_t)(N + 1) / 2;
+  return K * (K + 1) / 2;
+}
 
 void launch_node_table(const NodeParams& p, NodeTable t, cudaStream_t s);
 

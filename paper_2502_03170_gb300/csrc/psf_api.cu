@@ -368,6 +368,7 @@ static FourierLayout fourier_layout(void* ws, int N, const psf_grid* g,
   L.nodes.wfr = c.take<float>(NN);
   L.nodes.kh = c.take<float>(NN);
   L.nodes.kl = c.take<float>(NN);
+  L.nodes.rad = c.take<double>(kNodeRad * node_rad_count(N));
   L.zz = c.take<float2>(g->nz);
   auto capped = [&](int zc) { return zc < max_planes ? zc : (max_planes > 1 ? max_planes : 1); };
   L.zc = capped(fourier_zchunk(N, g->nx, g->ny, g->nz));
@@ -689,6 +690,7 @@ static BackwardLayout backward_layout(void* ws, int N, const psf_grid* g,
   L.nodes.wfr = c.take<float>(NN);
   L.nodes.kh = c.take<float>(NN);
   L.nodes.kl = c.take<float>(NN);
+  L.nodes.rad = c.take<double>(kNodeRad * node_rad_count(N));
   L.zz = c.take<float2>(g->nz);
   if (precision != PSF_PREC_FP32) {
     L.zc = tc_fourier_bwd_zchunk(N, g->nx, g->ny, g->nz, max_planes);
