@@ -41,7 +41,9 @@ constexpr int GSTAGES = 4;
 constexpr int GA_BYTES = GM * GK * 2;
 constexpr int GB_BYTES = GNMAX * GK * 2;
 constexpr int GSTAGE = GA_BYTES + GB_BYTES;   // 48 KB
-constexpr int GTHREADS = 192;
+constexpr int GEPI_WARPS = 16;          // four per TMEM lane quarter
+constexpr int GTHREADS = 64 + 32 * GEPI_WARPS;
+constexpr int GCH = 16;                 // epilogue columns per TMEM load
 constexpr int GSMEM = GSTAGES * GSTAGE + 1024 + 1024;
 
 struct KArgs {
@@ -51,6 +53,19 @@ struct KArgs {
 };
 
 PSF_D float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// 16 consecutive TMEM columns of this warp's lanes, waited in the same asm.
+PSF_D void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+        "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+        "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
 PSF_D uint16_t f2bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 
 __global__ void __launch_bounds__(GTHREADS, 1)
@@ -78,7 +93,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 128);
+      mbar_init(tempty_bar(b), 32 * GEPI_WARPS);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -167,7 +182,10 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
     mma_commit(drain_bar);
     mbar_drain_wait(drain_bar, 0);
   } else if (warp >= 2) {
-    const int quad = warp & 3;
+    // epilogue: warp (quad, part) reads the 16-column chunks part, part + 4, ..
+    // of its lane quarter (four warps per quarter hide the latency of the
+    // activation arithmetic and the row-wise stores)
+    const int quad = warp & 3, part = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
     int acc = 0;
     uint32_t acc_phase = 0;
@@ -181,19 +199,19 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
       const int m = mt * GM + row;
       const bool mok = m < g.M;
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256);
-      for (int c0 = 0; c0 < ka.n_tile; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tbase + (uint32_t)c0, r);
+      for (int c0 = part * GCH; c0 < ka.n_tile; c0 += 4 * GCH) {
+        uint32_t r[GCH];
+        tmem_ld16(tbase + (uint32_t)c0, r);
         const int n0 = nt * ka.n_tile + c0;
         if (!mok || n0 >= g.N) continue;
-        const bool full = n0 + 32 <= g.N;
+        const bool full = n0 + GCH <= g.N;
         if (g.epi == EPI_HIDDEN || g.epi == EPI_DSILU) {
-          uint16_t v16[32], z16[32];
+          uint16_t v16[GCH], z16[GCH];
           if (g.epi == EPI_DSILU) {
             const uint16_t* zp = g.Z + (size_t)m * g.ldz + n0;
             if (full) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
+              for (int q = 0; q < GCH / 8; ++q) {
                 const uint4 w = ((const uint4*)zp)[q];
                 const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -204,11 +222,11 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
               }
             } else {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) z16[j] = n0 + j < g.N ? zp[j] : (uint16_t)0;
+              for (int j = 0; j < GCH; ++j) z16[j] = n0 + j < g.N ? zp[j] : (uint16_t)0;
             }
           }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < GCH; ++j) {
             const float a = __uint_as_float(r[j]);
             if (g.epi == EPI_HIDDEN) {
               const float z = a + (n0 + j < g.N ? g.bias[n0 + j] : 0.f);
@@ -225,7 +243,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
           uint16_t* yp = g.Y + (size_t)m * g.ldy + n0;
           if (full) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < GCH / 8; ++q)
               ((uint4*)yp)[q] = make_uint4(
                   (uint32_t)v16[8 * q] | ((uint32_t)v16[8 * q + 1] << 16),
                   (uint32_t)v16[8 * q + 2] | ((uint32_t)v16[8 * q + 3] << 16),
@@ -234,7 +252,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
             if (g.epi == EPI_HIDDEN && g.Z) {
               uint16_t* zp = g.Z + (size_t)m * g.ldz + n0;
 #pragma unroll
-              for (int q = 0; q < 4; ++q)
+              for (int q = 0; q < GCH / 8; ++q)
                 ((uint4*)zp)[q] = make_uint4(
                     (uint32_t)z16[8 * q] | ((uint32_t)z16[8 * q + 1] << 16),
                     (uint32_t)z16[8 * q + 2] | ((uint32_t)z16[8 * q + 3] << 16),
@@ -243,7 +261,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
             }
           } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < GCH; ++j)
               if (n0 + j < g.N) {
                 yp[j] = v16[j];
                 if (g.epi == EPI_HIDDEN && g.Z) g.Z[(size_t)m * g.ldz + n0 + j] = z16[j];
@@ -251,24 +269,24 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
           }
           if (g.YT) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < GCH; ++j)
               if (n0 + j < g.N) g.YT[(size_t)(n0 + j) * g.ldyt + m] = v16[j];
           }
         } else {
           float* op = g.out + (size_t)m * g.ldo + n0;
-          float v[32];
+          float v[GCH];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < GCH; ++j) {
             v[j] = __uint_as_float(r[j]);
             if (g.epi == EPI_LINEAR && n0 + j < g.N) v[j] += g.bias[n0 + j];
           }
           if (full && (g.ldo & 3) == 0) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < GCH / 4; ++q)
               ((float4*)op)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
           } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < GCH; ++j)
               if (n0 + j < g.N) op[j] = v[j];
           }
         }
