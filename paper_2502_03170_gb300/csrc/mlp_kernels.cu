@@ -37,14 +37,19 @@ using namespace tc;
 constexpr int GM = 128;                 // A rows per tile
 constexpr int GNMAX = 256;              // max B rows per tile
 constexpr int GK = 64;                  // K per stage (128-byte rows)
-constexpr int GSTAGES = 4;
+constexpr int GSTAGES = 3;
 constexpr int GA_BYTES = GM * GK * 2;
 constexpr int GB_BYTES = GNMAX * GK * 2;
 constexpr int GSTAGE = GA_BYTES + GB_BYTES;   // 48 KB
 constexpr int GEPI_WARPS = 16;          // four per TMEM lane quarter
 constexpr int GTHREADS = 64 + 32 * GEPI_WARPS;
 constexpr int GCH = 16;                 // epilogue columns per TMEM load
-constexpr int GSMEM = GSTAGES * GSTAGE + 1024 + 1024;
+// FP32 outputs of a chunk staged per epilogue warp (32 rows, stride 20 floats:
+// 16-byte aligned rows, conflict-free 16-byte writes) and stored 8 rows of
+// 64 bytes per instruction
+constexpr int GSTG_LD = GCH + 4;
+constexpr int GSTG_BYTES = GEPI_WARPS * 32 * GSTG_LD * 4;
+constexpr int GSMEM = GSTAGES * GSTAGE + GSTG_BYTES + 1024 + 1024;
 
 struct KArgs {
   GemmArgs g;
@@ -53,6 +58,23 @@ struct KArgs {
 };
 
 PSF_D float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// bias[n0 .. n0 + GCH) (0 past N), as four 16-byte loads when the chunk is full
+PSF_D void load_bias(const GemmArgs& g, int n0, bool full, float (&b)[GCH]) {
+  if (full && (((uintptr_t)(g.bias + n0) & 15) == 0)) {
+#pragma unroll
+    for (int q = 0; q < GCH / 4; ++q) {
+      const float4 w = __ldg((const float4*)(g.bias + n0) + q);
+      b[4 * q] = w.x;
+      b[4 * q + 1] = w.y;
+      b[4 * q + 2] = w.z;
+      b[4 * q + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < GCH; ++j) b[j] = n0 + j < g.N ? g.bias[n0 + j] : 0.f;
+  }
+}
 
 // 16 consecutive TMEM columns of this warp's lanes, waited in the same asm.
 PSF_D void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -73,7 +95,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
             const __grid_constant__ CUtensorMap mapB, const KArgs ka) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + GSTAGES * GSTAGE);
+  float* gstg = (float*)(smem + GSTAGES * GSTAGE);
+  uint64_t* bars = (uint64_t*)(smem + GSTAGES * GSTAGE + GSTG_BYTES);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * GSTAGES + 5);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const GemmArgs& g = ka.g;
@@ -203,8 +226,40 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
         uint32_t r[GCH];
         tmem_ld16(tbase + (uint32_t)c0, r);
         const int n0 = nt * ka.n_tile + c0;
-        if (!mok || n0 >= g.N) continue;
+        if (n0 >= g.N) continue;                    // the same for the whole warp
         const bool full = n0 + GCH <= g.N;
+        float* ow = g.out ? g.out + n0 : nullptr;
+        if ((g.epi == EPI_LINEAR || g.epi == EPI_STORE) && full && (g.ldo & 3) == 0 &&
+            ((uintptr_t)ow & 15) == 0) {
+          // FP32 output through the warp's staging rows
+          float* st = gstg + (warp - 2) * 32 * GSTG_LD;
+          float bias[GCH];
+          if (g.epi == EPI_LINEAR) load_bias(g, n0, true, bias);
+#pragma unroll
+          for (int q = 0; q < GCH / 4; ++q) {
+            float4 w = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            if (g.epi == EPI_LINEAR) {
+              w.x += bias[4 * q];
+              w.y += bias[4 * q + 1];
+              w.z += bias[4 * q + 2];
+              w.w += bias[4 * q + 3];
+            }
+            ((float4*)(st + lane * GSTG_LD))[q] = w;
+          }
+          __syncwarp();
+          const int m0 = mt * GM + quad * 32;
+#pragma unroll
+          for (int it = 0; it < 4; ++it) {
+            const int rr = it * 8 + (lane >> 2), q = lane & 3;
+            if (m0 + rr < g.M)
+              ((float4*)(ow + (size_t)(m0 + rr) * g.ldo))[q] =
+                  ((const float4*)(st + rr * GSTG_LD))[q];
+          }
+          __syncwarp();
+          continue;
+        }
+        if (!mok) continue;
         if (g.epi == EPI_HIDDEN || g.epi == EPI_DSILU) {
           uint16_t v16[GCH], z16[GCH];
           if (g.epi == EPI_DSILU) {
@@ -225,18 +280,21 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
               for (int j = 0; j < GCH; ++j) z16[j] = n0 + j < g.N ? zp[j] : (uint16_t)0;
             }
           }
+          float bias[GCH];
+          if (g.epi == EPI_HIDDEN) load_bias(g, n0, full, bias);
+          // the logistic through the fast exp and reciprocal: its FP32 error
+          // (a few ulp) is far below the BF16 rounding that follows
 #pragma unroll
           for (int j = 0; j < GCH; ++j) {
             const float a = __uint_as_float(r[j]);
             if (g.epi == EPI_HIDDEN) {
-              const float z = a + (n0 + j < g.N ? g.bias[n0 + j] : 0.f);
-              const uint16_t zb = f2bf(z);
+              const uint16_t zb = f2bf(a + bias[j]);
               const float zr = bf2f(zb);
               z16[j] = zb;
-              v16[j] = f2bf(zr / (1.f + expf(-zr)));   // SiLU of the stored z
+              v16[j] = f2bf(zr * __frcp_rn(1.f + __expf(-zr)));   // SiLU of the stored z
             } else {
               const float z = bf2f(z16[j]);
-              const float sg = 1.f / (1.f + expf(-z));
+              const float sg = __frcp_rn(1.f + __expf(-z));
               v16[j] = f2bf(a * sg * (1.f + z * (1.f - sg)));
             }
           }
@@ -274,11 +332,12 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
           }
         } else {
           float* op = g.out + (size_t)m * g.ldo + n0;
-          float v[GCH];
+          float v[GCH], bias[GCH];
+          if (g.epi == EPI_LINEAR) load_bias(g, n0, full, bias);
 #pragma unroll
           for (int j = 0; j < GCH; ++j) {
             v[j] = __uint_as_float(r[j]);
-            if (g.epi == EPI_LINEAR && n0 + j < g.N) v[j] += g.bias[n0 + j];
+            if (g.epi == EPI_LINEAR) v[j] += bias[j];
           }
           if (full && (g.ldo & 3) == 0) {
 #pragma unroll
