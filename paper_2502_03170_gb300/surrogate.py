@@ -72,15 +72,17 @@ class Surrogate:
             api._ptr(loss), api._ptr(ws), ws.numel(), api._stream()))
         return g, loss
 
-    def forward(self, query):
+    def forward(self, query, error_head=True):
+        """Profiles [B][1536] and the error head's log10 relative error [B]
+        (None with error_head=False: the network alone)."""
         q = self._f32(query)
         B = q.shape[0]
         ws = self._work(B)
         out = torch.empty((B, 1536), dtype=torch.float32, device=self.dev)
-        err = torch.empty(B, dtype=torch.float32, device=self.dev)
+        err = torch.empty(B, dtype=torch.float32, device=self.dev) if error_head else None
         _lib.check(self.lib, self.lib.psf_mlp_forward(
-            api._ptr(self.state), api._ptr(q), B, api._ptr(out), api._ptr(err),
-            api._ptr(ws), ws.numel(), api._stream()))
+            api._ptr(self.state), api._ptr(q), B, api._ptr(out),
+            api._ptr(err) if error_head else None, api._ptr(ws), ws.numel(), api._stream()))
         return out, err
 
     def profiles(self, query, optics, max_rel_err, n_theta, nx, ny, dx, dy,

@@ -19,6 +19,9 @@ the device), then exits.  Cases:
   (``--mmax`` to set it) with the adaptive per-emitter order
   (``--tail-tol``, default 1e-7; 0 keeps the bound order); ``--precision
   split_fp16`` puts the radial contraction on the tensor cores.
+* ``surrogate`` - the surrogate network (seeded initial weights) on
+  ``--batch`` queries: the forward with the error head (one BF16 tcgen05 GEMM
+  per layer).
 """
 import argparse
 import os
@@ -36,7 +39,7 @@ from paper_2502_03170_gb300 import workloads as W  # noqa: E402
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["fourier", "bessel", "bessel_backward",
-                                     "fourier_backward", "bessel_harmonic"])
+                                     "fourier_backward", "bessel_harmonic", "surrogate"])
     ap.add_argument("--mmax", type=int, default=-1)
     ap.add_argument("--tail-tol", type=float, default=1e-7)
     ap.add_argument("--batch", type=int, default=8)
@@ -72,6 +75,14 @@ def main():
                 precision=args.precision)
         torch.cuda.synchronize()
         assert torch.isfinite(gW).all()
+    elif args.case == "surrogate":
+        from paper_2502_03170_gb300 import surrogate as sg
+        s = sg.Surrogate(seed=3)
+        q = torch.as_tensor(sg.queries(args.batch, seed_salt=99), device="cuda")
+        for _ in range(2):
+            out, err = s.forward(q)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all()
     elif args.case == "bessel_harmonic":
         c = W.bessel(n_emitters=args.emitters)
         m = args.mmax if args.mmax >= 0 else api.harmonic_order(c["zernike"], 1e-7)
