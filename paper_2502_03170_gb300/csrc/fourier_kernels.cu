@@ -502,36 +502,43 @@ void launch_grad_accum(const float2* Gh, const float2* P, float* gW, int NN,
 // (Eq. 15).  FP64 radial polynomial; cos(m phi) and sin(m phi) are the real
 // and imaginary parts of ((u + i v) / rho)^m, so no trigonometric call.
 __global__ void k_zernike_table(ZernBasis zb, int N, float* __restrict__ Zt) {
-  const long long NN = (long long)N * N;
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)zb.n_zern * NN) return;
-  const int j = (int)(idx / NN);
-  const int i = (int)(idx - (long long)j * NN);
+  // one thread per node, every term: the azimuthal factors cos / sin(m phi)
+  // once per node by the rotation recursion, the radial polynomial of each
+  // term by Horner (FP64)
+  const int NN = N * N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NN) return;
   const int ip = i / N, iq = i - (i / N) * N;
-  const int m = zb.m[j], am = m < 0 ? -m : m;
   const double u = (double)(2 * ip + 1 - N) / N, v = (double)(2 * iq + 1 - N) / N;
   const double rn = sqrt(u * u + v * v);
-  double r = 0.0;
-  for (int k = kZernMaxOrder; k >= 0; --k) r = r * rn + zb.rc[j][k];
-  double ang = 1.0;
-  if (am > 0 && rn == 0.0) {
-    ang = 0.0;                                    // odd N: the centre node
-  } else if (am > 0) {
-    const double c = u / rn, sn = v / rn;
-    double cr = 1.0, ci = 0.0;
-    for (int k = 0; k < am; ++k) {
-      const double t = cr * c - ci * sn;
-      ci = cr * sn + ci * c;
-      cr = t;
-    }
-    ang = m > 0 ? cr : ci;
+  double cm[kZernMaxOrder + 1], sm[kZernMaxOrder + 1];
+  cm[0] = 1.0;
+  sm[0] = 0.0;
+  const double c = rn > 0.0 ? u / rn : 1.0, sn = rn > 0.0 ? v / rn : 0.0;
+#pragma unroll
+  for (int k = 0; k < kZernMaxOrder; ++k) {
+    cm[k + 1] = cm[k] * c - sm[k] * sn;
+    sm[k + 1] = cm[k] * sn + sm[k] * c;
   }
-  Zt[idx] = (float)(r * ang);
+  for (int j = 0; j < zb.n_zern; ++j) {
+    const int m = zb.m[j], am = m < 0 ? -m : m;
+    double r = 0.0;
+    for (int k = kZernMaxOrder; k >= 0; --k) r = r * rn + zb.rc[j][k];
+    double ang = 1.0;
+    if (am > 0 && rn == 0.0) {
+      ang = 0.0;                                  // odd N: the centre node
+    } else if (am > 0) {
+#pragma unroll
+      for (int q = 1; q <= kZernMaxOrder; ++q)
+        if (q == am) ang = m > 0 ? cm[q] : sm[q];
+    }
+    Zt[(size_t)j * NN + i] = (float)(r * ang);
+  }
 }
 
 void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s) {
-  const long long n = (long long)zb.n_zern * N * N;
-  if (n > 0) k_zernike_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(zb, N, Zt);
+  const int NN = N * N;
+  if (zb.n_zern > 0 && NN > 0) k_zernike_table<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(zb, N, Zt);
 }
 
 // dL/dc_j = sum_{p,q} Z_j[p][q] dL/dW_0[p][q] for `nb` pupils at once: CTA

@@ -744,19 +744,36 @@ __global__ void k_zernike_parts_fin(const double* __restrict__ zpart, int n_zern
 //   wfr[k][i] = frac(wfr_gl[i] + (sum_j c[k][j] Z_j[i] + W_0[k][i]) / 2 pi)
 // (Zernike basis table Zt [n_zern][N N]; the Zernike and free phases are
 // O(1) rad, so FP32 terms keep ~1e-7 rad).
+// Eight pupils per thread (grid y): each basis value is read once for all of
+// them; every pupil's sum runs over j in order, as for one pupil alone.
+constexpr int kGpPupils = 8;
 __global__ void k_group_phase(const float* __restrict__ wfr_gl, const float* __restrict__ Zt,
                               const double* __restrict__ coef, int n_zern,
-                              const float* __restrict__ phase_map, int NN, float* wfr) {
+                              const float* __restrict__ phase_map, int NN, int nb,
+                              float* wfr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN) return;
-  const int k = blockIdx.y;
-  float w = 0.f;
-  for (int j = 0; j < n_zern; ++j)
-    w = fmaf((float)coef[(size_t)k * n_zern + j], Zt[(size_t)j * NN + i], w);
-  if (phase_map) w += phase_map[(size_t)k * NN + i];
-  float cyc = wfr_gl[i] + w * (float)(0.5 / kPi);
-  cyc -= rintf(cyc);
-  wfr[(size_t)k * NN + i] = cyc;
+  const int k0 = blockIdx.y * kGpPupils;
+  float w[kGpPupils];
+#pragma unroll
+  for (int u = 0; u < kGpPupils; ++u) w[u] = 0.f;
+  for (int j = 0; j < n_zern; ++j) {
+    const float z = Zt[(size_t)j * NN + i];
+#pragma unroll
+    for (int u = 0; u < kGpPupils; ++u)
+      if (k0 + u < nb) w[u] = fmaf((float)coef[(size_t)(k0 + u) * n_zern + j], z, w[u]);
+  }
+  const float g = wfr_gl[i];
+#pragma unroll
+  for (int u = 0; u < kGpPupils; ++u) {
+    const int k = k0 + u;
+    if (k >= nb) break;
+    float wk = w[u];
+    if (phase_map) wk += phase_map[(size_t)k * NN + i];
+    float cyc = g + wk * (float)(0.5 / kPi);
+    cyc -= rintf(cyc);
+    wfr[(size_t)k * NN + i] = cyc;
+  }
 }
 
 // loss[k] = sum of the partials of pupil k (n_per each), FP64, fixed order.
@@ -1561,8 +1578,8 @@ struct TcBwdMaps {
 void tc_group_phase(const TcBwdOperands& ops, const float* wfr_gl, const float* Zt,
                     const double* coef, int n_zern, const float* phase_map, int N, int nb,
                     cudaStream_t s) {
-  tc::k_group_phase<<<dim3(ceil_div(N * N, 256), nb), 256, 0, s>>>(wfr_gl, Zt, coef, n_zern,
-                                                               phase_map, N * N, ops.wfr);
+  tc::k_group_phase<<<dim3(ceil_div(N * N, 256), ceil_div(nb, tc::kGpPupils)), 256, 0, s>>>(
+      wfr_gl, Zt, coef, n_zern, phase_map, N * N, nb, ops.wfr);
 }
 
 size_t tc_zernike_parts_bytes(int N, int n_zern, int nb) {
