@@ -539,6 +539,17 @@ def fourier_fwd_bwd(args, dev, stream, flush, world, check=True, steps=5):
                (3.0 if args.precision != "fp32" else 0.0) * flop / (ms * 1e-3) / 1e12
                / bf16_peak(),
            "l2": "flushed between timed steps (256 MB write)"}
+    if args.precision != "fp32":
+        # the split adjoint's intermediates, each written once and read back
+        # once per plane (bytes): pupil planes P, stage-1 output U, adjoint
+        # source R, V = A_x^H R (16-bit hi + lo) and Gh (FP32), plus the target
+        per_plane = 2 * (3 * N * 2 * N * 4 + 3 * ny * 2 * N * 4 + 3 * ny * 2 * nx * 4
+                         + 3 * N * 2 * ny * 4 + 3 * 2 * N * N * 4) + nx * ny * 4
+        inter = float(per_plane) * B * nz
+        hbm = load_peaks()[0].get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+        out["intermediate_bytes_per_step"] = inter
+        out["intermediate_traffic_gbs"] = inter / (ms * 1e-3) / 1e9
+        out["intermediate_traffic_frac_of_hbm"] = inter / (ms * 1e-3) / 1e9 / hbm
     if check:
         from oracle import adjoint as oadj
         from oracle.optics import Optics
