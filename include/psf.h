@@ -455,9 +455,24 @@ int psf_mlp_forward(const void* state, const float* query, int batch, float* out
 int psf_mlp_get_params(const void* state, float* params, void* stream);
 int psf_mlp_set_params(void* state, const float* params, void* stream);
 
+/* The profiles' on-axis phase phi (theta = 0 of Eq. 10-11): the Gibson-Lanni
+ * path of Eq. 13 at the query's depth t_s, the m = 0 Zernike terms of Eq. 15
+ * at rho = 0 (query coefficients c_1..c_21) and the defocus n_i z / lambda,
+ * in cycles (FP64, reduced mod 1).  Multiplies the complex profiles data
+ * [batch][3 x 256] (the interleaved re / im [batch][1536] layout) in place
+ * by e^{direction 2 pi i phi}.  The network is trained on targets with the
+ * phase divided out (direction -1: a smoother function of z and t_s) and
+ * psf_mlp_forward returns that form; psf_surrogate_profiles restores the
+ * phase (direction +1).  query: device float [batch][23]; data: device.
+ * PSF_ERR_ARG for NULL pointers, direction not +-1 or batch outside
+ * [0, 1048576]. */
+int psf_surrogate_phase(const psf_optics* base, const float* query, int batch,
+                        float* data, int direction, void* stream);
+
 /* Profiles of `batch` queries by the surrogate, with the Bessel path as the
- * fallback: queries whose predicted relative error, doubled as a safety
- * margin, exceeds max_rel_err (or is not finite) are
+ * fallback: the network's answer with its on-axis phase restored
+ * (psf_surrogate_phase), and queries whose predicted relative error, doubled
+ * as a safety margin, exceeds max_rel_err (or is not finite) are
  * recomputed by psf_bessel_vectorial (geometry of `base`, n_theta Gauss-
  * Legendre nodes, 256 radii up to the corner radius of the nx x ny grid at
  * dx, dy) and their outputs replaced.  Synchronises the stream once (to size

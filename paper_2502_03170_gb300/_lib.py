@@ -93,6 +93,7 @@ PROTOTYPES = {
     "psf_mlp_get_params": (_I, [_P, _P, _P]),
     "psf_mlp_set_params": (_I, [_P, _P, _P]),
     "psf_surrogate_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I]),
+    "psf_surrogate_phase": (_I, [_OPT, _P, _I, _P, _I, _P]),
     "psf_surrogate_profiles": (_I, [_P, _OPT, _P, _I, _D, _I, _I, _I, _D, _D,
                                     _I, _P, ctypes.POINTER(_I), _P, _S, _P]),
     "psf_bessel_workspace_size": (_S, [_OPT, _I, _I, _I, _I, _I, _I, _I]),

@@ -347,7 +347,7 @@ LayerPtrs layer_ptrs(const State& S) {
 // forward / backward sequences
 // ---------------------------------------------------------------------------
 int forward(const State& S, const Work& W, const float* q, int B, float* out,
-            bool train, int* status, cudaStream_t s) {
+            bool train, int* status, cudaStream_t s, const float2* row_phase = nullptr) {
   const ParamLayout P = param_layout();
   const int Bp = pad8(B);
   k_prep<<<ceil_div(B * IN_PAD, 256), 256, 0, s>>>(q, B, Bp, W.X0, train ? W.X0T : nullptr);
@@ -375,6 +375,7 @@ int forward(const State& S, const Work& W, const float* q, int B, float* out,
       g.epi = EPI_LINEAR;
       g.out = out;
       g.ldo = OUT;
+      g.row_phase = row_phase;
     }
     const int r = gemm(g, s);
     if (r) return r;
@@ -524,6 +525,13 @@ extern "C" int psf_mlp_gradients(void* state, const float* query, const float* t
 
 extern "C" int psf_mlp_forward(const void* state, const float* query, int batch, float* out,
                                float* err_log10, void* ws, size_t ws_bytes, void* stream) {
+  return psf::mlp::forward_rows(state, query, batch, out, err_log10, ws, ws_bytes, nullptr,
+                                stream);
+}
+
+int psf::mlp::forward_rows(const void* state, const float* query, int batch, float* out,
+                           float* err_log10, void* ws, size_t ws_bytes,
+                           const float2* row_phase, void* stream) {
   int r = check_batch(batch);
   if (r) return r;
   if (!state || !query || !out || !ws) return err(PSF_ERR_ARG, "mlp: NULL pointer");
@@ -532,7 +540,7 @@ extern "C" int psf_mlp_forward(const void* state, const float* query, int batch,
   cudaStream_t s = (cudaStream_t)stream;
   const State S = state_layout((void*)state);
   cudaMemsetAsync(ws, 0, sizeof(int), s);
-  r = forward(S, W, query, batch, out, false, (int*)ws, s);
+  r = forward(S, W, query, batch, out, false, (int*)ws, s, row_phase);
   if (r) return err(r, "mlp: GEMM launch failed");
   if (err_log10) {
     const ParamLayout P = param_layout();

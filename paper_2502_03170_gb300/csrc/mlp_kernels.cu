@@ -59,6 +59,12 @@ struct KArgs {
 
 PSF_D float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
+// (re, im) pairs of a float4 times the complex e
+PSF_D float4 cmul2(float4 w, float2 e) {
+  return make_float4(w.x * e.x - w.y * e.y, w.x * e.y + w.y * e.x,
+                     w.z * e.x - w.w * e.y, w.z * e.y + w.w * e.x);
+}
+
 // bias[n0 .. n0 + GCH) (0 past N), as four 16-byte loads when the chunk is full
 PSF_D void load_bias(const GemmArgs& g, int n0, bool full, float (&b)[GCH]) {
   if (full && (((uintptr_t)(g.bias + n0) & 15) == 0)) {
@@ -233,6 +239,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
             ((uintptr_t)ow & 15) == 0) {
           // FP32 output through the warp's staging rows
           float* st = gstg + (warp - 2) * 32 * GSTG_LD;
+          // the row's complex factor applies to (re, im) column pairs (n0 even)
+          const bool rp_ok = g.row_phase != nullptr && mok;
+          const float2 e_row = rp_ok ? g.row_phase[m] : make_float2(1.f, 0.f);
           float bias[GCH];
           if (g.epi == EPI_LINEAR) load_bias(g, n0, true, bias);
 #pragma unroll
@@ -244,6 +253,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
               w.y += bias[4 * q + 1];
               w.z += bias[4 * q + 2];
               w.w += bias[4 * q + 3];
+              if (rp_ok) w = cmul2(w, e_row);
             }
             ((float4*)(st + lane * GSTG_LD))[q] = w;
           }
@@ -338,6 +348,15 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
           for (int j = 0; j < GCH; ++j) {
             v[j] = __uint_as_float(r[j]);
             if (g.epi == EPI_LINEAR) v[j] += bias[j];
+          }
+          if (g.epi == EPI_LINEAR && g.row_phase) {
+            const float2 e = g.row_phase[m];
+#pragma unroll
+            for (int j = 0; j < GCH; j += 2) {
+              const float re = v[j] * e.x - v[j + 1] * e.y;
+              v[j + 1] = v[j] * e.y + v[j + 1] * e.x;
+              v[j] = re;
+            }
           }
           if (full && (g.ldo & 3) == 0) {
 #pragma unroll

@@ -47,10 +47,17 @@ struct GemmArgs {
   uint16_t* YT;  int ldyt;       // [N][M] bf16
   uint16_t* Z;   int ldz;        // [M][N] bf16 (pre-activation; read by EPI_DSILU)
   float* out;    int ldo;        // [M][N] fp32
+  const float2* row_phase;       // EPI_LINEAR: row m's (re, im) column pairs times row_phase[m], or null
   int* status;
 };
 
 int gemm(const GemmArgs& g, cudaStream_t s);
+
+// psf_mlp_forward with the output rows multiplied by the complex factors
+// row_phase[B] (null: as psf_mlp_forward) inside the output layer's epilogue.
+int forward_rows(const void* state, const float* query, int batch, float* out,
+                 float* err_log10, void* ws, size_t ws_bytes, const float2* row_phase,
+                 void* stream);
 
 }  // namespace mlp
 }  // namespace psf

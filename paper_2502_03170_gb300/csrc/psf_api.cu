@@ -181,6 +181,19 @@ static GLLayers gl_layers(const psf_optics* o, double ts) {
   return g;
 }
 
+// On-axis (theta = 0) optical path of Eq. 13 as a0 + a1 t_s cycles: every
+// layer contributes t_l n_l / lambda, and the thicknesses are affine in t_s.
+void psf_axis_path_cycles(const psf_optics* o, double* a0, double* a1) {
+  const GLLayers L0 = gl_layers(o, 0.0), L1 = gl_layers(o, 1.0);
+  double s0 = 0.0, s1 = 0.0;
+  for (int l = 0; l < L0.n; ++l) {
+    s0 += L0.t[l] * L0.n_idx[l];
+    s1 += (L1.t[l] - L0.t[l]) * L0.n_idx[l];
+  }
+  *a0 = s0 / o->lambda;
+  *a1 = s1 / o->lambda;
+}
+
 // Layers with the same index share one root: t_a sqrt(n^2 - .) + t_b sqrt(n^2 - .)
 // = (t_a + t_b) sqrt(n^2 - .).  Design layers equal to the actual ones cancel.
 static GLLayers merge_layers(const GLLayers& in) {
@@ -486,6 +499,16 @@ size_t fourier_min_workspace_size(const psf_optics* opt, int n_pupil, const psf_
                                   int precision) {
   if (check_fourier_args(opt, n_pupil, grid, precision)) return 0;
   return fourier_layout(nullptr, n_pupil, grid, precision, 1).bytes;
+}
+
+// Z_j at the pupil centre (rho = 0) for Noll j = 1 .. n_zern (Eq. 15,
+// RMS normalisation): sqrt(n + 1) (-1)^(n/2) for m = 0, 0 otherwise.
+void psf_axis_zernike(int n_zern, double* z0) {
+  for (int j = 1; j <= n_zern; ++j) {
+    int n, m;
+    noll_nm(j, &n, &m);
+    z0[j - 1] = m == 0 ? sqrt(n + 1.0) * (((n / 2) & 1) ? -1.0 : 1.0) : 0.0;
+  }
 }
 
 }  // namespace psf

@@ -10,6 +10,8 @@
 
 namespace psf {
 void set_last_error(const char* msg);
+void psf_axis_path_cycles(const psf_optics* o, double* a0, double* a1);
+void psf_axis_zernike(int n_zern, double* z0);
 }
 
 namespace {
@@ -45,6 +47,65 @@ __global__ void k_scatter(const float* __restrict__ prof, const int* __restrict_
   out[(size_t)idx[k] * mlp::OUT + e] = prof[i];
 }
 
+// The profiles' on-axis phase (theta = 0 in Eq. 10-11): Gibson-Lanni path
+// (Eq. 13) a0 + a1 t_s and the m = 0 Zernike terms at rho = 0 (Eq. 15) of the
+// pupil, plus the defocus n_i z / lambda, in cycles.  The network learns the
+// profiles with this phase divided out (a smoother function of z and t_s);
+// k_axis_phase multiplies [B][3 x 256] complex values by e^{dir 2 pi i phi}.
+struct AxisPhase {
+  double a0, a1, n_over_lambda;
+  double z0[21];
+};
+
+PSF_D float2 axis_phasor(const float* __restrict__ qb, const AxisPhase& ap, int dir) {
+  double cyc = ap.a0 + ap.a1 * (double)qb[21] + ap.n_over_lambda * (double)qb[22];
+  double zs = 0.0;
+  for (int j = 0; j < 21; ++j) zs += ap.z0[j] * (double)qb[j];
+  cyc += zs * (0.5 / 3.14159265358979323846);
+  cyc -= rint(cyc);
+  double sn, cs;
+  sincospi(2.0 * cyc, &sn, &cs);
+  return make_float2((float)cs, (float)(dir > 0 ? sn : -sn));
+}
+
+// e^{dir 2 pi i phi} of each query, one thread per query (FP64 phase
+// reduced mod 1 cycle, then the FP64 sincospi)
+__global__ void k_axis_phasor(const float* __restrict__ q, int B, AxisPhase ap, int dir,
+                              float2* ph) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  ph[b] = axis_phasor(q + (size_t)b * mlp::IN, ap, dir);
+}
+
+// data [B][768] complex times the phasor of its query: 16 queries per block,
+// their phasors computed in parallel into shared memory first
+constexpr int kRowsPerBlock = 16;
+__global__ void __launch_bounds__(256)
+k_rows_phase(const float* __restrict__ q, int B, AxisPhase ap, int dir, float4* data) {
+  __shared__ float2 ph[kRowsPerBlock];
+  const int b0 = blockIdx.x * kRowsPerBlock;
+  if (threadIdx.x < kRowsPerBlock && b0 + threadIdx.x < B)
+    ph[threadIdx.x] = axis_phasor(q + (size_t)(b0 + threadIdx.x) * mlp::IN, ap, dir);
+  __syncthreads();
+  const int nb = min(kRowsPerBlock, B - b0);
+  constexpr int PER = mlp::OUT / 4;                       // float4 per query
+  float4* d = data + (size_t)b0 * PER;
+  for (int i = threadIdx.x; i < nb * PER; i += blockDim.x) {
+    const float2 e = ph[i / PER];
+    const float4 w = d[i];
+    d[i] = make_float4(w.x * e.x - w.y * e.y, w.x * e.y + w.y * e.x,
+                       w.z * e.x - w.w * e.y, w.z * e.y + w.w * e.x);
+  }
+}
+
+AxisPhase axis_phase(const psf_optics* o) {
+  AxisPhase ap;
+  psf_axis_path_cycles(o, &ap.a0, &ap.a1);
+  ap.n_over_lambda = o->n_i / o->lambda;
+  psf_axis_zernike(21, ap.z0);
+  return ap;
+}
+
 struct SurLayout {
   size_t mlp_ws, bessel_ws;
   int* idx;
@@ -53,6 +114,7 @@ struct SurLayout {
   double *depth, *zern, *z;
   int* offs;
   float* prof;
+  float2* phase;
   char* mlp;
   char* bessel;
   size_t bytes;
@@ -81,6 +143,7 @@ SurLayout sur_layout(void* base, const psf_optics* opt, int B, int n_theta, int 
   L.z = (double*)take((size_t)B * 8);
   L.offs = (int*)take((size_t)(B + 1) * 4);
   L.prof = (float*)take((size_t)B * mlp::OUT * 4);
+  L.phase = (float2*)take((size_t)B * 8);
   L.bessel = take(L.bessel_ws);
   L.bytes = align_up(off, 256);
   return L;
@@ -119,7 +182,11 @@ extern "C" int psf_surrogate_profiles(const void* state, const psf_optics* base,
   cudaStream_t s = (cudaStream_t)stream;
   // the MLP answers all queries; its error head gives log10(rel. error)
   float* errp = L.errp;
-  int r = psf_mlp_forward(state, query, batch, out, errp, L.mlp, L.mlp_ws, stream);
+  // the network's profiles carry the on-axis phase divided out: the output
+  // layer's epilogue restores it row by row
+  k_axis_phasor<<<ceil_div(batch, 256), 256, 0, s>>>(query, batch, axis_phase(base), 1,
+                                                     L.phase);
+  int r = mlp::forward_rows(state, query, batch, out, errp, L.mlp, L.mlp_ws, L.phase, stream);
   if (r) return r;
   cudaMemsetAsync(L.count, 0, 4, s);
   // accept a prediction only if twice its predicted error is within the bound
@@ -147,6 +214,26 @@ extern "C" int psf_surrogate_profiles(const void* state, const psf_optics* base,
   }
   if (cudaPeekAtLastError() != cudaSuccess) {
     set_last_error("surrogate: launch failed");
+    return PSF_ERR_CUDA;
+  }
+  return PSF_OK;
+}
+
+extern "C" int psf_surrogate_phase(const psf_optics* base, const float* query, int batch,
+                                   float* data, int direction, void* stream) {
+  if (!base || !query || !data) {
+    set_last_error("surrogate phase: NULL pointer");
+    return PSF_ERR_ARG;
+  }
+  if (batch < 0 || batch > (1 << 20) || (direction != 1 && direction != -1)) {
+    set_last_error("surrogate phase: batch outside [0, 1048576] or direction not +-1");
+    return PSF_ERR_ARG;
+  }
+  if (batch == 0) return PSF_OK;
+  k_rows_phase<<<ceil_div(batch, kRowsPerBlock), 256, 0, (cudaStream_t)stream>>>(
+      query, batch, axis_phase(base), direction, (float4*)data);
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    set_last_error("surrogate phase: launch failed");
     return PSF_ERR_CUDA;
   }
   return PSF_OK;

@@ -73,8 +73,10 @@ class Surrogate:
         return g, loss
 
     def forward(self, query, error_head=True):
-        """Profiles [B][1536] and the error head's log10 relative error [B]
-        (None with error_head=False: the network alone)."""
+        """The network's profiles [B][1536] (on-axis phase divided out:
+        axis_phase(query, out, optics, +1) restores them, as profiles() does)
+        and the error head's log10 relative error [B] (None with
+        error_head=False: the network alone)."""
         q = self._f32(query)
         B = q.shape[0]
         ws = self._work(B)
@@ -104,6 +106,25 @@ class Surrogate:
             n_theta, nx, ny, float(dx), float(dy), prec, api._ptr(out),
             ctypes.byref(nfb), api._ptr(ws), ws.numel(), api._stream()))
         return out, nfb.value
+
+
+def axis_phase(query, data, optics, direction):
+    """In place: the complex profiles data [B][1536] times e^{direction 2 pi i
+    phi}, phi the on-axis phase of each query (psf_surrogate_phase).  The
+    network learns the profiles with the phase divided out (direction -1)."""
+    lib = _lib.load()
+    q = query if torch.is_tensor(query) else torch.as_tensor(np.asarray(query))
+    q = q.to(device=data.device, dtype=torch.float32).contiguous()
+    o = optics if isinstance(optics, _lib.PsfOptics) else api.make_optics(optics)
+    _lib.check(lib, lib.psf_surrogate_phase(ctypes.byref(o), api._ptr(q), q.shape[0],
+                                            api._ptr(data), int(direction), api._stream()))
+    return data
+
+
+def residual_targets(query, targets, optics):
+    """Training targets in the form the network learns: the Bessel-path
+    profiles with their on-axis phase divided out (a copy)."""
+    return axis_phase(query, targets.clone(), optics, -1)
 
 
 def bessel_targets(query, optics, n_theta, nx, ny, dx, dy, precision="split_fp16",

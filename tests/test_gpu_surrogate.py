@@ -79,8 +79,37 @@ def test_fallback_paths(lib):
     assert np.array_equal(out.cpu().numpy(), ref)
     out2, nfb2 = s.profiles(q, d, max_rel_err=1e30, **GEOM)  # nothing falls back
     mo, _ = s.forward(q)
+    sg.axis_phase(q, mo, d, +1)                              # the same restore
     assert nfb2 == 0
     assert torch.equal(out2, mo)
+
+
+def test_axis_phase_against_oracle(lib):
+    """The on-axis phase against its definition evaluated by the oracle's own
+    Gibson-Lanni path (Eq. 13-14) and Zernike polynomials (Eq. 15) at rho = 0
+    plus k z; and the -1 / +1 round trip."""
+    import math
+
+    from oracle.optics import Optics, gibson_lanni_phase, zernike
+    d = W.optics_gibson_lanni(0.0)
+    opt = Optics.from_dict(d)
+    q = sg.queries(64, seed_salt=5)
+    q[:, 0] = 0.3                                            # piston enters as well
+    ones = torch.zeros((64, 1536), device="cuda")
+    ones[:, 0::2] = 1.0
+    ph = sg.axis_phase(q, ones.clone(), d, +1).cpu().numpy()
+    got = ph[:, 0::2] + 1j * ph[:, 1::2]
+    for b in range(64):
+        phi = float(np.real(gibson_lanni_phase(opt.with_depth(float(q[b, 21])),
+                                               np.zeros(1)))[0])
+        phi += sum(float(q[b, j - 1]) * float(zernike(j, np.zeros(1), np.zeros(1))[0])
+                   for j in range(1, 22))
+        phi += opt.k * float(q[b, 22])
+        ref = complex(math.cos(phi), math.sin(phi))
+        assert np.max(np.abs(got[b] - ref)) <= 2e-6, b
+    t = torch.randn((64, 1536), device="cuda")
+    back = sg.axis_phase(q, sg.residual_targets(q, t, d), d, +1)
+    assert rel_l2(back.cpu().numpy(), t.cpu().numpy()) <= 1e-6
 
 
 def train_surrogate(d, n_train=1 << 20, B=4096, steps=20000, lr0=2e-3, seed=12):
@@ -89,6 +118,7 @@ def train_surrogate(d, n_train=1 << 20, B=4096, steps=20000, lr0=2e-3, seed=12):
     t_all = torch.empty((n_train, 1536), device="cuda")
     for k in range(0, n_train, 131072):
         t_all[k:k + 131072] = sg.bessel_targets(q_all[k:k + 131072], d, **GEOM)
+    sg.axis_phase(q_all, t_all, d, -1)              # the form the network learns
     s = sg.Surrogate(seed=seed)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
@@ -117,6 +147,7 @@ def test_training_gain(lib):
     q = torch.as_tensor(sg.queries(nq, seed_salt=99), device="cuda")
     ref = sg.bessel_targets(q, d, **GEOM)
     out, err_pred = s.forward(q)
+    sg.axis_phase(q, out, d, +1)
     true = (torch.linalg.norm(out - ref, dim=1) / torch.linalg.norm(ref, dim=1)).cpu().numpy()
     pred = err_pred.cpu().numpy()
     for thr in (1e-3, 3e-2, 1e-1):
