@@ -270,8 +270,8 @@ def test_split_modes_outside_the_envelope_are_refused(lib):
         assert e.value.code == _lib.PSF_ERR_PRECISION, (N, prec)
 
 
-@pytest.mark.parametrize("N,mode", [(256, "split_fp16"), (1024, "split_bf16"),
-                                    (1536, "chirpz_fp32")])
+@pytest.mark.parametrize("N,mode", [(256, "split_fp16"), (512, "split_fp16"),
+                                    (1024, "split_bf16"), (1536, "chirpz_fp32")])
 def test_auto_precision(lib, N, mode):
     """"auto" runs the fastest mode inside the accuracy envelope (bitwise that
     mode's stack) and stays within 1e-5 of the oracle."""
