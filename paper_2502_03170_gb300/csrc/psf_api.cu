@@ -7,6 +7,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "bessel_backward.cuh"
@@ -275,7 +278,7 @@ static ZernPoly zernike_poly(const double* c, int n_zern) {
 // Gauss-Legendre nodes on [-1, 1] by Newton's method on P_n (three-term
 // recurrence), weights 2 / ((1 - x^2) P_n'(x)^2).
 // ---------------------------------------------------------------------------
-static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+static void gauss_legendre_compute(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
   for (int i = 0; i < (n + 1) / 2; ++i) {
@@ -299,6 +302,22 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
     x[n - 1 - i] = r;
     w[i] = w[n - 1 - i] = 2.0 / ((1.0 - r * r) * dp * dp);
   }
+}
+
+// The rule depends on n alone: computed once per n (the Newton iterations
+// cost a few hundred microseconds of host time at 200 nodes) and kept.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  static std::mutex mu;
+  static std::map<int, std::pair<std::vector<double>, std::vector<double>>> rules;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = rules.find(n);
+  if (it == rules.end()) {
+    std::vector<double> xs, ws;
+    gauss_legendre_compute(n, xs, ws);
+    it = rules.emplace(n, std::make_pair(std::move(xs), std::move(ws))).first;
+  }
+  x = it->second.first;
+  w = it->second.second;
 }
 
 // ---------------------------------------------------------------------------
