@@ -218,8 +218,31 @@ struct Shape {
   static constexpr int TAB = kCztTw2 + kCztTwL + L;   // float2 words
   static constexpr int TAB4 = (TAB + 1) / 2;          // in 16-byte elements
   static constexpr size_t SMEM = 16 * ((size_t)TAB4 + (size_t)SLOTS * STRIDE);
+  // Barrier group: the whole warps that hold the QL interleaved transform
+  // pairs of one buffer set (threads [g GROUP, (g + 1) GROUP)); only they
+  // exchange data through those buffers.
+  static constexpr int GROUP = QL * T < 32 ? 32 : QL * T;
+  static constexpr int GROUPS = THREADS / GROUP;
   static_assert(SLOTS % QL == 0, "slots");
+  static_assert(THREADS % GROUP == 0 && GROUP % 32 == 0, "barrier group");
+  static_assert(GROUPS <= 15, "named barriers 1..15");
 };
+
+// Synchronise the barrier group of the calling thread (named barrier
+// 1 + group, GROUP threads, every one of which arrives): the transform
+// buffers of different groups are independent, so the groups of a CTA run
+// their FFT passes out of step.
+template <class S>
+PSF_D void group_sync() {
+  if constexpr (S::GROUP == S::THREADS) {
+    __syncthreads();
+  } else if constexpr (S::GROUP == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / S::GROUP), "n"(S::GROUP)
+                 : "memory");
+  }
+}
 
 // inputs with r >= NIN are zero: NIN = smallest of {4, 8, 16} >= ceil(N / T)
 template <class S>
@@ -246,7 +269,7 @@ PSF_D void load_tables(const CztDir& d, float2* tab) {
 
 // Forward DFT_L of the transform pair whose elements t + T r this thread
 // holds in v[r] (zero for r >= NIN); on return v[r] = X[t + T r].  Every
-// thread of the CTA calls it together (it synchronises the CTA).
+// thread of a barrier group calls it together (it synchronises the group).
 template <class S, int NIN>
 PSF_D void fft_block(c2 (&v)[16], float4* buf, const float2* tab, int t) {
   constexpr int T = S::T, R3 = S::R3;
@@ -254,10 +277,10 @@ PSF_D void fft_block(c2 (&v)[16], float4* buf, const float2* tab, int t) {
   const float2* twL = tab + kCztTw2;
   // pass 1: radix 16, Ns = 1
   dft16<NIN>(v);
-  __syncthreads();   // earlier readers of buf are done
+  group_sync<S>();   // earlier readers of buf are done
 #pragma unroll
   for (int s = 0; s < 16; ++s) buf[pidx(16 * t + s)] = st(v[s]);
-  __syncthreads();
+  group_sync<S>();
   // pass 2: radix 16, Ns = 16
   const int k = t & 15;
 #pragma unroll
@@ -268,11 +291,11 @@ PSF_D void fft_block(c2 (&v)[16], float4* buf, const float2* tab, int t) {
   if constexpr (R3 == 1) {
     return;   // L = 256: v[s] = X[t + 16 s]
   } else {
-    __syncthreads();
+    group_sync<S>();
     const int base = (t >> 4) * 256 + k;
 #pragma unroll
     for (int s = 0; s < 16; ++s) buf[pidx(base + 16 * s)] = st(v[s]);
-    __syncthreads();
+    group_sync<S>();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = ld(buf[pidx(t + T * r)]);
     // pass 3: radix R3, Ns = 256; j = t + T i holds elements i + r (16/R3)

@@ -4,7 +4,9 @@
 // FFT; CS channel slots of a column pair run side by side (CS = 3) or in
 // turn (CS = 1, the longest FFT).  A CTA walks a group of z-planes and, where
 // shared memory allows, prefetches the next item's input rows with cp.async
-// while the current one is transformed.
+// while the current one is transformed.  The FFT passes synchronise one
+// barrier group (the warps of one slot); only the channel sum of CS = 3,
+// which reads the three channel slots, synchronises the CTA.
 #include "czt_fft.cuh"
 
 namespace psf {
@@ -124,7 +126,7 @@ k_czt_stage2(const float2* __restrict__ Tin, int N, int nx, int ny, int nzc, int
     fft_block<S, 16>(v, buf, tab, t);
     float2* fo = F ? F + (size_t)(zc * 3 + c) * nx * ny + b : nullptr;
     float2* red = reinterpret_cast<float2*>(buf);
-    if constexpr (CS == 3) __syncthreads();   // the last pass has read buf
+    if constexpr (CS == 3) group_sync<S>();   // the last pass has read buf
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int a = t + T * r;
@@ -170,6 +172,9 @@ k_czt_stage2(const float2* __restrict__ Tin, int N, int nx, int ny, int nzc, int
         }
       }
     }
+    // the channel slots read above are rewritten by the next item's FFT,
+    // whose barriers span one group only
+    if constexpr (CS == 3) __syncthreads();
   }
   if constexpr (G::PREFETCH) cp_async_wait_all();
 }
