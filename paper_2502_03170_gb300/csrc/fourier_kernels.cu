@@ -504,7 +504,8 @@ void launch_grad_accum(const float2* Gh, const float2* P, float* gW, int NN,
 __global__ void k_zernike_table(ZernBasis zb, int N, float* __restrict__ Zt) {
   // one thread per node, every term: the azimuthal factors cos / sin(m phi)
   // once per node by the rotation recursion, the radial polynomial of each
-  // term by Horner (FP64)
+  // term by Horner from its degree down (FP64; the coefficients above the
+  // degree are zero, so starting higher would add exact zeros only)
   const int NN = N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN) return;
@@ -523,7 +524,7 @@ __global__ void k_zernike_table(ZernBasis zb, int N, float* __restrict__ Zt) {
   for (int j = 0; j < zb.n_zern; ++j) {
     const int m = zb.m[j], am = m < 0 ? -m : m;
     double r = 0.0;
-    for (int k = kZernMaxOrder; k >= 0; --k) r = r * rn + zb.rc[j][k];
+    for (int k = zb.deg[j]; k >= 0; --k) r = r * rn + zb.rc[j][k];
     double ang = 1.0;
     if (am > 0 && rn == 0.0) {
       ang = 0.0;                                  // odd N: the centre node

@@ -121,6 +121,7 @@ void launch_grad_accum(const float2* Gh, const float2* P, float* gW, int NN,
 struct ZernBasis {
   int n_zern;
   int m[66];                    // signed azimuthal order (Noll)
+  int deg[66];                  // radial degree n: rc[j][k] = 0 for k > deg[j]
   double rc[66][11];            // radial coefficients (normalised)
 };
 void launch_zernike_table(const ZernBasis& zb, int N, float* Zt, cudaStream_t s);

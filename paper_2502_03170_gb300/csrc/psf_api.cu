@@ -772,6 +772,7 @@ static ZernBasis zernike_basis(int n_zern) {
     int n, m;
     noll_nm(j, &n, &m);
     zb.m[j - 1] = m;
+    zb.deg[j - 1] = n;
     zernike_radial_coeffs(n, m < 0 ? -m : m, zb.rc[j - 1]);
   }
   return zb;

@@ -745,23 +745,31 @@ __global__ void k_zernike_parts_fin(const double* __restrict__ zpart, int n_zern
 // (Zernike basis table Zt [n_zern][N N]; the Zernike and free phases are
 // O(1) rad, so FP32 terms keep ~1e-7 rad).
 // Eight pupils per thread (grid y): each basis value is read once for all of
-// them; every pupil's sum runs over j in order, as for one pupil alone.
+// them; every pupil's sum runs over j in order, as for one pupil alone.  The
+// block's coefficients are rounded to FP32 once, into shared memory (a
+// double-to-float conversion issues at the FP64 rate).
 constexpr int kGpPupils = 8;
+constexpr int kGpMaxZern = 66;
 __global__ void k_group_phase(const float* __restrict__ wfr_gl, const float* __restrict__ Zt,
                               const double* __restrict__ coef, int n_zern,
                               const float* __restrict__ phase_map, int NN, int nb,
                               float* wfr) {
+  __shared__ float cf[kGpPupils][kGpMaxZern];
+  const int k0 = blockIdx.y * kGpPupils;
+  for (int e = threadIdx.x; e < kGpPupils * n_zern; e += blockDim.x) {
+    const int u = e / n_zern, j = e - u * n_zern;
+    cf[u][j] = k0 + u < nb ? (float)coef[(size_t)(k0 + u) * n_zern + j] : 0.f;
+  }
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN) return;
-  const int k0 = blockIdx.y * kGpPupils;
   float w[kGpPupils];
 #pragma unroll
   for (int u = 0; u < kGpPupils; ++u) w[u] = 0.f;
   for (int j = 0; j < n_zern; ++j) {
     const float z = Zt[(size_t)j * NN + i];
 #pragma unroll
-    for (int u = 0; u < kGpPupils; ++u)
-      if (k0 + u < nb) w[u] = fmaf((float)coef[(size_t)(k0 + u) * n_zern + j], z, w[u]);
+    for (int u = 0; u < kGpPupils; ++u) w[u] = fmaf(cf[u][j], z, w[u]);
   }
   const float g = wfr_gl[i];
 #pragma unroll
