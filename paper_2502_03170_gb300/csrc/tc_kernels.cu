@@ -673,6 +673,7 @@ __global__ void k_twiddle_adj_split(int N, int n_out, double alpha, uint16_t* hi
 // chain rule of Eq. 15 follows at once (Zt non-null): each warp reduces
 // Z_j gW over its 32 nodes for every j and writes one FP64 partial to
 // zpart[pupil][j][warp]; k_zernike_parts_fin sums them in a fixed order.
+constexpr int kGwPlanes = 4;   // planes whose Gh loads are in flight together
 __global__ void __launch_bounds__(256)
 k_gw_fold(const float* __restrict__ Ghf, NodeTable t, const float2* __restrict__ zz, int N,
           int p0, int planes, int nz_per, float scale, float* gW,
@@ -691,20 +692,46 @@ k_gw_fold(const float* __restrict__ Ghf, NodeTable t, const float2* __restrict__
     const f2x kap{t.kh[i], t.kl[i]};
     float* dst = gW + (size_t)pk * NN + i;
     v = (p0 + a - pk * nz_per == 0) ? 0.f : *dst;
-#pragma unroll 4
-    for (int pl = a; pl < b; ++pl) {
+    // one plane's contribution, its six Gh values already loaded
+    auto plane_term = [&](int pl, const float (&gh)[6]) {
       const float2 z = zz[p0 + pl - pk * nz_per];
       const float2 e = cis_cycles(frac_mul_add(kap, f2x{z.x, z.y}, w));
       float acc = 0.f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const size_t gb = ((size_t)(pl * 3 + c) * 2) * NN + i;
         const float pr = amp[2 * c] * e.x - amp[2 * c + 1] * e.y;
         const float pi = amp[2 * c] * e.y + amp[2 * c + 1] * e.x;
-        acc = fmaf(Ghf[gb], pr, acc);
-        acc = fmaf(Ghf[gb + NN], pi, acc);
+        acc = fmaf(gh[2 * c], pr, acc);
+        acc = fmaf(gh[2 * c + 1], pi, acc);
       }
       v = fmaf(scale, acc, v);
+    };
+    // the Gh values of kGwPlanes planes are loaded before any is used: the
+    // kernel streams Gh once, and these loads in flight are what keeps HBM
+    // busy (the sum still runs plane by plane, in order)
+    int pl = a;
+    for (; pl + kGwPlanes <= b; pl += kGwPlanes) {
+      float gh[kGwPlanes][6];
+#pragma unroll
+      for (int u = 0; u < kGwPlanes; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t gb = ((size_t)((pl + u) * 3 + c) * 2) * NN + i;
+          gh[u][2 * c] = Ghf[gb];
+          gh[u][2 * c + 1] = Ghf[gb + NN];
+        }
+#pragma unroll
+      for (int u = 0; u < kGwPlanes; ++u) plane_term(pl + u, gh[u]);
+    }
+    for (; pl < b; ++pl) {
+      float gh[6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t gb = ((size_t)(pl * 3 + c) * 2) * NN + i;
+        gh[2 * c] = Ghf[gb];
+        gh[2 * c + 1] = Ghf[gb + NN];
+      }
+      plane_term(pl, gh);
     }
     *dst = v;
   }
