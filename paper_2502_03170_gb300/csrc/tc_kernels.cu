@@ -997,6 +997,17 @@ constexpr int PSTAGE_BYTES = 2 * A_BYTES + 2 * PB_BYTES;
 constexpr int PSMEM_BYTES = PS_STAGES * PSTAGE_BYTES + 1024 + 1024;
 
 
+// Returns the accumulator to the leader: an arrival on its mbarrier (a
+// shared::cluster address) with the default release.cta semantics.  A
+// cluster-scope release would first wait until every global store of the
+// tile just written is visible cluster-wide, holding the accumulator for the
+// stores' latency; the hand-off orders only TMEM reads, which
+// tcgen05.wait::ld has completed and tcgen05.fence::before_thread_sync
+// orders before this arrival.
+PSF_D void release_acc_remote(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
 PSF_D void decode_pair(const Params& p, int t, int& plane, int& mp, int& nt) {
   const int m_pairs = (p.m_tiles + 1) / 2;
   const int tpp = m_pairs * p.n_tiles;
@@ -1164,7 +1175,7 @@ k_split_cgemm_pair(const __grid_constant__ CUtensorMap mapA_hi,
       const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * ACC_COL);
       tile_epilogue(p, tbase, plane, mt, nt, quad, lane);
       tmem_fence_before();
-      mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));   // the leader's barrier
+      release_acc_remote(mapa_shared(tempty_bar(acc), 0));   // the leader's barrier
       if (++acc == PS_ACCS) {
         acc = 0;
         acc_phase ^= 1u;
