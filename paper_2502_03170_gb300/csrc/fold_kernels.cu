@@ -251,11 +251,17 @@ PSF_D void store_piece(const FoldParams& p, size_t off, size_t lo_delta, const f
 }
 
 // Releases the accumulator on the leader's barrier once this warp has read
-// its columns (before the arithmetic and the stores of the tile).
+// its columns (before the arithmetic and the stores of the tile).  The
+// arrival keeps the default release.cta semantics: a cluster-scope release
+// would first wait until the warp's earlier global stores (the previous
+// tile's output, often still in flight) are visible cluster-wide, while the
+// hand-off orders only the TMEM reads, which tcgen05.wait::ld has completed
+// and tcgen05.fence::before_thread_sync orders before the arrival.
 PSF_D void release_acc(int lane, uint32_t bar_cluster) {
   tmem_fence_before();
   __syncwarp();
-  if (lane == 0) mbar_arrive_cluster(bar_cluster);
+  if (lane == 0)
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
 // ---------------------------------------------------------------------------
