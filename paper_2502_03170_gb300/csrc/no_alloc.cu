@@ -12,11 +12,10 @@
 //
 // The array is a file-scope __device__ variable, so every GPU on which the
 // library is loaded holds PSF_NOALLOC_SCRATCH_BYTES of it until the process
-// exits.  Host code cannot use the array's name as a device address: its
-// address is looked up once per device with cudaGetSymbolAddress.
+// exits.  Host code cannot use the array's name as a device address: each
+// call looks its address up in the current context with
+// cudaGetSymbolAddress.
 #include <stdio.h>
-
-#include <mutex>
 
 #include "psf_common.cuh"
 
@@ -32,32 +31,19 @@ void set_last_error(const char* msg);
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 __device__ __align__(256) unsigned char g_noalloc_scratch[PSF_NOALLOC_SCRATCH_BYTES];
 
-void* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device (set-up on the
-// first call for that device).
+// Device address of the scratch array in the current context.  It is looked
+// up on every call (a host-side lookup) rather than cached, so a call after
+// a device reset, which reloads the module, sees the new address.
 int scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    psf::set_last_error("noalloc: no usable current CUDA device");
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    psf::set_last_error("noalloc: cudaGetSymbolAddress of the scratch array failed");
     return PSF_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      psf::set_last_error("noalloc: cudaGetSymbolAddress of the scratch array failed");
-      return PSF_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return PSF_OK;
 }
 
