@@ -769,14 +769,13 @@ k_fold_pupil(NodeTable t, int N, int H, int Kp, const float2* __restrict__ zz, i
             *(uint4*)(P + o) = make_uint4(h[0], h[1], h[2], h[3]);
             *(uint4*)(P + o + var) = make_uint4(l[0], l[1], l[2], l[3]);
           } else {
-            uint16_t h[4], l[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) split16(v[s][r][ri][k], bf16, h[k], l[k]);
+            // packed pairs: element k in the low half, k + 1 in the high half
+            uint32_t h01, l01, h23, l23;
+            split2(v[s][r][ri][0], v[s][r][ri][1], bf16, h01, l01);
+            split2(v[s][r][ri][2], v[s][r][ri][3], bf16, h23, l23);
             uint16_t* P = (uint16_t*)Pout;
-            *(uint2*)(P + o) = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
-                                          (uint32_t)h[2] | ((uint32_t)h[3] << 16));
-            *(uint2*)(P + o + var) = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16),
-                                                (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+            *(uint2*)(P + o) = make_uint2(h01, h23);
+            *(uint2*)(P + o + var) = make_uint2(l01, l23);
           }
         }
   }
