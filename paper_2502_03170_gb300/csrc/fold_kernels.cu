@@ -36,6 +36,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "split_pack.cuh"
 #include "tc_kernels.cuh"
 #include "tc_pair_ptx.cuh"
 #include "tc_ptx.cuh"
@@ -170,25 +171,6 @@ PSF_D void decode(const FoldParams& p, int t, int& plane, int& mp, int& nt) {
   const int rem = t - plane * tpp;
   nt = rem / p.m_pairs;
   mp = rem - nt * p.m_pairs;
-}
-
-// Two values split hi + lo at once (packed conversions; the same rounding
-// as split16 element by element): hi = (hi(a), hi(b)), lo likewise, a in the
-// low 16 bits.
-PSF_D void split2(float a, float b, int bf16, uint32_t& hi, uint32_t& lo) {
-  if (bf16) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 f = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(a - f.x, b - f.y);
-    hi = *(const uint32_t*)&h;
-    lo = *(const uint32_t*)&l;
-  } else {
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 f = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
-    hi = *(const uint32_t*)&h;
-    lo = *(const uint32_t*)&l;
-  }
 }
 
 // 16 split values of one output row piece: one 32-byte store each for hi

@@ -23,6 +23,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "split_pack.cuh"
 #include "tc_kernels.cuh"
 #include "tc_pair_ptx.cuh"
 #include "tc_ptx.cuh"
@@ -869,22 +870,20 @@ __global__ void k_pupil_z_split(NodeTable t, int N, const float2* __restrict__ z
       e[k] = cis_cycles(frac_mul_add(f2x{khv[k], klv[k]}, f2x{z.x, z.y}, wv[k]));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      uint16_t hr[4], lr[4], hm[4], lm[4];
+      float2 v[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 v = cmul(amp[c][k], e[k]);
-        split16(v.x, bf16, hr[k], lr[k]);
-        split16(v.y, bf16, hm[k], lm[k]);
-      }
+      for (int k = 0; k < 4; ++k) v[k] = cmul(amp[c][k], e[k]);
+      // packed pairs of consecutive nodes: node k in the low half
+      uint32_t hr0, lr0, hr1, lr1, hm0, lm0, hm1, lm1;
+      split2(v[0].x, v[1].x, bf16, hr0, lr0);
+      split2(v[2].x, v[3].x, bf16, hr1, lr1);
+      split2(v[0].y, v[1].y, bf16, hm0, lm0);
+      split2(v[2].y, v[3].y, bf16, hm1, lm1);
       const size_t row = ((size_t)(zc * 3 + c) * N + ip) * (size_t)(2 * N);
-      auto pack = [](const uint16_t* s) {
-        return make_uint2((uint32_t)s[0] | ((uint32_t)s[1] << 16),
-                          (uint32_t)s[2] | ((uint32_t)s[3] << 16));
-      };
-      *(uint2*)(hi + row + iq) = pack(hr);
-      *(uint2*)(lo + row + iq) = pack(lr);
-      *(uint2*)(hi + row + N + iq) = pack(hm);
-      *(uint2*)(lo + row + N + iq) = pack(lm);
+      *(uint2*)(hi + row + iq) = make_uint2(hr0, hr1);
+      *(uint2*)(lo + row + iq) = make_uint2(lr0, lr1);
+      *(uint2*)(hi + row + N + iq) = make_uint2(hm0, hm1);
+      *(uint2*)(lo + row + N + iq) = make_uint2(lm0, lm1);
     }
   }
 }
