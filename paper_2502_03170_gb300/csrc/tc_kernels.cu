@@ -334,13 +334,9 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
                                (size_t)part * p.N + p0;
             uint32_t hw[16], lw[16];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint16_t h0, l0, h1, l1;
-              split16(p.out_scale * __uint_as_float(r[j]), p.bf16, h0, l0);
-              split16(p.out_scale * __uint_as_float(r[j + 1]), p.bf16, h1, l1);
-              hw[j / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-              lw[j / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-            }
+            for (int j = 0; j < 32; j += 2)
+              split2(p.out_scale * __uint_as_float(r[j]), p.out_scale * __uint_as_float(r[j + 1]),
+                     p.bf16, hw[j / 2], lw[j / 2]);
             if (p0 + 32 <= p.n_rows) {
               // Each lane holds 64 bytes (four 16-byte units) of its own row.
               // A 4 x 4 transpose of units inside every group of four lanes
@@ -1832,11 +1828,6 @@ __global__ void k_bessel_jmat_split(BesselParams p, ThetaTable t, double sB,
 // multiple of 8), stored as 8-byte packs of four 16-bit values per row.
 constexpr int FG_TX = 64, FG_TY = 4;
 
-PSF_D uint2 pack4(const uint16_t (&v)[4]) {
-  return make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
-                    (uint32_t)v[2] | ((uint32_t)v[3] << 16));
-}
-
 __global__ void __launch_bounds__(FG_TX * FG_TY)
 k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable et,
                     const int* __restrict__ slice_em, const float2* __restrict__ zz,
@@ -1865,24 +1856,28 @@ k_bessel_fgen_split(BesselParams p, ThetaTable t, EmitterTable et,
       }
     }
     for (int n = 0; n < n_ord; ++n) {
-      uint16_t hr[4], lr[4], hm[4], lm[4];
+      float2 w[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int j = 4 * q + u;
-        float2 w = v[u];
+        w[u] = v[u];
         if (n_ord > 1 && j < p.n_theta) {
           const float2 g = make_float2((float)t.g[(2 * n) * p.n_theta + j],
                                        (float)t.g[(2 * n + 1) * p.n_theta + j]);
-          w = cmul(g, w);
+          w[u] = cmul(g, w[u]);
         }
-        split16(w.x, bf16, hr[u], lr[u]);
-        split16(w.y, bf16, hm[u], lm[u]);
       }
+      // packed pairs of consecutive nodes: node 4q + u in the low half
+      uint32_t hr0, lr0, hr1, lr1, hm0, lm0, hm1, lm1;
+      split2(w[0].x, w[1].x, bf16, hr0, lr0);
+      split2(w[2].x, w[3].x, bf16, hr1, lr1);
+      split2(w[0].y, w[1].y, bf16, hm0, lm0);
+      split2(w[2].y, w[3].y, bf16, hm1, lm1);
       const size_t r0 = ((size_t)n * plane_rows + 2 * (size_t)s) * Kp + 4 * q, r1 = r0 + Kp;
-      *reinterpret_cast<uint2*>(hi + r0) = pack4(hr);
-      *reinterpret_cast<uint2*>(lo + r0) = pack4(lr);
-      *reinterpret_cast<uint2*>(hi + r1) = pack4(hm);
-      *reinterpret_cast<uint2*>(lo + r1) = pack4(lm);
+      *reinterpret_cast<uint2*>(hi + r0) = make_uint2(hr0, hr1);
+      *reinterpret_cast<uint2*>(lo + r0) = make_uint2(lr0, lr1);
+      *reinterpret_cast<uint2*>(hi + r1) = make_uint2(hm0, hm1);
+      *reinterpret_cast<uint2*>(lo + r1) = make_uint2(lm0, lm1);
     }
   }
 }
