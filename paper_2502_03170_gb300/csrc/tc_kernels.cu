@@ -282,15 +282,32 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
             uint32_t r[32];
             tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
             if (!row_ok) continue;
+            const int bb0 = nt * BOUT + h * 32;
+            const size_t pitch = (size_t)(2 * p.nx);
+            const size_t o0 = ((size_t)(plane * 3 + c) * p.ny + bb0) * pitch + col;
+            if (bb0 + 32 <= p.ny) {
+              // the whole chunk is in range: no per-row test
+              uint16_t* rh = p.R_hi + o0;
+              uint16_t* rl = p.R_lo + o0;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const float gj = (h == part) ? g[j] : go[j];
+                uint16_t hh, ll;
+                split16(sgn * gj * __uint_as_float(r[j]), 1, hh, ll);
+                rh[(size_t)j * pitch] = hh;
+                rl[(size_t)j * pitch] = ll;
+              }
+              continue;
+            }
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const int bb = nt * BOUT + h * 32 + j;
+              const int bb = bb0 + j;
               if (bb >= p.ny) continue;
               // outputs h * 32 + j: the lane's own g for h == part, else the partner's
               const float gj = (h == part) ? g[j] : go[j];
               uint16_t hh, ll;
               split16(sgn * gj * __uint_as_float(r[j]), 1, hh, ll);
-              const size_t o = ((size_t)(plane * 3 + c) * p.ny + bb) * (size_t)(2 * p.nx) + col;
+              const size_t o = o0 + (size_t)j * pitch;
               p.R_hi[o] = hh;
               p.R_lo[o] = ll;
             }
@@ -314,9 +331,17 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
             tmem_ld32(tbase + (uint32_t)(c * BOUT + h * 32), r);
             if (!q_ok) continue;
             float* dst = p.gWz + (((size_t)(plane * 3 + c) * 2 + part) * p.n_rows) * p.m_out + mo;
+            const int pp0 = nt * BOUT + h * 32;
+            if (pp0 + 32 <= p.n_rows) {
+              // the whole chunk is in range: no per-row test
+              float* d0 = dst + (size_t)pp0 * p.m_out;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) d0[(size_t)j * p.m_out] = __uint_as_float(r[j]);
+              continue;
+            }
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const int pp = nt * BOUT + h * 32 + j;
+              const int pp = pp0 + j;
               if (pp < p.n_rows) dst[(size_t)pp * p.m_out] = __uint_as_float(r[j]);
             }
           }
