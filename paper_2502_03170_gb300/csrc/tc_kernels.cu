@@ -201,9 +201,19 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
           uint32_t r[32];
           tmem_ld32(tbase + (uint32_t)(h * 32), r);
           if (grow < p.rows_total) {
+            const int s0 = nt * (BN / 2) + h * 16;
+            if (s0 + 16 <= p.n_slices) {
+              // the whole chunk is in range: no per-slice test
+              float2* d = p.prof + (size_t)s0 * p.rows_total + grow;
+#pragma unroll
+              for (int k = 0; k < 16; ++k)
+                d[(size_t)k * p.rows_total] =
+                    make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
+              continue;
+            }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              const int s = nt * (BN / 2) + h * 16 + k;
+              const int s = s0 + k;
               if (s < p.n_slices)
                 p.prof[(size_t)s * p.rows_total + grow] =
                     make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
@@ -219,9 +229,20 @@ PSF_D void tile_epilogue(const Params& p, uint32_t tbase, int plane, int mt, int
           uint32_t r[32];
           tmem_ld32(tbase + (uint32_t)(h * 32), r);
           if (gi < p.rows_total) {
+            const int col0 = nt * (BN / 2) + h * 16;
+            if (col0 + 16 <= p.n_slices) {
+              // the whole chunk is in range: no per-column test
+              const size_t cs = (size_t)p.n_ord * p.rows_total;
+              float2* d = p.prof + ((size_t)col0 * p.n_ord + plane) * p.rows_total + gi;
+#pragma unroll
+              for (int k = 0; k < 16; ++k)
+                d[(size_t)k * cs] =
+                    make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
+              continue;
+            }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              const int col = nt * (BN / 2) + h * 16 + k;
+              const int col = col0 + k;
               if (col < p.n_slices)
                 p.prof[((size_t)col * p.n_ord + plane) * p.rows_total + gi] =
                     make_float2(sc * __uint_as_float(r[2 * k]), sc * __uint_as_float(r[2 * k + 1]));
